@@ -1,0 +1,403 @@
+"""Plain FP64 CPU oracle for the RBF-FD staggered-node Navier-Stokes hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import or call
+this module: only the tests, the package's smoke check and the benchmark's
+CPU-baseline leg use it.  It shares no code with the CUDA path.
+
+Every function restates a step of the paper (Chu & Schmidt, "RBF-FD
+discretization of the Navier-Stokes equations on scattered but staggered
+nodes") in the plainest form that numpy/scipy allow:
+
+  * stencils: the n nearest beta-nodes of each alpha-node (Section 2.2),
+    brute force, ties broken by node index;
+  * weights: one dense solve of the augmented PHS+poly saddle system per
+    stencil (Section 2.1, Eq. rbf_poly_compact), LU with partial pivoting
+    (numpy.linalg.solve);
+  * operators: CSR matrices D_L^(alpha,beta) (Section 2.2);
+  * the fractional step (Section 3): AB2 convection, Crank-Nicolson viscous
+    solve, divergence, pressure Poisson, pressure, velocity correction, with
+    the Kim & Moin intermediate-velocity boundary values.  The implicit
+    matrices are LU-factorised once, as in the paper (end of Section 3).
+
+Readings of points the paper leaves open (each one is listed in the design doc):
+  R1 local coordinates: shift by the stencil centre, scale by the largest
+     centre-to-node distance s; weights of first derivatives are divided by s
+     and of the Laplacian by s^2 afterwards.
+  R2 monomials in graded lexicographic order 1, x, y, x^2, xy, y^2, ...
+  R3 k-NN ties: sort by (squared distance, index); squared distance is
+     dx*dx + dy*dy with each operation rounded (no fused multiply-add).
+  R4 pressure Poisson: boundary P-rows are replaced by a homogeneous Neumann
+     row n_x D_x + n_y D_y; the constant null space is removed by bordering
+     [L e; 1^T 0][p; lam] = [b; 0], where e is 1 on interior P-rows and 0 on
+     boundary rows (the multiplier absorbs the incompatibility of the
+     non-symmetric L in the interior rows only; the Neumann rows stay
+     homogeneous).  The result is the mean-zero pressure correction.
+  R5 boundary V-rows of the Crank-Nicolson solve are identity rows whose
+     right-hand side is the Kim & Moin value: the wall data g_{j+1} plus
+     dt times the tangential component of D^(VP) p~_j along the wall
+     (the normal component is not added: it is zero under the Neumann
+     pressure condition of the continuous problem).
+  R6 after the velocity correction, boundary V-nodes are overwritten with
+     g_{j+1} (switchable).
+  R7 AB2 at the first step uses C_{-1} = C_0; the flow starts from rest with
+     p~_0 = 0.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+OP_INTERP, OP_DX, OP_DY, OP_LAP = "interp", "dx", "dy", "lap"
+ALL_OPS = (OP_INTERP, OP_DX, OP_DY, OP_LAP)
+
+
+# --------------------------------------------------------------------------
+# Stencils (Section 2.2: row i uses the n nearest beta-nodes of alpha-node i)
+# --------------------------------------------------------------------------
+def knn(ax, ay, bx, by, k: int, chunk: int = 256) -> np.ndarray:
+    """Indices of the k nearest beta-nodes of every alpha-node, nearest first.
+
+    Brute force over all beta-nodes; ordering key (d^2, index) with
+    d^2 = dx*dx + dy*dy evaluated one rounded operation at a time.
+    Returns int64 [n_alpha, k].
+    """
+    ax = np.asarray(ax, np.float64)
+    ay = np.asarray(ay, np.float64)
+    bx = np.asarray(bx, np.float64)
+    by = np.asarray(by, np.float64)
+    nb = bx.size
+    if k > nb:
+        raise ValueError("stencil size exceeds the number of beta-nodes")
+    out = np.empty((ax.size, k), np.int64)
+    cols = np.arange(nb)
+    for s in range(0, ax.size, chunk):
+        dx = bx[None, :] - ax[s:s + chunk, None]
+        dy = by[None, :] - ay[s:s + chunk, None]
+        d2 = dx * dx + dy * dy
+        for r in range(d2.shape[0]):
+            row = d2[r]
+            kth = np.partition(row, k - 1)[k - 1]
+            cand = np.nonzero(row <= kth)[0]
+            order = np.lexsort((cols[cand], row[cand]))[:k]
+            out[s + r] = cand[order]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Local weights (Section 2.1)
+# --------------------------------------------------------------------------
+def monomial_exponents(q: int) -> list[tuple[int, int]]:
+    """(a, b) of x^a y^b for all monomials of degree <= q, graded lex (R2).
+
+    There are (q+1)(q+2)/2 of them (Eq. Lf_PHS); q = -1 means none.
+    """
+    return [(d - b, b) for d in range(q + 1) for b in range(d + 1)]
+
+
+def _phs(r, m):
+    """phi(r) = r^m, m odd (Section 2.1)."""
+    return r ** m
+
+
+def _op_rhs_rbf(op, X, m):
+    """L phi(||x - x_j||) at the stencil centre x = 0 (right side of Eq. w_local)."""
+    r = np.sqrt(X[..., 0] ** 2 + X[..., 1] ** 2)
+    if op == OP_INTERP:
+        return _phs(r, m)
+    # d/dx r^m = m r^(m-2) (x - x_j); at x = 0 this is -m r^(m-2) x_j
+    if op == OP_DX:
+        return -m * r ** (m - 2) * X[..., 0]
+    if op == OP_DY:
+        return -m * r ** (m - 2) * X[..., 1]
+    # 2-D Laplacian of r^m: m(m-1) r^(m-2) + (1/r) m r^(m-1) = m^2 r^(m-2)
+    if op == OP_LAP:
+        return m * m * r ** (m - 2)
+    raise ValueError(op)
+
+
+def _op_rhs_poly(op, q):
+    """L P_i at the stencil centre x = 0 (the vanishing-moment right side)."""
+    out = []
+    for a, b in monomial_exponents(q):
+        if op == OP_INTERP:
+            v = 1.0 if (a, b) == (0, 0) else 0.0
+        elif op == OP_DX:
+            v = 1.0 if (a, b) == (1, 0) else 0.0
+        elif op == OP_DY:
+            v = 1.0 if (a, b) == (0, 1) else 0.0
+        elif op == OP_LAP:
+            v = 2.0 if (a, b) in ((2, 0), (0, 2)) else 0.0
+        else:
+            raise ValueError(op)
+        out.append(v)
+    return np.array(out)
+
+
+def augmented_matrix(X: np.ndarray, m: int, q: int) -> np.ndarray:
+    """A_aug = [[A, P], [P^T, 0]] of Eq. rbf_poly_compact for stencil nodes X.
+
+    X: [..., n, 2] local (shifted, scaled) coordinates.
+    A_ij = phi(||x_i - x_j||) (Eq. A), P_ji = P_i(x_j).
+    """
+    n = X.shape[-2]
+    mono = monomial_exponents(q)
+    S = n + len(mono)
+    batch = X.shape[:-2]
+    Aaug = np.zeros(batch + (S, S))
+    diff = X[..., :, None, :] - X[..., None, :, :]
+    r = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
+    Aaug[..., :n, :n] = _phs(r, m)
+    for i, (a, b) in enumerate(mono):
+        col = X[..., 0] ** a * X[..., 1] ** b
+        Aaug[..., :n, n + i] = col
+        Aaug[..., n + i, :n] = col
+    return Aaug
+
+
+def stencil_weights(center, nodes, m: int, q: int, ops=(OP_DX, OP_DY, OP_LAP)):
+    """Weights w (Eq. Lf) of each operator for one or many stencils.
+
+    center: [..., 2]; nodes: [..., n, 2] (global coordinates).
+    Returns {op: [..., n]} and the per-stencil scale s.
+    Steps: shift to the centre and divide by s = max ||x_j - x_0|| (R1);
+    assemble A_aug (Eq. rbf_poly_compact); solve A_aug [w; c] = [L phi; L P]
+    by LU with partial pivoting; keep w; undo the scaling.
+    """
+    center = np.asarray(center, np.float64)
+    nodes = np.asarray(nodes, np.float64)
+    n = nodes.shape[-2]
+    X = nodes - center[..., None, :]
+    s = np.sqrt((X[..., 0] ** 2 + X[..., 1] ** 2).max(-1))
+    X = X / s[..., None, None]
+    Aaug = augmented_matrix(X, m, q)
+    rhs = []
+    for op in ops:
+        top = _op_rhs_rbf(op, X, m)
+        bot = np.broadcast_to(_op_rhs_poly(op, q), X.shape[:-2] + (Aaug.shape[-1] - n,))
+        rhs.append(np.concatenate([top, bot], -1))
+    B = np.stack(rhs, -1)  # [..., S, nops]
+    sol = np.linalg.solve(Aaug, B)
+    out = {}
+    for j, op in enumerate(ops):
+        w = sol[..., :n, j]
+        if op in (OP_DX, OP_DY):
+            w = w / s[..., None]
+        elif op == OP_LAP:
+            w = w / (s[..., None] ** 2)
+        out[op] = w
+    return out, s
+
+
+def build_weights(ax, ay, bx, by, k: int, m: int = 7, q: int = 3,
+                  ops=(OP_DX, OP_DY, OP_LAP), chunk: int = 4096, idx=None):
+    """Stencils and weights of D_L^(alpha,beta) for every alpha-node.
+
+    Returns (idx [n_alpha, k] int64, {op: w [n_alpha, k] float64}).
+    """
+    ax = np.asarray(ax, np.float64)
+    ay = np.asarray(ay, np.float64)
+    bx = np.asarray(bx, np.float64)
+    by = np.asarray(by, np.float64)
+    if idx is None:
+        idx = knn(ax, ay, bx, by, k)
+    W = {op: np.empty(idx.shape) for op in ops}
+    for s0 in range(0, ax.size, chunk):
+        sl = slice(s0, s0 + chunk)
+        c = np.stack([ax[sl], ay[sl]], -1)
+        X = np.stack([bx[idx[sl]], by[idx[sl]]], -1)
+        w, _ = stencil_weights(c, X, m, q, ops)
+        for op in ops:
+            W[op][sl] = w[op]
+    return idx, W
+
+
+def csr(idx: np.ndarray, w: np.ndarray, n_cols: int) -> sp.csr_matrix:
+    """The sparse matrix D with D[i, idx[i, s]] = w[i, s] (Section 2.2)."""
+    n_rows, k = idx.shape
+    indptr = np.arange(0, n_rows * k + 1, k)
+    return sp.csr_matrix((w.ravel(), idx.ravel(), indptr), shape=(n_rows, n_cols))
+
+
+# --------------------------------------------------------------------------
+# Accuracy measures (Section 4)
+# --------------------------------------------------------------------------
+def local_spacing(x, y, n_adj: int = 6) -> np.ndarray:
+    """Delta r_j: mean distance from node j to its n_adj nearest other nodes
+    of the same set (reading of Section 3's 'locally averaged distance')."""
+    idx = knn(x, y, x, y, n_adj + 1)
+    d = np.hypot(x[idx[:, 1:]] - x[:, None], y[idx[:, 1:]] - y[:, None])
+    return d.mean(1)
+
+
+def modified_wavenumber(w_dx, w_dy, idx, ax, ay, bx, by, kx, ky):
+    """Radial modified wavenumber k* of Eq. 2d_mw at every alpha-node.
+
+    delta_r = (kx D_x + ky D_y)/k~ applied to exp(i k~ r~), r~ = (kx x + ky y)/k~,
+    then multiplied by -i exp(-i k~ r~(x_0)).
+    """
+    kt = np.hypot(kx, ky)
+    phase_b = np.exp(1j * (kx * bx + ky * by))
+    phase_a = np.exp(-1j * (kx * ax + ky * ay))
+    d_r = (kx * w_dx + ky * w_dy) / kt
+    return (-1j * (d_r * phase_b[idx]).sum(1) * phase_a)
+
+
+# --------------------------------------------------------------------------
+# The fractional-step Navier-Stokes solver (Section 3)
+# --------------------------------------------------------------------------
+@dataclass
+class Operators:
+    """The seven differentiation matrices of Section 4 plus P->P first
+    derivatives for the Neumann rows of reading R4."""
+    vv_x: sp.csr_matrix
+    vv_y: sp.csr_matrix
+    vv_lap: sp.csr_matrix
+    pv_x: sp.csr_matrix  # D^(P,V): V-values -> P-nodes
+    pv_y: sp.csr_matrix
+    pp_lap: sp.csr_matrix
+    pp_x: sp.csr_matrix
+    pp_y: sp.csr_matrix
+    vp_x: sp.csr_matrix  # D^(V,P): P-values -> V-nodes
+    vp_y: sp.csr_matrix
+    raw: dict
+
+
+def build_operators(nodes, k: int = 28, m: int = 7, q: int = 3) -> Operators:
+    """All operators of Section 4 for a staggered node set."""
+    px, py, vx, vy = nodes.px, nodes.py, nodes.vx, nodes.vy
+    M, N = px.size, vx.size
+    i_vv, w_vv = build_weights(vx, vy, vx, vy, k, m, q, (OP_DX, OP_DY, OP_LAP))
+    i_pv, w_pv = build_weights(px, py, vx, vy, k, m, q, (OP_DX, OP_DY))
+    i_pp, w_pp = build_weights(px, py, px, py, k, m, q, (OP_DX, OP_DY, OP_LAP))
+    i_vp, w_vp = build_weights(vx, vy, px, py, k, m, q, (OP_DX, OP_DY))
+    raw = {"vv": (i_vv, w_vv), "pv": (i_pv, w_pv), "pp": (i_pp, w_pp), "vp": (i_vp, w_vp)}
+    return Operators(
+        vv_x=csr(i_vv, w_vv[OP_DX], N), vv_y=csr(i_vv, w_vv[OP_DY], N),
+        vv_lap=csr(i_vv, w_vv[OP_LAP], N),
+        pv_x=csr(i_pv, w_pv[OP_DX], N), pv_y=csr(i_pv, w_pv[OP_DY], N),
+        pp_lap=csr(i_pp, w_pp[OP_LAP], M), pp_x=csr(i_pp, w_pp[OP_DX], M),
+        pp_y=csr(i_pp, w_pp[OP_DY], M),
+        vp_x=csr(i_vp, w_vp[OP_DX], M), vp_y=csr(i_vp, w_vp[OP_DY], M), raw=raw)
+
+
+def poisson_matrix(ops: Operators, p_boundary, p_nx, p_ny) -> sp.csr_matrix:
+    """Bordered pressure matrix [[L, e], [1^T, 0]] of reading R4.
+
+    L = D^(P,P)_Lap (Eq. pressure_Poisson) with every boundary P-row replaced
+    by n_x D^(P,P)_x + n_y D^(P,P)_y; e = indicator of interior P-rows.
+    """
+    M = ops.pp_lap.shape[0]
+    bnd = sp.diags(p_boundary.astype(float))
+    inn = sp.diags((~p_boundary).astype(float))
+    L = inn @ ops.pp_lap + bnd @ (sp.diags(p_nx) @ ops.pp_x + sp.diags(p_ny) @ ops.pp_y)
+    e = sp.csr_matrix((~p_boundary).astype(float)[:, None])
+    one = sp.csr_matrix(np.ones((1, M)))
+    return sp.bmat([[L, e], [one, None]], format="csc")
+
+
+def helmholtz_matrix(ops: Operators, v_boundary, a: float) -> sp.csr_matrix:
+    """I - a D^(V,V)_Lap (Eq. u_ss, a = dt/(2 Re)) with identity boundary rows (R5)."""
+    N = ops.vv_lap.shape[0]
+    inn = sp.diags((~v_boundary).astype(float))
+    return (sp.identity(N) - a * (inn @ ops.vv_lap)).tocsc()
+
+
+@dataclass
+class FlowState:
+    u: np.ndarray
+    v: np.ndarray
+    cu_prev: np.ndarray  # C_{j-1}(u)
+    cv_prev: np.ndarray
+    pt: np.ndarray       # pressure correction p~_j
+    p: np.ndarray        # pressure p_j
+    lam: float = 0.0     # bordering multiplier of the last Poisson solve
+    j: int = 0
+
+
+class FractionalStep:
+    """Three-stage semi-implicit step of Section 3 on a staggered node set."""
+
+    def __init__(self, nodes, Re: float, dt: float, k: int = 28, m: int = 7,
+                 q: int = 3, ops: Operators | None = None, overwrite_bc: bool = True):
+        self.nodes = nodes
+        self.Re = float(Re)
+        self.dt = float(dt)
+        self.a = self.dt / (2.0 * self.Re)
+        self.ops = ops if ops is not None else build_operators(nodes, k, m, q)
+        self.vb = nodes.v_boundary
+        self.pb = nodes.p_boundary
+        # unit tangent (-n_y, n_x) of the wall at boundary V-nodes (R5)
+        self.tx = -nodes.v_ny
+        self.ty = nodes.v_nx
+        self.overwrite_bc = overwrite_bc
+        self.H = helmholtz_matrix(self.ops, self.vb, self.a)
+        self.Pb = poisson_matrix(self.ops, self.pb, nodes.p_nx, nodes.p_ny)
+        self.H_lu = spla.splu(self.H)
+        self.P_lu = spla.splu(self.Pb)
+
+    def initial_state(self, u0=None, v0=None) -> FlowState:
+        N, M = self.nodes.N, self.nodes.M
+        u = np.zeros(N) if u0 is None else np.array(u0, np.float64)
+        v = np.zeros(N) if v0 is None else np.array(v0, np.float64)
+        return FlowState(u=u, v=v, cu_prev=np.zeros(N), cv_prev=np.zeros(N),
+                         pt=np.zeros(M), p=np.zeros(M))
+
+    def convection(self, u, v, qv):
+        """C(q) = -[u o (D_x q) + v o (D_y q)] on the V-grid (Section 3, stage 1)."""
+        return -(u * (self.ops.vv_x @ qv) + v * (self.ops.vv_y @ qv))
+
+    def step(self, st: FlowState, gu, gv) -> FlowState:
+        """Advance from step j to j+1.  gu, gv: boundary values g_{j+1} at
+        every V-node (only the boundary entries are used)."""
+        o, dt, a, vb = self.ops, self.dt, self.a, self.vb
+        cu, cv, uss, vss, F = self.intermediate(st, gu, gv)
+        # stage 3: pressure Poisson, pressure, correction
+        b = np.where(self.pb, 0.0, F / dt)
+        sol = self.P_lu.solve(np.concatenate([b, [0.0]]))
+        pt, lam = sol[:-1], sol[-1]
+        p = pt - a * (o.pp_lap @ pt)
+        un = uss - dt * (o.vp_x @ pt)
+        vn = vss - dt * (o.vp_y @ pt)
+        if self.overwrite_bc:
+            un[vb] = gu[vb]
+            vn[vb] = gv[vb]
+        return FlowState(u=un, v=vn, cu_prev=cu, cv_prev=cv, pt=pt, p=p,
+                         lam=float(lam), j=st.j + 1)
+
+    def intermediate(self, st: FlowState, gu, gv):
+        """Stages 1-2 and the divergence of stage 3: C_j(u), C_j(v), u**, v**
+        and F_{j+1} = D^(P,V)_x u** + D^(P,V)_y v** (Eq. divergence)."""
+        o, dt, a, vb = self.ops, self.dt, self.a, self.vb
+        # stage 1: Adams-Bashforth convection
+        cu = self.convection(st.u, st.v, st.u)
+        cv = self.convection(st.u, st.v, st.v)
+        cu_prev = cu if st.j == 0 else st.cu_prev
+        cv_prev = cv if st.j == 0 else st.cv_prev
+        us = st.u + dt * (1.5 * cu - 0.5 * cu_prev)
+        vs = st.v + dt * (1.5 * cv - 0.5 * cv_prev)
+        # stage 2: Crank-Nicolson viscous step, Kim & Moin boundary values
+        ru = us + a * (o.vv_lap @ us)
+        rv = vs + a * (o.vv_lap @ vs)
+        gpx = o.vp_x @ st.pt
+        gpy = o.vp_y @ st.pt
+        gt = self.tx * gpx + self.ty * gpy  # tangential pressure-gradient
+        ru[vb] = gu[vb] + dt * (gt * self.tx)[vb]
+        rv[vb] = gv[vb] + dt * (gt * self.ty)[vb]
+        uss = self.H_lu.solve(ru)
+        vss = self.H_lu.solve(rv)
+        F = o.pv_x @ uss + o.pv_y @ vss
+        return cu, cv, uss, vss, F
+
+
+def lid_bc(nodes, lid_u=1.0):
+    """Cavity boundary data: u = lid_u on the top wall, u = v = 0 elsewhere
+    (Section 5.1).  lid_u may be a scalar or a per-V-node array."""
+    from paper_2206_06495_gb300.nodesets import WALL_TOP
+    from_top = nodes.v_wall == WALL_TOP
+    gu = np.zeros(nodes.N)
+    gu[from_top] = (np.broadcast_to(lid_u, (nodes.N,)))[from_top]
+    gv = np.zeros(nodes.N)
+    return gu, gv

@@ -1,0 +1,310 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a closed form, an
+invariant, a special case that reduces to a simpler textbook problem, a
+convergence rate, a brute-force count, or a bound the paper prints.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import rbffd_oracle as O
+from paper_2206_06495_gb300 import nodesets as ns
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+@pytest.fixture(scope="module")
+def cavity20():
+    return ns.jittered_cavity(20, 0)
+
+
+@pytest.fixture(scope="module")
+def ops20(cavity20):
+    return O.build_operators(cavity20)
+
+
+def test_parameters_and_monomial_count():
+    g = _golden("parameters.txt")
+    assert len(O.monomial_exponents(int(g["q"]))) == g["n_monomials_q3"]
+    assert len(O.monomial_exponents(int(g["q_variant"]))) == g["n_monomials_q4"]
+    # graded lexicographic order, reading R2
+    assert O.monomial_exponents(2) == [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]
+
+
+# ---------------------------------------------------------------- stencils
+def test_knn_exact_lattice_shells():
+    """On a perfect unit lattice the shells around an interior node hold
+    1, 4, 4, 4, 8, 4, 4 nodes at d^2 = 0, 1, 2, 4, 5, 8, 9; the 28 nearest are
+    the 25 nodes with d^2 <= 8 plus the 3 lowest-index nodes at d^2 = 9."""
+    n = 11
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x = ii.ravel().astype(float)
+    y = jj.ravel().astype(float)
+    c = 5 * n + 5
+    idx = O.knn(x[[c]], y[[c]], x, y, 28)[0]
+    d2 = (x[idx] - x[c]) ** 2 + (y[idx] - y[c]) ** 2
+    assert idx[0] == c
+    assert np.all(np.diff(d2) >= 0)
+    assert np.count_nonzero(d2 <= 8) == 25
+    ring9 = np.nonzero((x - x[c]) ** 2 + (y - y[c]) ** 2 == 9)[0]
+    assert sorted(idx[d2 == 9]) == sorted(ring9)[:3]
+
+
+def test_knn_brute_force_small_random():
+    """Against a direct enumeration of all pairs on a tiny set."""
+    rng = np.random.default_rng(5)
+    x, y = rng.random(60), rng.random(60)
+    qx, qy = rng.random(7), rng.random(7)
+    idx = O.knn(qx, qy, x, y, 9)
+    for i in range(7):
+        pairs = sorted(((x[j] - qx[i]) ** 2 + (y[j] - qy[i]) ** 2, j) for j in range(60))
+        assert list(idx[i]) == [j for _, j in pairs[:9]]
+
+
+# ---------------------------------------------------------------- weights
+@pytest.mark.parametrize("q", [3, 4])
+def test_polynomial_exactness_all_grids(cavity20, q):
+    """P1: every operator reproduces derivatives of all monomials of degree
+    <= q exactly (vanishing-moment conditions, Section 2.1)."""
+    nd = cavity20
+    pairs = {"vv": (nd.vx, nd.vy, nd.vx, nd.vy), "pv": (nd.px, nd.py, nd.vx, nd.vy),
+             "pp": (nd.px, nd.py, nd.px, nd.py), "vp": (nd.vx, nd.vy, nd.px, nd.py)}
+    for name, (ax, ay, bx, by) in pairs.items():
+        idx, W = O.build_weights(ax, ay, bx, by, 28, 7, q, O.ALL_OPS)
+        for a, b in O.monomial_exponents(q):
+            f = bx ** a * by ** b
+            ex = {
+                O.OP_INTERP: ax ** a * ay ** b,
+                O.OP_DX: a * ax ** max(a - 1, 0) * ay ** b,
+                O.OP_DY: b * ax ** a * ay ** max(b - 1, 0),
+                O.OP_LAP: a * (a - 1) * ax ** max(a - 2, 0) * ay ** b
+                + b * (b - 1) * ax ** a * ay ** max(b - 2, 0),
+            }
+            for op in O.ALL_OPS:
+                got = (W[op] * f[idx]).sum(1)
+                scale = 1.0 / nd.h ** (2 if op == O.OP_LAP else 1)
+                assert np.abs(got - ex[op]).max() < 1e-8 * scale, (name, op, a, b)
+
+
+def test_exactness_stops_at_degree_q(cavity20):
+    """The reproduction is not accidental: degree q+1 is not exact."""
+    nd = cavity20
+    idx, W = O.build_weights(nd.vx, nd.vy, nd.vx, nd.vy, 28, 7, 3, (O.OP_DX,))
+    f = nd.vx ** 4
+    err = np.abs((W[O.OP_DX] * f[idx]).sum(1) - 4 * nd.vx ** 3).max()
+    assert err > 1e-6
+
+
+def test_weight_sum_identities(ops20):
+    """Sum of weights: 0 for derivatives, and sum w_j x_j = 1 for d/dx."""
+    for D in (ops20.vv_x, ops20.vv_lap, ops20.pv_y, ops20.pp_lap, ops20.vp_x):
+        assert np.abs(D.sum(1)).max() < 1e-8 / 0.05 ** 2
+
+
+def test_interpolation_is_lagrange_on_collocated(cavity20):
+    """An interpolant through the stencil reproduces the data at the stencil
+    nodes, so collocated interpolation weights are the unit vector e_0."""
+    nd = cavity20
+    idx, W = O.build_weights(nd.px, nd.py, nd.px, nd.py, 28, 7, 3, (O.OP_INTERP,))
+    e0 = np.zeros(28)
+    e0[0] = 1.0
+    assert np.abs(W[O.OP_INTERP] - e0).max() < 1e-9
+
+
+def test_unisolvent_special_case_is_polynomial_interpolation():
+    """P2: with n equal to the number of monomials the vanishing-moment rows
+    alone fix w (P^T w = L P); the RBF block drops out.  Checked against the
+    transposed Vandermonde system solved on its own."""
+    rng = np.random.default_rng(3)
+    q = 3
+    mono = O.monomial_exponents(q)
+    X = rng.uniform(-1, 1, (len(mono), 2))
+    c = np.array([0.1, -0.2])
+    w, _ = O.stencil_weights(c, X, 7, q, (O.OP_DX, O.OP_LAP))
+    Xl = X - c
+    V = np.array([[xl ** a * yl ** b for a, b in mono] for xl, yl in Xl])
+    rhs_dx = np.array([1.0 if ab == (1, 0) else 0.0 for ab in mono])
+    rhs_lap = np.array([2.0 if ab in ((2, 0), (0, 2)) else 0.0 for ab in mono])
+    assert np.allclose(w[O.OP_DX], np.linalg.solve(V.T, rhs_dx), rtol=1e-8, atol=1e-8)
+    assert np.allclose(w[O.OP_LAP], np.linalg.solve(V.T, rhs_lap), rtol=1e-8, atol=1e-8)
+
+
+def test_scale_translation_invariance():
+    """P3: weights of a translated and scaled stencil scale like the operator."""
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (28, 2))
+    c = np.zeros(2)
+    w1, _ = O.stencil_weights(c, X, 7, 3, (O.OP_DX, O.OP_LAP))
+    s, t = 3.7e-3, np.array([12.5, -4.0])
+    w2, _ = O.stencil_weights(c * s + t, X * s + t, 7, 3, (O.OP_DX, O.OP_LAP))
+    assert np.abs(w2[O.OP_DX] * s - w1[O.OP_DX]).max() < 1e-10 * np.abs(w1[O.OP_DX]).max()
+    assert np.abs(w2[O.OP_LAP] * s * s - w1[O.OP_LAP]).max() < 1e-10 * np.abs(w1[O.OP_LAP]).max()
+
+
+def test_truncation_error_converges_for_wave_function():
+    """P4: error of D_x and D_Lap on f = sin(8 pi x + 4 pi y) cos(6 pi y)
+    falls under refinement at a high order (q sets the order)."""
+    errs = {"dx": [], "lap": []}
+    hs = []
+    for n in (33, 65, 129):
+        nd = ns.jittered_cavity(n, 1)
+        x, y = nd.px, nd.py
+        inner = (x > 0.2) & (x < 0.8) & (y > 0.2) & (y < 0.8)
+        ax, ay = x[inner], y[inner]
+        idx, W = O.build_weights(ax, ay, x, y, 28, 7, 3, (O.OP_DX, O.OP_LAP))
+        f, fx, fy, lap = ns.wave_test_function(x, y)
+        _, efx, _, elap = ns.wave_test_function(ax, ay)
+        # mean error over max |L f|, the form of Eq. relative_error
+        errs["dx"].append(np.abs((W[O.OP_DX] * f[idx]).sum(1) - efx).mean() / np.abs(efx).max())
+        errs["lap"].append(np.abs((W[O.OP_LAP] * f[idx]).sum(1) - elap).mean() / np.abs(elap).max())
+    # q = 3: first derivatives O(h^3), second derivatives O(h^2)
+    for key, lo in (("dx", 2.6), ("lap", 1.8)):
+        e = np.array(errs[key])
+        rate = np.log(e[0] / e[-1]) / np.log(4.0)
+        assert np.all(e[1:] < e[:-1]) and rate > lo, (key, e, rate)
+
+
+def test_modified_wavenumber_within_paper_bound():
+    """P5 with the paper's printed bound: at k~ Delta r = sqrt(2) the radial
+    modified wavenumber of the 28-point (7, 3) operators deviates from k~ by
+    at most 1.5 % over wave angles (Section 6), on the collocated grids.
+    Delta r: mean distance to the 6 nearest same-grid nodes (reading R10)."""
+    bound = _golden("mw_deviation_bounds.txt")["all_angles_bound"]
+    nd = ns.jittered_cavity(40, 0)
+    h = nd.h
+    for ax, ay in ((nd.vx, nd.vy), (nd.px, nd.py)):
+        idx, W = O.build_weights(ax, ay, ax, ay, 28, 7, 3, (O.OP_DX, O.OP_DY, O.OP_LAP))
+        dr = O.local_spacing(ax, ay).mean()
+        inner = (ax > 5 * h) & (ax < 1 - 5 * h) & (ay > 5 * h) & (ay < 1 - 5 * h)
+        for th in np.linspace(0, np.pi / 2, 5):
+            kt = np.sqrt(2.0) / dr
+            kx, ky = kt * np.cos(th), kt * np.sin(th)
+            ks = O.modified_wavenumber(W[O.OP_DX], W[O.OP_DY], idx, ax, ay, ax, ay, kx, ky)
+            assert np.abs(ks[inner].real / kt - 1).mean() < bound
+            ph = np.exp(1j * (kx * ax + ky * ay))
+            k2 = -(W[O.OP_LAP] * ph[idx]).sum(1) * np.conj(ph)
+            assert np.abs(k2[inner].real / kt ** 2 - 1).mean() < bound
+        # and the spectral limit: k*/k~ -> 1 as k~ Delta r -> 0
+        kt = 0.05 / dr
+        ks = O.modified_wavenumber(W[O.OP_DX], W[O.OP_DY], idx, ax, ay, ax, ay, kt, 0.0)
+        assert np.abs(ks[inner] / kt - 1).max() < 1e-5
+
+
+# ---------------------------------------------------------------- the step
+def _tg(x, y, t, Re):
+    e = np.exp(-2 * t / Re)
+    return (-np.cos(x) * np.sin(y) * e, np.sin(x) * np.cos(y) * e,
+            -0.25 * (np.cos(2 * x) + np.cos(2 * y)) * e * e)
+
+
+def _tg_run(n, dt, T, Re=10.0):
+    nd = ns.jittered_cavity(n, 0, length=np.pi)
+    fs = O.FractionalStep(nd, Re=Re, dt=dt)
+    u0, v0, _ = _tg(nd.vx, nd.vy, 0.0, Re)
+    st = fs.initial_state(u0, v0)
+    steps = int(round(T / dt))
+    for j in range(steps):
+        gu, gv, _ = _tg(nd.vx, nd.vy, (j + 1) * dt, Re)
+        st = fs.step(st, gu, gv)
+    return nd, st, steps * dt
+
+
+def test_taylor_green_spatial_convergence():
+    """P6: the decaying Taylor-Green vortex on [0, pi]^2 with its exact wall
+    data.  Velocity and mean-free pressure errors fall at high order."""
+    Re = 10.0
+    eu, ep = [], []
+    for n in (9, 17, 33):
+        nd, st, T = _tg_run(n, 0.005, 0.25, Re)
+        ue, ve, _ = _tg(nd.vx, nd.vy, T, Re)
+        _, _, pe = _tg(nd.px, nd.py, T, Re)
+        eu.append(max(np.abs(st.u - ue).max(), np.abs(st.v - ve).max()))
+        ep.append(np.abs((st.p - st.p.mean()) - (pe - pe.mean())).max())
+    eu, ep = np.array(eu), np.array(ep)
+    assert eu[-1] < 1e-4
+    assert np.all(np.log2(eu[:-1] / eu[1:]) > 2.5), eu
+    assert ep[-1] < 1e-3 and np.all(ep[1:] < ep[:-1]), ep
+
+
+def test_taylor_green_time_refinement():
+    """Error against a fine-step run on the same nodes falls with dt."""
+    ref = _tg_run(17, 0.000625, 0.2)[1]
+    errs = []
+    for dt in (0.01, 0.005, 0.0025):
+        st = _tg_run(17, dt, 0.2)[1]
+        errs.append(np.abs(st.u - ref.u).max())
+    errs = np.array(errs)
+    assert np.all(errs[:-1] / errs[1:] > 1.8), errs
+
+
+def test_projection_reduces_divergence(ops20):
+    """P7 / R13: after the correction the interior divergence is far below
+    that of the intermediate field, and shrinks under refinement."""
+    ratios = []
+    for n in (20, 40):
+        nd = ns.jittered_cavity(n, 0)
+        fs = O.FractionalStep(nd, Re=100.0, dt=2e-3)
+        st = fs.initial_state()
+        gu, gv = O.lid_bc(nd)
+        for _ in range(20):
+            st = fs.step(st, gu, gv)
+        _, _, uss, vss, F = fs.intermediate(st, gu, gv)
+        st2 = fs.step(st, gu, gv)
+        inner = ~nd.p_boundary
+        div = fs.ops.pv_x @ st2.u + fs.ops.pv_y @ st2.v
+        ratios.append(np.linalg.norm(div[inner]) / np.linalg.norm(F[inner]))
+    assert ratios[0] < 0.6 and ratios[1] < 0.6 * ratios[0], ratios
+
+
+def test_bordered_poisson_compatible_rhs_has_zero_multiplier(ops20, cavity20):
+    """R4: for a right side in the range of L the multiplier vanishes and the
+    solution is the generating field minus its mean."""
+    nd = cavity20
+    fs = O.FractionalStep(nd, Re=100.0, dt=2e-3, ops=ops20)
+    p = np.cos(3 * nd.px) * np.sin(2 * nd.py) + nd.px ** 2
+    A = fs.Pb.tocsr()
+    M = nd.M
+    b = A[:M, :M] @ p
+    sol = fs.P_lu.solve(np.concatenate([b, [0.0]]))
+    assert abs(sol[-1]) < 1e-8
+    assert np.abs(sol[:-1] - (p - p.mean())).max() < 1e-8
+
+
+def test_helmholtz_boundary_rows_are_identity(ops20, cavity20):
+    nd = cavity20
+    fs = O.FractionalStep(nd, Re=100.0, dt=2e-3, ops=ops20)
+    H = fs.H.tocsr()
+    b = np.nonzero(nd.v_boundary)[0]
+    for i in b[:20]:
+        row = H.getrow(i).toarray().ravel()
+        e = np.zeros(nd.N)
+        e[i] = 1.0
+        assert np.array_equal(row, e)
+
+
+def test_cavity_runs_stably_and_keeps_wall_data(cavity20, ops20):
+    """Config-0-like cavity (Re 100, dt 2e-3) stays bounded; wall nodes hold
+    the lid and no-slip data exactly (reading R6)."""
+    nd = cavity20
+    fs = O.FractionalStep(nd, Re=100.0, dt=2e-3, ops=ops20)
+    st = fs.initial_state()
+    gu, gv = O.lid_bc(nd)
+    for _ in range(150):
+        st = fs.step(st, gu, gv)
+    assert np.isfinite(st.u).all() and np.abs(st.u).max() <= 1.0 + 1e-9
+    vb = nd.v_boundary
+    assert np.array_equal(st.u[vb], gu[vb]) and np.array_equal(st.v[vb], gv[vb])
+    assert abs(st.pt.mean()) < 1e-12

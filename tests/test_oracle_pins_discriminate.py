@@ -1,0 +1,83 @@
+"""The pins catch plausible mistakes: each test plants one in the oracle (on
+the CPU, through monkeypatching) and checks that a pin then fails."""
+import numpy as np
+import pytest
+
+from oracle import rbffd_oracle as O
+from tests import test_oracle_pins as pins
+
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def test_wrong_laplacian_of_phs_is_caught(monkeypatch):
+    """m(m-1) r^(m-2) (the 1-D second derivative) instead of m^2 r^(m-2)."""
+    orig = O._op_rhs_rbf
+
+    def bad(op, X, m):
+        if op == O.OP_LAP:
+            r = np.sqrt(X[..., 0] ** 2 + X[..., 1] ** 2)
+            return m * (m - 1) * r ** (m - 2)
+        return orig(op, X, m)
+
+    monkeypatch.setattr(O, "_op_rhs_rbf", bad)
+    assert _fails(pins.test_modified_wavenumber_within_paper_bound)
+
+
+def test_wrong_sign_of_rbf_derivative_is_caught(monkeypatch):
+    orig = O._op_rhs_rbf
+
+    def bad(op, X, m):
+        if op == O.OP_DX:
+            return -orig(op, X, m)
+        return orig(op, X, m)
+
+    monkeypatch.setattr(O, "_op_rhs_rbf", bad)
+    assert _fails(pins.test_modified_wavenumber_within_paper_bound)
+
+
+def test_transposed_polynomial_block_is_caught(monkeypatch):
+    """Swapping x and y in the monomials of the P block."""
+    orig = O.augmented_matrix
+
+    def bad(X, m, q):
+        return orig(X[..., ::-1], m, q) * 0 + _mix(X, m, q, orig)
+
+    def _mix(X, m, q, f):
+        A = f(X, m, q)
+        n = X.shape[-2]
+        Xs = X[..., ::-1]
+        B = f(Xs, m, q)
+        A[..., :n, n:] = B[..., :n, n:]
+        A[..., n:, :n] = B[..., n:, :n]
+        return A
+
+    monkeypatch.setattr(O, "augmented_matrix", bad)
+    assert _fails(pins.test_polynomial_exactness_all_grids, pins.ns.jittered_cavity(20, 0), 3)
+
+
+@pytest.mark.parametrize("mistake", ["convection_sign", "drop_ab2", "pressure_sign"])
+def test_step_mistakes_are_caught_by_taylor_green(monkeypatch, mistake):
+    if mistake == "convection_sign":
+        orig = O.FractionalStep.convection
+        monkeypatch.setattr(O.FractionalStep, "convection",
+                            lambda self, u, v, q: -orig(self, u, v, q))
+    elif mistake == "drop_ab2":
+        orig = O.FractionalStep.convection
+        monkeypatch.setattr(O.FractionalStep, "convection",
+                            lambda self, u, v, q: 0.0 * orig(self, u, v, q))
+    else:
+        orig_init = O.FractionalStep.__init__
+
+        def init(self, *a, **k):
+            orig_init(self, *a, **k)
+            self.ops.vp_x = -self.ops.vp_x
+            self.ops.vp_y = -self.ops.vp_y
+        monkeypatch.setattr(O.FractionalStep, "__init__", init)
+    with np.errstate(all="ignore"):
+        assert _fails(pins.test_taylor_green_spatial_convergence)
