@@ -1,0 +1,215 @@
+/*
+ * rbffd.h - C ABI of the GB300 RBF-FD staggered-node Navier-Stokes hot path.
+ *
+ * The method is the semi-implicit fractional-step solver of Chu & Schmidt,
+ * "RBF-FD discretization of the Navier-Stokes equations on scattered but
+ * staggered nodes": polyharmonic-spline-plus-polynomial (PHS+poly) stencil
+ * weights (Section 2), sparse differentiation matrices between a pressure
+ * node set (P-grid) and a velocity node set (V-grid) (Section 2.2, Section 4),
+ * and the three-stage time step of Section 3.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an int status: RBFFD_OK (0) or a negative RBFFD_ERR_*.
+ *    No exception crosses the ABI and nothing calls exit/abort.
+ *    rbffd_last_error(ctx) gives a message for the last failing call on ctx.
+ *  - Array arguments are DEVICE pointers owned by the caller unless stated
+ *    otherwise.  The library owns only the workspace inside the opaque
+ *    rbffd_ctx, released by rbffd_destroy.
+ *  - Work is issued on the caller's cudaStream_t.  Calls that report a
+ *    device-side status (singular stencil, Krylov convergence) synchronise
+ *    that stream before returning.
+ *  - Sparse operators use a slot-major ELL layout: for an operator with n
+ *    rows, stencil size k and leading dimension ld >= n (a multiple of 32),
+ *    idx[s * ld + i] is the s-th stencil node of row i (int32, nearest first)
+ *    and w[s * ld + i] its weight.  Operators built on the same node pair
+ *    share one idx array.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RBFFD_OK 0
+#define RBFFD_ERR_INVALID_ARG (-1)      /* null pointer, bad size, even m, k too small or too large */
+#define RBFFD_ERR_SINGULAR_STENCIL (-2) /* an augmented system had a zero or non-finite pivot */
+#define RBFFD_ERR_NOT_CONVERGED (-3)    /* a Krylov solve reached its iteration cap */
+#define RBFFD_ERR_NONFINITE (-4)        /* a non-finite value appeared in a solve */
+#define RBFFD_ERR_CUDA (-5)             /* a CUDA runtime call failed */
+#define RBFFD_ERR_OOM (-6)              /* workspace allocation failed */
+
+/* operator selection bits for rbffd_build_weights (Section 2.1, Eq. Lf) */
+#define RBFFD_OP_INTERP 1u /* L = identity: interpolation to the alpha-node  */
+#define RBFFD_OP_DX 2u     /* L = d/dx                                        */
+#define RBFFD_OP_DY 4u     /* L = d/dy                                        */
+#define RBFFD_OP_LAP 8u    /* L = d2/dx2 + d2/dy2                             */
+
+/* element types */
+#define RBFFD_F64 0
+#define RBFFD_F32 1
+
+/* precision policy of rbffd_step */
+#define RBFFD_PREC_FP64 0  /* everything in FP64 */
+#define RBFFD_PREC_MIXED 1 /* FP32 SpMVs and inner Krylov, FP64 iterative refinement */
+
+typedef struct rbffd_ctx rbffd_ctx;
+
+/* Stencil parameters (n, m, q) of Section 4; the paper selects (28, 7, 3). */
+typedef struct rbffd_params {
+  int32_t n; /* stencil size: nearest beta-nodes per alpha-node, 1..64        */
+  int32_t m; /* PHS exponent of phi(r) = r^m; odd, 3..13                     */
+  int32_t q; /* degree of the polynomial augmentation, -1 (none) .. 5;
+                the system size (n + (q+1)(q+2)/2) must not exceed 96 and n
+                must be at least the number of monomials                    */
+} rbffd_params;
+
+/* Create a context.  p may be NULL for (28, 7, 3). */
+int rbffd_create(rbffd_ctx** ctx, const rbffd_params* p);
+/* Release a context and its workspace (after the caller's streams are idle). */
+int rbffd_destroy(rbffd_ctx* ctx);
+/* Message of the last failing call on ctx; never NULL. */
+const char* rbffd_last_error(const rbffd_ctx* ctx);
+/* Library version as major*10000 + minor*100 + patch. */
+int rbffd_version(void);
+
+/*
+ * rbffd_build_weights - stencils and PHS+poly weights of D_L^(alpha,beta).
+ *
+ * Section 2.2: row i of D_L^(alpha,beta) uses the n nearest beta-nodes of
+ * alpha-node i; Section 2.1, Eq. rbf_poly_compact: the weights solve
+ *   [A P; P^T 0] [w; c] = [L phi; L P]
+ * with A_ij = |x_i - x_j|^m and P the monomials up to degree q.  Each system
+ * is shifted to the alpha-node and scaled by the largest stencil radius before
+ * the solve (LU with partial pivoting, FP64); the weights are unscaled after.
+ *
+ * ax, ay     alpha-node coordinates, double[n_alpha]
+ * bx, by     beta-node coordinates, double[n_beta]
+ * op_mask    OR of RBFFD_OP_* (at least one)
+ * idx        out: int32[n * ld], nearest first, ties by lower index;
+ *            distances are compared as dx*dx + dy*dy, each operation rounded
+ * w          out: double[nops * n * ld]; the operators are stored in bit
+ *            order INTERP, DX, DY, LAP, skipping those not requested
+ * ld         leading dimension, >= n_alpha, a multiple of 32
+ * bad_node   HOST out (may be NULL): lowest alpha index whose system was
+ *            singular, or -1
+ * Errors: INVALID_ARG (n > n_beta, sizes), SINGULAR_STENCIL (weights of
+ * singular rows are set to 0; all other rows are valid), CUDA, OOM.
+ * Synchronises `stream`.
+ */
+int rbffd_build_weights(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,
+                        const double* bx, const double* by, int64_t n_beta, uint32_t op_mask,
+                        int32_t* idx, double* w, int64_t ld, int64_t* bad_node,
+                        cudaStream_t stream);
+
+/* One ELL operator (see the conventions above). */
+typedef struct rbffd_ell {
+  const int32_t* idx; /* int32[n * ld]                                       */
+  const void* w;      /* double or float [n * ld], per w_dtype               */
+  int64_t n_rows;     /* alpha-nodes                                          */
+  int64_t n_cols;     /* beta-nodes (every idx entry is < n_cols)            */
+  int64_t ld;         /* leading dimension, >= n_rows, a multiple of 32      */
+  int32_t n;          /* stencil size                                         */
+  int32_t w_dtype;    /* RBFFD_F64 or RBFFD_F32                               */
+} rbffd_ell;
+
+/*
+ * rbffd_apply_op - y = alpha * D x + beta * y (Section 2.2: D f(x^beta)
+ * approximates L f(x^alpha)).  x has n_cols entries and y n_rows, both of
+ * xy_dtype (RBFFD_F64 or RBFFD_F32).  With beta == 0, y is not read.
+ * Accumulation is in FP64 for FP64 weights and in FP32 for FP32 weights.
+ * Asynchronous.  Errors: INVALID_ARG, CUDA.
+ */
+int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
+                   double beta, int32_t xy_dtype, cudaStream_t stream);
+
+/*
+ * Staggered flow problem (Section 3).  Every operator is FP64 ELL with the
+ * stencil size of the context; idx arrays index the beta set named second:
+ *   vv_*: V-grid -> V-grid (N rows, ld_v), pv_*: V-values -> P-nodes
+ *   (D^(P,V), M rows, ld_p), pp_*: P -> P (M rows, ld_p), vp_*: P-values ->
+ *   V-nodes (D^(V,P), N rows, ld_v).
+ * Boundary description:
+ *   v_bc[i] != 0   V-node i lies on a wall; u, v there are Dirichlet data
+ *   v_nx, v_ny     outward wall normal at wall V-nodes (unit length)
+ *   p_bc[i] != 0   P-node i is a boundary node: its pressure row is the
+ *                  homogeneous Neumann row p_nx D_x + p_ny D_y
+ *   p_nx, p_ny     outward normal at boundary P-nodes
+ * Re, dt          Reynolds number and time step; a = dt / (2 Re)
+ * precision       RBFFD_PREC_FP64 or RBFFD_PREC_MIXED
+ * tol             relative residual of both implicit solves (scaled systems)
+ * inner_tol       MIXED only: relative tolerance of each FP32 inner solve
+ * max_iter        cap on Krylov iterations per solve (inner iterations summed)
+ * km_mode         boundary value of the intermediate velocity (Kim & Moin):
+ *                 0 = wall data only, 1 = wall data + dt * tangential part of
+ *                 D^(V,P) p~_j (default), 2 = + dt * the full D^(V,P) p~_j
+ * overwrite_bc    1 = set wall V-nodes to the wall data after the correction
+ */
+typedef struct rbffd_flow {
+  int64_t N, M, ld_v, ld_p;
+  const int32_t* vv_idx;
+  const double *vv_dx, *vv_dy, *vv_lap;
+  const int32_t* pv_idx;
+  const double *pv_dx, *pv_dy;
+  const int32_t* pp_idx;
+  const double *pp_dx, *pp_dy, *pp_lap;
+  const int32_t* vp_idx;
+  const double *vp_dx, *vp_dy;
+  const uint8_t* v_bc;
+  const double *v_nx, *v_ny;
+  const uint8_t* p_bc;
+  const double *p_nx, *p_ny;
+  double Re, dt;
+  int32_t precision;
+  double tol, inner_tol;
+  int32_t max_iter;
+  int32_t km_mode;
+  int32_t overwrite_bc;
+} rbffd_flow;
+
+/* Solver state at step j (all FP64 device arrays owned by the caller). */
+typedef struct rbffd_state {
+  double *u, *v;             /* velocity at V-nodes, [N]                     */
+  double *cu_prev, *cv_prev; /* convective terms C_{j-1}(u), C_{j-1}(v), [N] */
+  double *pt;                /* pressure correction p~_j (mean zero), [M]    */
+  double *p;                 /* pressure p_j, [M]                            */
+  int64_t j;                 /* step counter; j == 0 uses C_{-1} = C_0       */
+} rbffd_state;
+
+/* Per-call statistics (host struct, filled by rbffd_step). */
+typedef struct rbffd_stats {
+  int64_t steps;            /* steps taken                                    */
+  int64_t helm_iters;       /* Krylov iterations of the viscous solves        */
+  int64_t poisson_iters;    /* Krylov iterations of the pressure solves      */
+  int64_t refinements;      /* FP64 refinement sweeps (MIXED)                 */
+  double helm_relres;       /* last relative residual, viscous solve         */
+  double poisson_relres;    /* last relative residual, pressure solve        */
+} rbffd_stats;
+
+/*
+ * rbffd_step - advance `n_steps` fractional steps (Section 3):
+ *  1. C_j(q) = -[u o D^(V,V)_x q + v o D^(V,V)_y q]; u* = u_j + dt (3/2 C_j - 1/2 C_{j-1})
+ *  2. (I - a D^(V,V)_Lap) u** = (I + a D^(V,V)_Lap) u* (Eq. u_ss), wall rows = identity
+ *     with the Kim & Moin value (km_mode); likewise v**
+ *  3. F = D^(P,V)_x u** + D^(P,V)_y v** (Eq. divergence); D^(P,P)_Lap p~ = F/dt
+ *     (Eq. pressure_Poisson) with Neumann boundary rows; p~ has zero mean
+ *  4. p = p~ - a D^(P,P)_Lap p~;  u_{j+1} = u** - dt D^(V,P)_x p~, v likewise
+ *     (Eq. velocity_next_timestep); wall nodes set to the wall data
+ * gu, gv: device double[N], wall data g_{j+1} (used at wall V-nodes only),
+ * held fixed over the n_steps of one call.  state is updated in place;
+ * state->j advances by n_steps.  stats (HOST, may be NULL) is filled.
+ * Errors: INVALID_ARG, NOT_CONVERGED (state holds the last iterate), NONFINITE,
+ * CUDA, OOM.  Synchronises `stream`.
+ */
+int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const double* gu,
+               const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFFD_H */

@@ -1,0 +1,162 @@
+// C ABI: context lifetime, error reporting, argument validation.
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace rbffd {
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+int set_error(rbffd_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int check_cuda(rbffd_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return RBFFD_OK;
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(ctx, RBFFD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(ctx, RBFFD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ctx_scratch(rbffd_ctx* ctx, size_t bytes, void** out) {
+  if (bytes > ctx->scratch_bytes) {
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    size_t want = bytes + bytes / 4;
+    int rc = check_cuda(ctx, cudaMalloc(&ctx->scratch, want), "scratch allocation");
+    if (rc) return rc;
+    ctx->scratch_bytes = want;
+  }
+  *out = ctx->scratch;
+  return RBFFD_OK;
+}
+
+static int n_monomials(int q) { return q < 0 ? 0 : (q + 1) * (q + 2) / 2; }
+
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" {
+
+int rbffd_version(void) { return 100; }
+
+int rbffd_create(rbffd_ctx** ctx, const rbffd_params* p) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  *ctx = nullptr;
+  rbffd_params prm{28, 7, 3};
+  if (p) prm = *p;
+  if (prm.n < 1 || prm.n > kMaxStencil || prm.m < 3 || prm.m > 13 || (prm.m % 2) == 0 ||
+      prm.q < -1 || prm.q > 5 || prm.n < n_monomials(prm.q) ||
+      prm.n + n_monomials(prm.q) > kMaxSystem)
+    return RBFFD_ERR_INVALID_ARG;
+  rbffd_ctx* c = new (std::nothrow) rbffd_ctx();
+  if (!c) return RBFFD_ERR_OOM;
+  c->prm = prm;
+  if (cudaMallocHost(&c->host_pinned, kHostPinnedBytes) != cudaSuccess) {
+    delete c;
+    return RBFFD_ERR_CUDA;
+  }
+  *ctx = c;
+  return RBFFD_OK;
+}
+
+int rbffd_destroy(rbffd_ctx* ctx) {
+  if (!ctx) return RBFFD_OK;
+  if (ctx->plan) step_plan_free(ctx->plan);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  delete ctx;
+  return RBFFD_OK;
+}
+
+const char* rbffd_last_error(const rbffd_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+int rbffd_build_weights(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,
+                        const double* bx, const double* by, int64_t n_beta, uint32_t op_mask,
+                        int32_t* idx, double* w, int64_t ld, int64_t* bad_node,
+                        cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (bad_node) *bad_node = -1;
+  const int k = ctx->prm.n;
+  if (n_alpha < 0 || n_beta < 0)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "negative node count");
+  if ((op_mask & 15u) == 0 || (op_mask & ~15u))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "op_mask must be a nonzero OR of RBFFD_OP_*");
+  if (n_alpha == 0) return RBFFD_OK;
+  if (n_beta < k)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "stencil size %d exceeds %lld beta-nodes", k,
+                     (long long)n_beta);
+  if (n_alpha > INT32_MAX || n_beta > INT32_MAX)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "node counts must fit int32");
+  if (!ax || !ay || !bx || !by || !idx || !w)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null array pointer");
+  if (ld < n_alpha || ld % 32)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "ld must be >= n_alpha and a multiple of 32");
+  int rc = knn_build(ctx, ax, ay, n_alpha, bx, by, n_beta, k, idx, ld, stream);
+  if (rc) return rc;
+  return weights_build(ctx, ax, ay, n_alpha, bx, by, idx, ld, op_mask, w, bad_node, stream);
+}
+
+int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
+                   double beta, int32_t xy_dtype, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!D || !D->idx || !D->w || !x || !y)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  if (D->n_rows < 0 || D->n_cols < 1 || D->n < 1 || D->n > kMaxStencil || D->ld < D->n_rows ||
+      D->ld % 32)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad operator shape");
+  if ((D->w_dtype != RBFFD_F64 && D->w_dtype != RBFFD_F32) ||
+      (xy_dtype != RBFFD_F64 && xy_dtype != RBFFD_F32))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad dtype");
+  if (D->n_rows == 0) return RBFFD_OK;
+  return spmv_apply(ctx, D, x, y, alpha, beta, xy_dtype, stream);
+}
+
+int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const double* gu,
+               const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!flow || !state || !gu || !gv)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  const rbffd_flow& f = *flow;
+  if (n_steps < 0) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "negative n_steps");
+  if (f.N < ctx->prm.n || f.M < ctx->prm.n || f.ld_v < f.N || f.ld_p < f.M || f.ld_v % 32 ||
+      f.ld_p % 32 || f.N > INT32_MAX || f.M > INT32_MAX)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad node counts or leading dimensions");
+  if (!f.vv_idx || !f.vv_dx || !f.vv_dy || !f.vv_lap || !f.pv_idx || !f.pv_dx || !f.pv_dy ||
+      !f.pp_idx || !f.pp_dx || !f.pp_dy || !f.pp_lap || !f.vp_idx || !f.vp_dx || !f.vp_dy ||
+      !f.v_bc || !f.v_nx || !f.v_ny || !f.p_bc || !f.p_nx || !f.p_ny)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null operator or boundary array");
+  if (!state->u || !state->v || !state->cu_prev || !state->cv_prev || !state->pt || !state->p)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
+  if (!(f.Re > 0) || !(f.dt > 0) || !(f.tol > 0) || f.max_iter < 1 ||
+      (f.precision != RBFFD_PREC_FP64 && f.precision != RBFFD_PREC_MIXED) || f.km_mode < 0 ||
+      f.km_mode > 2 || (f.precision == RBFFD_PREC_MIXED && !(f.inner_tol > 0 && f.inner_tol < 1)))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad Re, dt, tolerances or modes");
+  if (n_steps == 0) return RBFFD_OK;
+  return step_run(ctx, flow, state, gu, gv, n_steps, stats, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// Shared device helpers and the context definition of the CUDA path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "rbffd.h"
+
+namespace rbffd {
+
+constexpr int kWarp = 32;
+constexpr int kMaxStencil = 64;  // largest n accepted by the ABI
+constexpr int kMaxSystem = 96;   // largest n + (q+1)(q+2)/2
+constexpr size_t kHostPinnedBytes = 65536;  // per-context pinned status buffer
+
+// Number of SMs on the current device; grid sizes are multiples of it.
+int sm_count();
+
+// -------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV values per thread, fixed reduction tree (deterministic
+// for a fixed block size).  Result valid in thread 0.  `sh` holds at least
+// NV * (blockDim.x / 32) doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[j * nw + wid] = v[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = lane < nw ? sh[j * nw + lane] : 0.0;
+      v[j] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide deterministic reduction via "last block finishes": every block
+// writes its partial sums, the last block to arrive adds all partials in
+// block order with a fixed tree and runs `fin` on the totals in thread 0.
+// No block waits on another; the counter is reset by the last block.
+struct GridReduce {
+  double* partials;       // [gridDim.x * NV]
+  unsigned int* counter;  // one word, zero between launches
+};
+
+template <int NV, typename Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], GridReduce gr, double* sh, Fin fin) {
+  block_sum<NV>(v, sh);
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) gr.partials[blockIdx.x * NV + j] = v[j];
+    __threadfence();
+    unsigned int t = atomicAdd(gr.counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] += ((volatile double*)gr.partials)[b * NV + j];
+  }
+  block_sum<NV>(acc, sh);
+  if (threadIdx.x == 0) {
+    fin(acc);
+    *gr.counter = 0u;
+  }
+}
+
+}  // namespace rbffd
+
+// ------------------------------------------------------------------ context
+namespace rbffd {
+struct StepPlan;
+}
+
+struct rbffd_ctx {
+  rbffd_params prm;
+  std::string err;
+  // scratch owned by the context (grown on demand)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  void* host_pinned = nullptr;  // small pinned buffer for status words
+  rbffd::StepPlan* plan = nullptr;
+};
+
+namespace rbffd {
+
+int set_error(rbffd_ctx* ctx, int code, const char* fmt, ...);
+int check_cuda(rbffd_ctx* ctx, cudaError_t e, const char* what);
+// grow-only device scratch of the context
+int ctx_scratch(rbffd_ctx* ctx, size_t bytes, void** out);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// entry points implemented per translation unit
+int knn_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
+              const double* by, int64_t nb, int k, int32_t* idx, int64_t ld, cudaStream_t st);
+int weights_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
+                  const double* by, const int32_t* idx, int64_t ld, uint32_t op_mask, double* w,
+                  int64_t* bad_node, cudaStream_t st);
+int spmv_apply(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
+               double beta, int32_t xy_dtype, cudaStream_t st);
+int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
+             const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st);
+void step_plan_free(struct StepPlan* p);
+
+}  // namespace rbffd

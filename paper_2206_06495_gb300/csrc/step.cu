@@ -1,0 +1,1121 @@
+// The fractional step of Section 3 on the GPU: explicit stages as fused ELL
+// kernels, implicit stages as BiCGSTAB solves built on the same ELL streams.
+//
+// Layout: every operator is slot-major ELL (idx[s*ld+i], w[s*ld+i]); vectors
+// are plain FP64 arrays, and in MIXED precision every vector that an FP32
+// operator gathers also has a split FP32 copy (hi, lo) with hi + lo == x to
+// about 2^-48 relative.  FP32 derivative operators gather differences
+// (x_j - x_ref) = (hi_j - hi_ref) + (lo_j - lo_ref) against the stencil's
+// nearest node, so the cancellation of a derivative stencil happens before
+// the rounding to FP32 rather than after it.
+//
+// Implicit solves (rows scaled as below, relative residual on the scaled
+// system):
+//   viscous:  H x = b, H = I - a_i D^(V,V)_Lap, a_i = dt/(2 Re) inside and 0
+//             on wall rows, which are identity rows (Eq. u_ss);
+//   pressure: S (L - e 1^T) x = S b, L = D^(P,P)_Lap inside and the Neumann
+//             row n_x D_x + n_y D_y on boundary rows, e = indicator of interior
+//             rows, S = diag(1/L_ii) inside and diag(1/sum_j |L_ij|) on
+//             boundary rows.  L annihilates constants, so the rank-one term
+//             fixes the constant mode: x = p~ + c 1 for the mean-zero solution
+//             p~ of the bordered system [L e; 1^T 0] (the multiplier c absorbs
+//             the incompatibility of the non-symmetric L in the interior rows),
+//             and p~ = x - mean(x).
+// FP64 precision: BiCGSTAB in FP64.  MIXED: FP64 iterative refinement whose
+// corrections come from FP32 BiCGSTAB on FP32 copies of the scaled operators.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rbffd {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNV = 4;  // values reduced per kernel
+
+struct KScal {
+  double rho[2], alpha[2], omega[2], beta[2];
+  double rr[2], bb[2];
+  double sum_p, sum_s, sum_x;
+  double tol2;
+  int active[2];
+  int half[2];
+  int iters;
+  int maxit;
+  int done;
+  int status;  // 0 ok, 1 breakdown, 2 non-finite
+};
+
+__device__ __forceinline__ float2 split2(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
+template <typename TW, typename TV>
+struct KOp {
+  const int32_t* idx;
+  const TW* w;
+  int64_t ld;
+  int64_t n;
+  int k;
+  int diag1;     // add x_i (identity part of H)
+  const TV* es;  // rank-one column, or null
+};
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  using t = double;
+};
+template <>
+struct Acc<float> {
+  using t = float;
+};
+
+// sum_s w[s][i] * x[idx[s][i]] for one or two vectors sharing the stencil
+template <int K, int NRHS, typename TW, typename TV>
+__device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, const TV* const* x,
+                                            typename Acc<TW>::t* acc) {
+  using A = typename Acc<TW>::t;
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = 0;
+  const int k = K > 0 ? K : op.k;
+#pragma unroll(K > 0 ? K : 1)
+  for (int s = 0; s < k; ++s) {
+    const int j = op.idx[s * op.ld + i];
+    const A w = (A)op.w[s * op.ld + i];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
+  }
+}
+
+template <typename TV, int NRHS>
+struct Vecs {
+  TV* v[NRHS];
+};
+
+// ----------------------------------------------------------- Krylov kernels
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_sum(const TV* __restrict__ x, int64_t n,
+                                                  GridReduce gr, double* out) {
+  __shared__ double sh[kNV * kThreads / 32];
+  float part = 0.f;
+  double partd = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    if (sizeof(TV) == 8)
+      partd += (double)x[i];
+    else
+      part += (float)x[i];
+  }
+  double v[kNV] = {partd + (double)part, 0, 0, 0};
+  grid_reduce<kNV>(v, gr, sh, [&](double* t) { *out = t[0]; });
+}
+
+template <int K, int NRHS, bool RANK1, typename TW, typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_init(KOp<TW, TV> op, Vecs<TV, NRHS> x, Vecs<TV, NRHS> b, Vecs<TV, NRHS> r,
+           Vecs<TV, NRHS> rh, Vecs<TV, NRHS> p, const double* sigma_x, KScal* sc, GridReduce gr,
+           double tol2, int maxit) {
+  using A = typename Acc<TW>::t;
+  __shared__ double sh[kNV * kThreads / 32];
+  A prr[2] = {0, 0}, pbb[2] = {0, 0}, psum = 0;
+  const A sig = RANK1 ? (A)*sigma_x : (A)0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    A acc[NRHS];
+    gather_rows<K, NRHS>(op, i, (const TV* const*)x.v, acc);
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      A ax = acc[q];
+      if (op.diag1) ax += (A)x.v[q][i];
+      if (RANK1) ax += (A)op.es[i] * sig;
+      const A bi = (A)b.v[q][i];
+      const A ri = bi - ax;
+      r.v[q][i] = (TV)ri;
+      rh.v[q][i] = (TV)ri;
+      p.v[q][i] = (TV)ri;
+      prr[q] += ri * ri;
+      pbb[q] += bi * bi;
+      if (RANK1) psum += ri;
+    }
+  }
+  double v[kNV] = {(double)prr[0], (double)pbb[0], NRHS > 1 ? (double)prr[1] : (double)psum,
+                   NRHS > 1 ? (double)pbb[1] : 0.0};
+  grid_reduce<kNV>(v, gr, sh, [&](double* t) {
+    sc->tol2 = tol2;
+    sc->maxit = maxit;
+    sc->iters = 0;
+    sc->status = 0;
+    int any = 0;
+    for (int q = 0; q < NRHS; ++q) {
+      const double rr = t[2 * q], bb = t[2 * q + 1];
+      sc->rr[q] = rr;
+      sc->bb[q] = bb;
+      sc->rho[q] = rr;
+      sc->alpha[q] = 1.0;
+      sc->omega[q] = 1.0;
+      sc->half[q] = 0;
+      if (!isfinite(rr)) sc->status = 2;
+      sc->active[q] = (isfinite(rr) && rr > tol2 * bb) ? 1 : 0;
+      any |= sc->active[q];
+    }
+    for (int q = NRHS; q < 2; ++q) sc->active[q] = 0;
+    if (RANK1) sc->sum_p = t[2];
+    sc->done = (any && maxit > 0) ? 0 : 1;
+  });
+}
+
+// v = A p ; reduce (rh, v)
+template <int K, int NRHS, bool RANK1, typename TW, typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
+             GridReduce gr) {
+  using A = typename Acc<TW>::t;
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  const A sig = RANK1 ? (A)sc->sum_p : (A)0;
+  A pd[2] = {0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    A acc[NRHS];
+    gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      A y = acc[q];
+      if (op.diag1) y += (A)p.v[q][i];
+      if (RANK1) y += (A)op.es[i] * sig;
+      v.v[q][i] = (TV)y;
+      pd[q] += (A)rh.v[q][i] * y;
+    }
+  }
+  double vv[kNV] = {(double)pd[0], (double)pd[1], 0, 0};
+  grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
+    for (int q = 0; q < NRHS; ++q) {
+      if (!sc->active[q]) continue;
+      const double rv = t[q];
+      if (rv == 0.0 || !isfinite(rv)) {
+        sc->active[q] = 0;
+        sc->status = isfinite(rv) ? 1 : 2;
+        continue;
+      }
+      sc->alpha[q] = sc->rho[q] / rv;
+    }
+  });
+}
+
+// s = r - alpha v ; reduce (s, s) and sum(s)
+template <int NRHS, bool RANK1, typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_update_s(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> v, Vecs<TV, NRHS> s, KScal* sc,
+               GridReduce gr) {
+  using A = TV;
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  A al[2];
+  int act[2];
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) {
+    al[q] = (A)sc->alpha[q];
+    act[q] = sc->active[q];
+  }
+  A pss[2] = {0, 0}, psum = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      if (!act[q]) continue;
+      const A si = r.v[q][i] - al[q] * v.v[q][i];
+      s.v[q][i] = si;
+      pss[q] += si * si;
+      if (RANK1) psum += si;
+    }
+  }
+  double vv[kNV] = {(double)pss[0], (double)pss[1], (double)psum, 0};
+  grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
+    for (int q = 0; q < NRHS; ++q)
+      if (sc->active[q] && t[q] <= sc->tol2 * sc->bb[q]) sc->half[q] = 1;
+    if (RANK1) sc->sum_s = t[2];
+  });
+}
+
+// t = A s ; reduce (t, s), (t, t)
+template <int K, int NRHS, bool RANK1, typename TW, typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr) {
+  using A = typename Acc<TW>::t;
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  const A sig = RANK1 ? (A)sc->sum_s : (A)0;
+  A pts[2] = {0, 0}, ptt[2] = {0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    A acc[NRHS];
+    gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      A y = acc[q];
+      const A si = (A)s.v[q][i];
+      if (op.diag1) y += si;
+      if (RANK1) y += (A)op.es[i] * sig;
+      t.v[q][i] = (TV)y;
+      pts[q] += y * si;
+      ptt[q] += y * y;
+    }
+  }
+  double vv[kNV] = {(double)pts[0], (double)ptt[0], (double)pts[1], (double)ptt[1]};
+  grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+    for (int q = 0; q < NRHS; ++q) {
+      if (!sc->active[q] || sc->half[q]) continue;
+      const double ts = tt[2 * q], t2 = tt[2 * q + 1];
+      if (!(t2 > 0.0) || !isfinite(ts)) {
+        sc->omega[q] = 0.0;
+        sc->active[q] = 0;
+        sc->status = isfinite(t2) ? 1 : 2;
+        continue;
+      }
+      sc->omega[q] = ts / t2;
+    }
+  });
+}
+
+// x += alpha p + omega s ; r = s - omega t ; reduce (rh, r), (r, r)
+template <int NRHS, typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_update_xr(int64_t n, Vecs<TV, NRHS> x, Vecs<TV, NRHS> r, Vecs<TV, NRHS> rh,
+                Vecs<TV, NRHS> p, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr) {
+  using A = TV;
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  A al[2], om[2];
+  int act[2], hf[2];
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) {
+    al[q] = (A)sc->alpha[q];
+    om[q] = (A)sc->omega[q];
+    act[q] = sc->active[q];
+    hf[q] = sc->half[q];
+  }
+  A prh[2] = {0, 0}, prr[2] = {0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      if (!act[q]) continue;
+      const A si = s.v[q][i];
+      A ri;
+      if (hf[q]) {
+        x.v[q][i] += al[q] * p.v[q][i];
+        ri = si;
+      } else {
+        x.v[q][i] += al[q] * p.v[q][i] + om[q] * si;
+        ri = si - om[q] * t.v[q][i];
+      }
+      r.v[q][i] = ri;
+      prh[q] += rh.v[q][i] * ri;
+      prr[q] += ri * ri;
+    }
+  }
+  double vv[kNV] = {(double)prh[0], (double)prr[0], (double)prh[1], (double)prr[1]};
+  grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+    sc->iters += 1;
+    int any = 0;
+    for (int q = 0; q < NRHS; ++q) {
+      if (!sc->active[q]) continue;
+      const double rho_new = tt[2 * q], rr = tt[2 * q + 1];
+      sc->rr[q] = rr;
+      if (!isfinite(rr)) {
+        sc->status = 2;
+        sc->active[q] = 0;
+        continue;
+      }
+      if (sc->half[q] || rr <= sc->tol2 * sc->bb[q]) {
+        sc->active[q] = 0;
+        continue;
+      }
+      if (rho_new == 0.0 || sc->omega[q] == 0.0) {
+        sc->status = 1;
+        sc->active[q] = 0;
+        continue;
+      }
+      sc->beta[q] = (rho_new / sc->rho[q]) * (sc->alpha[q] / sc->omega[q]);
+      sc->rho[q] = rho_new;
+      any = 1;
+    }
+    if (!any || sc->iters >= sc->maxit) sc->done = 1;
+  });
+}
+
+// p = r + beta (p - omega v) ; reduce sum(p)
+template <int NRHS, bool RANK1, typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_update_p(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, KScal* sc,
+               GridReduce gr) {
+  using A = TV;
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  A be[2], om[2];
+  int act[2];
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) {
+    be[q] = (A)sc->beta[q];
+    om[q] = (A)sc->omega[q];
+    act[q] = sc->active[q];
+  }
+  A psum = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      if (!act[q]) continue;
+      const A pi = r.v[q][i] + be[q] * (p.v[q][i] - om[q] * v.v[q][i]);
+      p.v[q][i] = pi;
+      if (RANK1) psum += pi;
+    }
+  }
+  double vv[kNV] = {(double)psum, 0, 0, 0};
+  grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+    if (RANK1) sc->sum_p = tt[0];
+  });
+}
+
+// ------------------------------------------------- refinement helper kernels
+// r = b - A x in FP64 (scaled system); reduce (r, r), (b, b) per right side
+template <int K, int NRHS, bool RANK1>
+__global__ void __launch_bounds__(kThreads)
+    k_residual64(KOp<double, double> op, Vecs<double, NRHS> x, Vecs<double, NRHS> b,
+                 Vecs<double, NRHS> r, const double* sigma_x, double* out4, GridReduce gr) {
+  __shared__ double sh[kNV * kThreads / 32];
+  const double sig = RANK1 ? *sigma_x : 0.0;
+  double prr[2] = {0, 0}, pbb[2] = {0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double acc[NRHS];
+    gather_rows<K, NRHS>(op, i, (const double* const*)x.v, acc);
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      double ax = acc[q];
+      if (op.diag1) ax += x.v[q][i];
+      if (RANK1) ax += op.es[i] * sig;
+      const double bi = b.v[q][i], ri = bi - ax;
+      r.v[q][i] = ri;
+      prr[q] += ri * ri;
+      pbb[q] += bi * bi;
+    }
+  }
+  double vv[kNV] = {prr[0], pbb[0], prr[1], pbb[1]};
+  grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
+    for (int j = 0; j < kNV; ++j) out4[j] = t[j];
+  });
+}
+
+// r32 = r64 * inv_norm ; e32 = 0
+template <int NRHS>
+__global__ void k_to32(int64_t n, Vecs<double, NRHS> r, Vecs<float, NRHS> r32,
+                       Vecs<float, NRHS> e32, double inv0, double inv1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    r32.v[0][i] = (float)(r.v[0][i] * inv0);
+    e32.v[0][i] = 0.f;
+    if (NRHS > 1) {
+      r32.v[NRHS - 1][i] = (float)(r.v[NRHS - 1][i] * inv1);
+      e32.v[NRHS - 1][i] = 0.f;
+    }
+  }
+}
+
+// x64 += nrm * e32
+template <int NRHS>
+__global__ void k_addcorr(int64_t n, Vecs<double, NRHS> x, Vecs<float, NRHS> e32, double n0,
+                          double n1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x.v[0][i] += n0 * (double)e32.v[0][i];
+    if (NRHS > 1) x.v[NRHS - 1][i] += n1 * (double)e32.v[NRHS - 1][i];
+  }
+}
+
+__global__ void k_split(int64_t n, const double* __restrict__ x, float2* __restrict__ x2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x2[i] = split2(x[i]);
+}
+
+// ------------------------------------------------------- explicit stages
+// sum_s w[s][i] * f(x[idx[s][i]]) for FP64 (plain) or FP32 (split differences)
+template <int K, bool MIX, int NV>
+struct Gather;
+
+template <int K, int NV>
+struct Gather<K, false, NV> {
+  // NV operators (weights w[o]) applied to one vector x
+  __device__ __forceinline__ static void run(const int32_t* idx, const void* const* w, int64_t ld,
+                                             int k_rt, int64_t i, const double* x,
+                                             const float2*, double* out) {
+    const int k = K > 0 ? K : k_rt;
+#pragma unroll
+    for (int o = 0; o < NV; ++o) out[o] = 0.0;
+#pragma unroll(K > 0 ? K : 1)
+    for (int s = 0; s < k; ++s) {
+      const double xj = x[idx[s * ld + i]];
+#pragma unroll
+      for (int o = 0; o < NV; ++o) out[o] += ((const double*)w[o])[s * ld + i] * xj;
+    }
+  }
+};
+
+template <int K, int NV>
+struct Gather<K, true, NV> {
+  __device__ __forceinline__ static void run(const int32_t* idx, const void* const* w, int64_t ld,
+                                             int k_rt, int64_t i, const double*, const float2* x2,
+                                             double* out) {
+    const int k = K > 0 ? K : k_rt;
+    float acc[NV];
+#pragma unroll
+    for (int o = 0; o < NV; ++o) acc[o] = 0.f;
+    const float2 ref = x2[idx[i]];
+#pragma unroll(K > 0 ? K : 1)
+    for (int s = 0; s < k; ++s) {
+      const float2 xj = x2[idx[s * ld + i]];
+      const float d = (xj.x - ref.x) + (xj.y - ref.y);
+#pragma unroll
+      for (int o = 0; o < NV; ++o) acc[o] += ((const float*)w[o])[s * ld + i] * d;
+    }
+#pragma unroll
+    for (int o = 0; o < NV; ++o) out[o] = (double)acc[o];
+  }
+};
+
+struct ConvArgs {
+  int64_t n, ld;
+  int k;
+  const int32_t* idx;
+  const void *wdx, *wdy;
+  const double *u, *v;
+  const float2 *u2, *v2;
+  double *cu_prev, *cv_prev, *us, *vs;
+  float2 *us2, *vs2;
+  double dt;
+  int first;
+};
+
+// Stage 1: C_j(q) = -[u o D_x q + v o D_y q]; u* = u_j + dt (3/2 C_j - 1/2 C_{j-1})
+template <int K, bool MIX>
+__global__ void __launch_bounds__(kThreads) k_convect(ConvArgs a) {
+  const void* w[2] = {a.wdx, a.wdy};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double du[2], dv[2];
+    Gather<K, MIX, 2>::run(a.idx, w, a.ld, a.k, i, a.u, a.u2, du);
+    Gather<K, MIX, 2>::run(a.idx, w, a.ld, a.k, i, a.v, a.v2, dv);
+    const double ui = a.u[i], vi = a.v[i];
+    const double cu = -(ui * du[0] + vi * du[1]);
+    const double cv = -(ui * dv[0] + vi * dv[1]);
+    const double cup = a.first ? cu : a.cu_prev[i];
+    const double cvp = a.first ? cv : a.cv_prev[i];
+    const double us = ui + a.dt * (1.5 * cu - 0.5 * cup);
+    const double vs = vi + a.dt * (1.5 * cv - 0.5 * cvp);
+    a.us[i] = us;
+    a.vs[i] = vs;
+    a.cu_prev[i] = cu;
+    a.cv_prev[i] = cv;
+    if (MIX) {
+      a.us2[i] = split2(us);
+      a.vs2[i] = split2(vs);
+    }
+  }
+}
+
+struct HelmRhsArgs {
+  int64_t n, ld_v;
+  int k;
+  const int32_t* vv_idx;
+  const void* lap;
+  const double *us, *vs;
+  const float2 *us2, *vs2;
+  const int32_t* vp_idx;
+  const void *vp_dx, *vp_dy;
+  const double* pt;
+  const float2* pt2;
+  const uint8_t* v_bc;
+  const double *v_nx, *v_ny, *gu, *gv;
+  double a, dt;
+  int km;
+  double *ru, *rv, *xu, *xv;
+};
+
+// Stage 2 right side: (I + a D_Lap) u* inside; wall rows: Kim & Moin value
+template <int K, bool MIX>
+__global__ void __launch_bounds__(kThreads) k_helm_rhs(HelmRhsArgs a) {
+  const void* wl[1] = {a.lap};
+  const void* wg[2] = {a.vp_dx, a.vp_dy};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double bu, bv;
+    if (!a.v_bc[i]) {
+      double lu, lv;
+      Gather<K, MIX, 1>::run(a.vv_idx, wl, a.ld_v, a.k, i, a.us, a.us2, &lu);
+      Gather<K, MIX, 1>::run(a.vv_idx, wl, a.ld_v, a.k, i, a.vs, a.vs2, &lv);
+      bu = a.us[i] + a.a * lu;
+      bv = a.vs[i] + a.a * lv;
+    } else {
+      bu = a.gu[i];
+      bv = a.gv[i];
+      if (a.km) {
+        double g[2];
+        Gather<K, MIX, 2>::run(a.vp_idx, wg, a.ld_v, a.k, i, a.pt, a.pt2, g);
+        if (a.km == 1) {
+          const double tx = -a.v_ny[i], ty = a.v_nx[i];
+          const double gt = tx * g[0] + ty * g[1];
+          bu += a.dt * gt * tx;
+          bv += a.dt * gt * ty;
+        } else {
+          bu += a.dt * g[0];
+          bv += a.dt * g[1];
+        }
+      }
+    }
+    a.ru[i] = bu;
+    a.rv[i] = bv;
+    a.xu[i] = bu;
+    a.xv[i] = bv;
+  }
+}
+
+struct DivArgs {
+  int64_t n, ld_p;
+  int k;
+  const int32_t* idx;
+  const void *wdx, *wdy;
+  const double *uss, *vss;
+  const float2 *uss2, *vss2;
+  const uint8_t* p_bc;
+  const double* scale;
+  double inv_dt;
+  double* b;
+};
+
+// Stage 3a: F = D^(P,V)_x u** + D^(P,V)_y v**; scaled Poisson right side
+template <int K, bool MIX>
+__global__ void __launch_bounds__(kThreads) k_divergence(DivArgs a) {
+  const void* wx[1] = {a.wdx};
+  const void* wy[1] = {a.wdy};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double fx, fy;
+    Gather<K, MIX, 1>::run(a.idx, wx, a.ld_p, a.k, i, a.uss, a.uss2, &fx);
+    Gather<K, MIX, 1>::run(a.idx, wy, a.ld_p, a.k, i, a.vss, a.vss2, &fy);
+    a.b[i] = a.p_bc[i] ? 0.0 : a.scale[i] * (fx + fy) * a.inv_dt;
+  }
+}
+
+struct PresArgs {
+  int64_t n, ld_p;
+  int k;
+  const int32_t* idx;
+  const void* lap;
+  const double* px;
+  const float2* px2;
+  const double* sum;
+  double a;
+  double *pt, *p;
+  float2* pt2;
+};
+
+// Stage 3c: p~ = x - mean(x); p = p~ - a D^(P,P)_Lap p~
+template <int K, bool MIX>
+__global__ void __launch_bounds__(kThreads) k_pressure(PresArgs a) {
+  const void* wl[1] = {a.lap};
+  const double mean = *a.sum / (double)a.n;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double l;
+    Gather<K, MIX, 1>::run(a.idx, wl, a.ld_p, a.k, i, a.px, a.px2, &l);
+    const double pt = a.px[i] - mean;
+    a.pt[i] = pt;
+    a.p[i] = pt - a.a * l;
+    if (MIX) a.pt2[i] = split2(pt);
+  }
+}
+
+struct CorrArgs {
+  int64_t n, ld_v;
+  int k;
+  const int32_t* idx;
+  const void *wdx, *wdy;
+  const double* pt;
+  const float2* pt2;
+  const double *uss, *vss;
+  const uint8_t* v_bc;
+  const double *gu, *gv;
+  double dt;
+  int overwrite;
+  double *u, *v;
+  float2 *u2, *v2;
+};
+
+// Stage 3d: u_{j+1} = u** - dt D^(V,P)_x p~ (Eq. velocity_next_timestep)
+template <int K, bool MIX>
+__global__ void __launch_bounds__(kThreads) k_correct(CorrArgs a) {
+  const void* w[2] = {a.wdx, a.wdy};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double g[2];
+    Gather<K, MIX, 2>::run(a.idx, w, a.ld_v, a.k, i, a.pt, a.pt2, g);
+    double un = a.uss[i] - a.dt * g[0];
+    double vn = a.vss[i] - a.dt * g[1];
+    if (a.overwrite && a.v_bc[i]) {
+      un = a.gu[i];
+      vn = a.gv[i];
+    }
+    a.u[i] = un;
+    a.v[i] = vn;
+    if (MIX) {
+      a.u2[i] = split2(un);
+      a.v2[i] = split2(vn);
+    }
+  }
+}
+
+// --------------------------------------------------------------- set-up
+// Scaled pressure operator: Lw = S L, es = -S e (see the file comment)
+__global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __restrict__ idx,
+                                const double* __restrict__ lap, const double* __restrict__ dx,
+                                const double* __restrict__ dy, const uint8_t* __restrict__ p_bc,
+                                const double* __restrict__ nx, const double* __restrict__ ny,
+                                double* __restrict__ Lw, double* __restrict__ es,
+                                double* __restrict__ scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool bnd = p_bc[i] != 0;
+    double diag = 0.0, sabs = 0.0;
+    for (int s = 0; s < k; ++s) {
+      const double w = bnd ? nx[i] * dx[s * ld + i] + ny[i] * dy[s * ld + i] : lap[s * ld + i];
+      sabs += fabs(w);
+      if (idx[s * ld + i] == (int32_t)i) diag += w;
+    }
+    double sc;
+    if (bnd || diag == 0.0)
+      sc = sabs > 0.0 ? 1.0 / sabs : 1.0;
+    else
+      sc = 1.0 / diag;
+    for (int s = 0; s < k; ++s) {
+      const double w = bnd ? nx[i] * dx[s * ld + i] + ny[i] * dy[s * ld + i] : lap[s * ld + i];
+      Lw[s * ld + i] = sc * w;
+    }
+    es[i] = bnd ? 0.0 : -sc;
+    scale[i] = sc;
+  }
+}
+
+// Viscous operator without its identity part: Hw = -a_i D_Lap
+__global__ void k_build_helm(int64_t N, int64_t ld, int k, const double* __restrict__ lap,
+                             const uint8_t* __restrict__ v_bc, double a, double* __restrict__ Hw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ai = v_bc[i] ? 0.0 : a;
+    for (int s = 0; s < k; ++s) Hw[s * ld + i] = -ai * lap[s * ld + i];
+  }
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+struct StepPlan {
+  rbffd_flow key;
+  int k = 0;
+  int64_t N = 0, M = 0;
+  int grid = 0;
+  bool mix = false;
+  std::vector<void*> allocs;
+  // derived operators
+  double *Lw = nullptr, *es = nullptr, *scale = nullptr, *Hw = nullptr;
+  float *Lw32 = nullptr, *es32 = nullptr, *Hw32 = nullptr;
+  float *vv_dx32 = nullptr, *vv_dy32 = nullptr, *vv_lap32 = nullptr, *pv_dx32 = nullptr,
+        *pv_dy32 = nullptr, *pp_lap32 = nullptr, *vp_dx32 = nullptr, *vp_dy32 = nullptr;
+  // stage vectors
+  double *us = nullptr, *vs = nullptr, *ru = nullptr, *rv = nullptr, *uss = nullptr,
+         *vss = nullptr, *pb = nullptr, *px = nullptr;
+  float2 *u2 = nullptr, *v2 = nullptr, *us2 = nullptr, *vs2 = nullptr, *uss2 = nullptr,
+         *vss2 = nullptr, *pt2 = nullptr, *px2 = nullptr;
+  // Krylov work (6 vectors x 2 right sides) in FP64 and FP32
+  double* kw64[6][2] = {};
+  float* kw32[6][2] = {};
+  float *e32[2] = {}, *r32[2] = {};
+  double* r64[2] = {};
+  KScal* sc = nullptr;
+  double* dscal = nullptr;  // [0]: sum, [1..4]: residual norms
+  GridReduce gr{};
+};
+
+void step_plan_free(StepPlan* p) {
+  if (!p) return;
+  for (void* a : p->allocs) cudaFree(a);
+  delete p;
+}
+
+namespace {
+
+template <typename T>
+int palloc(rbffd_ctx* ctx, StepPlan* p, T** out, size_t count) {
+  void* ptr = nullptr;
+  int rc = check_cuda(ctx, cudaMalloc(&ptr, sizeof(T) * (count > 0 ? count : 1)), "plan alloc");
+  if (rc) return rc;
+  p->allocs.push_back(ptr);
+  *out = (T*)ptr;
+  return RBFFD_OK;
+}
+
+int to32(rbffd_ctx* ctx, StepPlan* p, const double* src, int64_t n, float** dst,
+         cudaStream_t st) {
+  int rc = palloc(ctx, p, dst, n);
+  if (rc) return rc;
+  k_to_f32<<<p->grid, kThreads, 0, st>>>(n, src, *dst);
+  return check_cuda(ctx, cudaGetLastError(), "to_f32");
+}
+
+int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t st) {
+  StepPlan* p = new StepPlan();
+  p->key = f;
+  p->k = ctx->prm.n;
+  p->N = f.N;
+  p->M = f.M;
+  p->mix = f.precision == RBFFD_PREC_MIXED;
+  p->grid = sm_count() * 4;
+  const int64_t nv = f.ld_v * p->k, np = f.ld_p * p->k;
+  const int64_t nmax = f.N > f.M ? f.N : f.M;
+  int rc = 0;
+#define TRY(x)                   \
+  do {                           \
+    rc = (x);                    \
+    if (rc) {                    \
+      step_plan_free(p);         \
+      return rc;                 \
+    }                            \
+  } while (0)
+  TRY(palloc(ctx, p, &p->Lw, np));
+  TRY(palloc(ctx, p, &p->es, f.M));
+  TRY(palloc(ctx, p, &p->scale, f.M));
+  TRY(palloc(ctx, p, &p->Hw, nv));
+  TRY(palloc(ctx, p, &p->us, f.N));
+  TRY(palloc(ctx, p, &p->vs, f.N));
+  TRY(palloc(ctx, p, &p->ru, f.N));
+  TRY(palloc(ctx, p, &p->rv, f.N));
+  TRY(palloc(ctx, p, &p->uss, f.N));
+  TRY(palloc(ctx, p, &p->vss, f.N));
+  TRY(palloc(ctx, p, &p->pb, f.M));
+  TRY(palloc(ctx, p, &p->px, f.M));
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw64[a][b], nmax));
+  TRY(palloc(ctx, p, &p->sc, 1));
+  TRY(palloc(ctx, p, &p->dscal, 8));
+  TRY(palloc(ctx, p, &p->gr.partials, (size_t)p->grid * kNV));
+  TRY(palloc(ctx, p, &p->gr.counter, 1));
+  TRY(check_cuda(ctx, cudaMemsetAsync(p->gr.counter, 0, sizeof(unsigned int), st), "memset"));
+  const double a = f.dt / (2.0 * f.Re);
+  k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.pp_dx,
+                                                 f.pp_dy, f.p_bc, f.p_nx, f.p_ny, p->Lw, p->es,
+                                                 p->scale);
+  k_build_helm<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bc, a, p->Hw);
+  TRY(check_cuda(ctx, cudaGetLastError(), "plan kernels"));
+  if (p->mix) {
+    TRY(to32(ctx, p, p->Lw, np, &p->Lw32, st));
+    TRY(to32(ctx, p, p->es, f.M, &p->es32, st));
+    TRY(to32(ctx, p, p->Hw, nv, &p->Hw32, st));
+    TRY(to32(ctx, p, f.vv_dx, nv, &p->vv_dx32, st));
+    TRY(to32(ctx, p, f.vv_dy, nv, &p->vv_dy32, st));
+    TRY(to32(ctx, p, f.vv_lap, nv, &p->vv_lap32, st));
+    TRY(to32(ctx, p, f.pv_dx, np, &p->pv_dx32, st));
+    TRY(to32(ctx, p, f.pv_dy, np, &p->pv_dy32, st));
+    TRY(to32(ctx, p, f.pp_lap, np, &p->pp_lap32, st));
+    TRY(to32(ctx, p, f.vp_dx, nv, &p->vp_dx32, st));
+    TRY(to32(ctx, p, f.vp_dy, nv, &p->vp_dy32, st));
+    TRY(palloc(ctx, p, &p->u2, f.N));
+    TRY(palloc(ctx, p, &p->v2, f.N));
+    TRY(palloc(ctx, p, &p->us2, f.N));
+    TRY(palloc(ctx, p, &p->vs2, f.N));
+    TRY(palloc(ctx, p, &p->uss2, f.N));
+    TRY(palloc(ctx, p, &p->vss2, f.N));
+    TRY(palloc(ctx, p, &p->pt2, f.M));
+    TRY(palloc(ctx, p, &p->px2, f.M));
+    for (int a2 = 0; a2 < 6; ++a2)
+      for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw32[a2][b], nmax));
+    for (int b = 0; b < 2; ++b) {
+      TRY(palloc(ctx, p, &p->e32[b], nmax));
+      TRY(palloc(ctx, p, &p->r32[b], nmax));
+      TRY(palloc(ctx, p, &p->r64[b], nmax));
+    }
+  }
+#undef TRY
+  *out = p;
+  return RBFFD_OK;
+}
+
+// ---------------------------------------------------------------- BiCGSTAB
+struct SolveResult {
+  int iters = 0;
+  double relres = 0.0;
+  int status = 0;  // 0 ok, 1 breakdown, 2 non-finite
+  bool converged = false;
+};
+
+template <int K, int NRHS, bool RANK1, typename TW, typename TV>
+int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
+             const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
+             cudaStream_t st) {
+  Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
+  for (int q = 0; q < NRHS; ++q) {
+    X.v[q] = x[q];
+    B.v[q] = (TV*)b[q];
+    R.v[q] = work[0][q];
+    RH.v[q] = work[1][q];
+    PP.v[q] = work[2][q];
+    V.v[q] = work[3][q];
+    S.v[q] = work[4][q];
+    T.v[q] = work[5][q];
+  }
+  const int G = P->grid;
+  double* sigx = P->dscal;
+  if (RANK1) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx);
+  k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
+                                                  tol * tol, maxit);
+  int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
+  if (rc) return rc;
+  KScal* h = (KScal*)ctx->host_pinned;
+  int issued = 0, chunk = 4;
+  for (;;) {
+    rc = check_cuda(ctx, cudaMemcpyAsync(h, P->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st),
+                    "scalar copy");
+    if (rc) return rc;
+    rc = check_cuda(ctx, cudaStreamSynchronize(st), "bicgstab sync");
+    if (rc) return rc;
+    if (h->done || issued >= maxit) break;
+    const int n = std::min(chunk, maxit - issued);
+    for (int it = 0; it < n; ++it) {
+      k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr);
+      k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr);
+      k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr);
+      k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
+      k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr);
+    }
+    rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
+    if (rc) return rc;
+    issued += n;
+    chunk = std::min(chunk * 2, 64);
+  }
+  res->iters = h->iters;
+  res->status = h->status;
+  double worst = 0.0;
+  bool conv = true;
+  for (int q = 0; q < NRHS; ++q) {
+    const double rel = h->bb[q] > 0 ? sqrt(h->rr[q] / h->bb[q]) : sqrt(h->rr[q]);
+    worst = fmax(worst, rel);
+    if (!(h->rr[q] <= h->tol2 * h->bb[q])) conv = false;
+  }
+  res->relres = worst;
+  res->converged = conv;
+  return RBFFD_OK;
+}
+
+// FP64 iterative refinement around FP32 BiCGSTAB corrections
+template <int K, int NRHS, bool RANK1>
+int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
+           const KOp<float, float>& op32, double* const* x, const double* const* b, double tol,
+           double inner_tol, int maxit, SolveResult* res, int* sweeps, cudaStream_t st) {
+  Vecs<double, NRHS> X, B, R;
+  Vecs<float, NRHS> R32, E32;
+  for (int q = 0; q < NRHS; ++q) {
+    X.v[q] = x[q];
+    B.v[q] = (double*)b[q];
+    R.v[q] = P->r64[q];
+    R32.v[q] = P->r32[q];
+    E32.v[q] = P->e32[q];
+  }
+  const int G = P->grid;
+  int used = 0;
+  res->iters = 0;
+  res->status = 0;
+  *sweeps = 0;
+  double* h = (double*)ctx->host_pinned + 64;
+  for (int sweep = 0;; ++sweep) {
+    if (RANK1) k_sum<double><<<G, kThreads, 0, st>>>(x[0], op64.n, P->gr, P->dscal);
+    k_residual64<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op64, X, B, R, P->dscal, P->dscal + 1,
+                                                         P->gr);
+    int rc = check_cuda(ctx, cudaGetLastError(), "residual");
+    if (rc) return rc;
+    rc = check_cuda(ctx, cudaMemcpyAsync(h, P->dscal + 1, 4 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, st),
+                    "residual copy");
+    if (rc) return rc;
+    rc = check_cuda(ctx, cudaStreamSynchronize(st), "residual sync");
+    if (rc) return rc;
+    double worst = 0.0, nrm[2] = {0, 0};
+    bool conv = true;
+    for (int q = 0; q < NRHS; ++q) {
+      const double rr = h[2 * q], bb = h[2 * q + 1];
+      if (!std::isfinite(rr)) {
+        res->status = 2;
+        res->relres = NAN;
+        res->converged = false;
+        return RBFFD_OK;
+      }
+      nrm[q] = sqrt(rr);
+      const double rel = bb > 0 ? sqrt(rr / bb) : sqrt(rr);
+      worst = fmax(worst, rel);
+      if (!(rr <= tol * tol * bb)) conv = false;
+    }
+    res->relres = worst;
+    res->converged = conv;
+    if (conv || used >= maxit || sweep >= 40) return RBFFD_OK;
+    ++*sweeps;
+    const double i0 = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+    const double i1 = NRHS > 1 && nrm[NRHS - 1] > 0 ? 1.0 / nrm[NRHS - 1] : 0.0;
+    k_to32<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, R32, E32, i0, i1);
+    SolveResult inner;
+    rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
+                                                maxit - used, &inner, st);
+    if (rc) return rc;
+    used += inner.iters > 0 ? inner.iters : 1;
+    res->iters += inner.iters;
+    k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, nrm[0], NRHS > 1 ? nrm[NRHS - 1] : 0.0);
+    rc = check_cuda(ctx, cudaGetLastError(), "correction");
+    if (rc) return rc;
+  }
+}
+
+template <int K, bool MIX>
+int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, const double* gu,
+              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st) {
+  const int G = P->grid;
+  const int k = P->k;
+  const double a = f.dt / (2.0 * f.Re);
+  const void* vdx = MIX ? (const void*)P->vv_dx32 : (const void*)f.vv_dx;
+  const void* vdy = MIX ? (const void*)P->vv_dy32 : (const void*)f.vv_dy;
+  const void* vlap = MIX ? (const void*)P->vv_lap32 : (const void*)f.vv_lap;
+  const void* pdx = MIX ? (const void*)P->pv_dx32 : (const void*)f.pv_dx;
+  const void* pdy = MIX ? (const void*)P->pv_dy32 : (const void*)f.pv_dy;
+  const void* plap = MIX ? (const void*)P->pp_lap32 : (const void*)f.pp_lap;
+  const void* gdx = MIX ? (const void*)P->vp_dx32 : (const void*)f.vp_dx;
+  const void* gdy = MIX ? (const void*)P->vp_dy32 : (const void*)f.vp_dy;
+  if (MIX) {
+    k_split<<<G, kThreads, 0, st>>>(f.N, s->u, P->u2);
+    k_split<<<G, kThreads, 0, st>>>(f.N, s->v, P->v2);
+    k_split<<<G, kThreads, 0, st>>>(f.M, s->pt, P->pt2);
+  }
+  KOp<double, double> H64{f.vv_idx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
+  KOp<double, double> L64{f.pp_idx, P->Lw, f.ld_p, f.M, k, 0, P->es};
+  KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr};
+  KOp<float, float> L32{f.pp_idx, P->Lw32, f.ld_p, f.M, k, 0, P->es32};
+  for (int32_t step = 0; step < n_steps; ++step) {
+    ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
+                P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,
+                s->j == 0 ? 1 : 0};
+    k_convect<K, MIX><<<G, kThreads, 0, st>>>(ca);
+    HelmRhsArgs ha{f.N,    f.ld_v, k,      f.vv_idx, vlap,   P->us,  P->vs,  P->us2,
+                   P->vs2, f.vp_idx, gdx,  gdy,      s->pt,  P->pt2, f.v_bc, f.v_nx,
+                   f.v_ny, gu,     gv,     a,        f.dt,   f.km_mode, P->ru, P->rv,
+                   P->uss, P->vss};
+    k_helm_rhs<K, MIX><<<G, kThreads, 0, st>>>(ha);
+    int rc = check_cuda(ctx, cudaGetLastError(), "stage 1-2 kernels");
+    if (rc) return rc;
+    double* hx[2] = {P->uss, P->vss};
+    const double* hb[2] = {P->ru, P->rv};
+    SolveResult hr;
+    int sweeps = 0;
+    if (MIX)
+      rc = refine<K, 2, false>(ctx, P, H64, H32, hx, hb, f.tol, f.inner_tol, f.max_iter, &hr,
+                               &sweeps, st);
+    else
+      rc = bicgstab<K, 2, false, double, double>(ctx, P, H64, hx, hb, P->kw64, f.tol, f.max_iter,
+                                                 &hr, st);
+    if (rc) return rc;
+    if (stats) {
+      stats->helm_iters += hr.iters;
+      stats->helm_relres = hr.relres;
+      stats->refinements += sweeps;
+    }
+    if (hr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite viscous solve");
+    if (!hr.converged)
+      return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
+                       "viscous solve: relative residual %.3e after %d iterations", hr.relres,
+                       hr.iters);
+    if (MIX) {
+      k_split<<<G, kThreads, 0, st>>>(f.N, P->uss, P->uss2);
+      k_split<<<G, kThreads, 0, st>>>(f.N, P->vss, P->vss2);
+    }
+    DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, pdx,      pdy,          P->uss,
+               P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb};
+    k_divergence<K, MIX><<<G, kThreads, 0, st>>>(da);
+    rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
+                                         cudaMemcpyDeviceToDevice, st),
+                    "warm start");
+    if (rc) return rc;
+    double* px[1] = {P->px};
+    const double* pbv[1] = {P->pb};
+    SolveResult pr;
+    if (MIX)
+      rc = refine<K, 1, true>(ctx, P, L64, L32, px, pbv, f.tol, f.inner_tol, f.max_iter, &pr,
+                              &sweeps, st);
+    else
+      rc = bicgstab<K, 1, true, double, double>(ctx, P, L64, px, pbv, P->kw64, f.tol, f.max_iter,
+                                                &pr, st);
+    if (rc) return rc;
+    if (stats) {
+      stats->poisson_iters += pr.iters;
+      stats->poisson_relres = pr.relres;
+      stats->refinements += MIX ? sweeps : 0;
+    }
+    if (pr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite pressure solve");
+    if (!pr.converged)
+      return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
+                       "pressure solve: relative residual %.3e after %d iterations", pr.relres,
+                       pr.iters);
+    k_sum<double><<<G, kThreads, 0, st>>>(P->px, f.M, P->gr, P->dscal);
+    if (MIX) k_split<<<G, kThreads, 0, st>>>(f.M, P->px, P->px2);
+    PresArgs pa{f.M, f.ld_p, k, f.pp_idx, plap, P->px, P->px2, P->dscal, a, s->pt, s->p, P->pt2};
+    k_pressure<K, MIX><<<G, kThreads, 0, st>>>(pa);
+    CorrArgs ka{f.N,    f.ld_v, k,      f.vp_idx, gdx,  gdy,  s->pt, P->pt2, P->uss,
+                P->vss, f.v_bc, gu,     gv,       f.dt, f.overwrite_bc, s->u, s->v,
+                P->u2,  P->v2};
+    k_correct<K, MIX><<<G, kThreads, 0, st>>>(ka);
+    rc = check_cuda(ctx, cudaGetLastError(), "stage 3 kernels");
+    if (rc) return rc;
+    s->j += 1;
+    if (stats) stats->steps += 1;
+  }
+  return check_cuda(ctx, cudaStreamSynchronize(st), "step sync");
+}
+
+}  // namespace
+
+int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
+             const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st) {
+  if (ctx->plan && memcmp(&ctx->plan->key, f, sizeof(rbffd_flow)) != 0) {
+    cudaStreamSynchronize(st);
+    step_plan_free(ctx->plan);
+    ctx->plan = nullptr;
+  }
+  if (!ctx->plan) {
+    int rc = build_plan(ctx, *f, &ctx->plan, st);
+    if (rc) return rc;
+  }
+  StepPlan* P = ctx->plan;
+  const bool mix = f->precision == RBFFD_PREC_MIXED;
+  if (P->k == 28)
+    return mix ? run_steps<28, true>(ctx, P, *f, s, gu, gv, n_steps, stats, st)
+               : run_steps<28, false>(ctx, P, *f, s, gu, gv, n_steps, stats, st);
+  return mix ? run_steps<0, true>(ctx, P, *f, s, gu, gv, n_steps, stats, st)
+             : run_steps<0, false>(ctx, P, *f, s, gu, gv, n_steps, stats, st);
+}
+
+}  // namespace rbffd
