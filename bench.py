@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Throughput of the staggered RBF-FD Navier-Stokes fractional step on GB300.
+
+Workload: lid-driven cavity at Re = 10^4 on a jittered 1000 x 1000 P-lattice
+(1,000,000 pressure nodes, ~3,000,000 velocity nodes), (n, m, q) = (28, 7, 3),
+dt = 2e-4, from rest.  A step is one full fractional step (convection,
+Crank-Nicolson viscous solves, divergence, pressure Poisson solve, pressure,
+correction) through rbffd_step.  The headline is the MIXED path (FP32 SpMVs and
+inner Krylov iterations, FP64 refinement to 1e-10 relative residual); the FP64
+path is timed beside it on the same box.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NS time steps/s at 1M nodes (mixed vs FP64 GPU); stencil SpMV % HBM peak"
+UNIT = "steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1000, help="P-lattice side (n x n P-nodes)")
+    ap.add_argument("--re", type=float, default=1.0e4)
+    ap.add_argument("--dt", type=float, default=2e-4)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-iter", type=int, default=400000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    src = os.path.join(ROOT, "paper_2206_06495_gb300", "csrc", "step.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            line = line.split("#")[0].split()
+            if len(line) >= 4 and line[0] == kernel_key and line[3] == sha:
+                return float(line[1]) / float(line[2])
+    except OSError:
+        pass
+    return None
+
+
+# ----------------------------------------------------------- CPU baseline
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import rbffd_oracle as O
+from paper_2206_06495_gb300 import nodesets as ns
+nd = ns.jittered_cavity({n}, 2)
+t0 = time.time()
+fs = O.FractionalStep(nd, Re={re}, dt={dt})
+setup = time.time() - t0
+st = fs.initial_state()
+gu, gv = O.lid_bc(nd)
+for _ in range({warm}):
+    st = fs.step(st, gu, gv)
+t0 = time.time()
+for _ in range({steps}):
+    st = fs.step(st, gu, gv)
+el = time.time() - t0
+print(json.dumps({{"M": nd.M, "N": nd.N, "setup_s": setup, "step_s": el / {steps}}}))
+"""
+
+
+def oracle_sample(n=100, steps=5, warm=1, re=1e4, dt=2e-4):
+    """The CPU oracle, as it stands, on a bounded cavity sample, one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, re=re, dt=dt, warm=warm, steps=steps)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_record(M_target, n=100, steps=5, warm=1, re=1e4, dt=2e-4):
+    r = oracle_sample(n=n, steps=steps, warm=warm, re=re, dt=dt)
+    scaled = (1.0 / r["step_s"]) * (r["M"] / M_target)
+    return {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle fractional step (dense-LU weights, CSR operators, sparse LU "
+                       f"solves) on a {n}x{n} P-lattice cavity (M={r['M']}, N={r['N']}), "
+                       f"{steps} timed steps after {warm} warm-up, {r['step_s']:.4f} s/step; "
+                       f"scaled to M={M_target} by node count (linear, optimistic for the "
+                       f"oracle); one thread")}
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2206_06495_gb300 import build
+    from paper_2206_06495_gb300 import nodesets as ns
+    build.build()
+    from paper_2206_06495_gb300 import rbffd as R
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    ctx = R.Context(28, 7, 3)
+    nd = ns.jittered_cavity(args.n, 2 + rank)
+    t_setup = time.time()
+    flows = {}
+    for name, prec in (("mixed", R.PREC_MIXED), ("fp64", R.PREC_FP64)):
+        if args.only not in ("both", name):
+            continue
+        if not flows:
+            base = R.flow_from_nodes(ctx, nd, Re=args.re, dt=args.dt, precision=prec,
+                                     tol=args.tol, inner_tol=1e-3, max_iter=args.max_iter)
+            flows[name] = base
+        else:
+            b0 = next(iter(flows.values()))
+            flows[name] = R.Flow(N=b0.N, M=b0.M, tensors=b0.tensors, Re=args.re, dt=args.dt,
+                                 precision=prec, tol=args.tol, inner_tol=1e-3,
+                                 max_iter=args.max_iter)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+    gu_h = np.zeros(nd.N)
+    gu_h[nd.v_wall == ns.WALL_TOP] = 1.0
+    gu = torch.as_tensor(gu_h, device="cuda")
+    gv = torch.zeros(nd.N, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    sampler = ClockSampler(local) if rank == 0 else None
+    for name, flow in flows.items():
+        st = R.State.zeros(flow)
+        flow.profile = 0
+        for _ in range(args.warmup):
+            R.step(ctx, flow, st, gu, gv, 1)
+        flow.profile = 1
+        barrier()
+        if sampler and not sampler.rows:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        agg = {"poisson_iters": 0, "helm_iters": 0, "launches": 0, "spmv_ms": 0.0,
+               "spmv_launches": 0, "refinements": 0}
+        e0.record(stream)
+        for _ in range(args.steps):
+            s = R.step(ctx, flow, st, gu, gv, 1)
+            for k in agg:
+                agg[k] += s[k]
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        res[name] = {"ms": ms, "agg": agg, "relres": s["poisson_relres"]}
+        # end to end: boundary data in from pinned host memory, velocity out, every step
+        flow.profile = 0
+        gu_p = torch.empty(nd.N, dtype=torch.float64, pin_memory=True)
+        gv_p = torch.empty(nd.N, dtype=torch.float64, pin_memory=True)
+        gu_p.copy_(torch.as_tensor(gu_h))
+        gv_p.zero_()
+        u_p = torch.empty(nd.N, dtype=torch.float64, pin_memory=True)
+        v_p = torch.empty(nd.N, dtype=torch.float64, pin_memory=True)
+        gu_d = torch.empty_like(gu)
+        gv_d = torch.empty_like(gv)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            gu_d.copy_(gu_p, non_blocking=True)
+            gv_d.copy_(gv_p, non_blocking=True)
+            R.step(ctx, flow, st, gu_d, gv_d, 1)
+            u_p.copy_(st.u, non_blocking=True)
+            v_p.copy_(st.v, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        res[name]["e2e_ms"] = ems
+    if sampler:
+        sampler.stop()
+
+    # stencil SpMV on its own: D^(V,V)_x over all V-nodes, FP64 and FP32 weights
+    spmv = {}
+    t = flows[next(iter(flows))].tensors
+    idx, wx = t["vv_idx"], t["vv_dx"]
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    for wname, w in (("fp64", wx), ("fp32", wx.float())):
+        x = torch.randn(nd.N, dtype=torch.float64 if wname == "fp64" else torch.float32,
+                        device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            R.apply_op(ctx, idx, w, nd.N, nd.N, x, y)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        a.record(stream)
+        for _ in range(reps):
+            R.apply_op(ctx, idx, w, nd.N, nd.N, x, y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        per = a.elapsed_time(b) / reps * 1e-3
+        k = 28
+        wb = 8 if wname == "fp64" else 4
+        bytes_row = k * 4 + k * wb + 2 * wb  # idx, weights, y written, x read once
+        gbs = nd.N * bytes_row / per / 1e9
+        spmv[wname] = {"rows": nd.N, "bytes_per_row": bytes_row, "us": per * 1e6,
+                       "achieved_gbs": gbs, "frac": gbs / hbm}
+
+    if rank != 0:
+        return None
+    head = "mixed" if "mixed" in res else "fp64"
+    r = res[head]
+    steps_total = args.steps * world
+    value = steps_total / (r["ms"] * 1e-3)
+    e2e = steps_total / (r["e2e_ms"] * 1e-3)
+    agg = r["agg"]
+    # roofline of the dominant kernel: the SpMV of the pressure solve
+    k = 28
+    if head == "mixed":
+        bytes_row, key = 8 * k + 16, "k_spmv_fp32_rank1"
+    else:
+        bytes_row, key = 12 * k + 32, "k_spmv_fp64_rank1"
+    per_launch_ms = agg["spmv_ms"] / max(agg["spmv_launches"], 1)
+    achieved = nd.M * bytes_row / (per_launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(key)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"lid-driven cavity Re={args.re:g}, jittered {args.n}x{args.n} "
+                               f"P-lattice (M={nd.M}, N={nd.N}), (n,m,q)=(28,7,3), "
+                               f"dt={args.dt:g}, from rest, pressure/viscous solves to "
+                               f"{args.tol:g} relative residual",
+                   "precision": head, "parallelism": f"replicas{world}",
+                   "l2": "working set (operators ~7 GB) exceeds L2; no flush needed"},
+        "gpu_launches": agg["launches"],
+        "poisson_iters_per_step": agg["poisson_iters"] / args.steps,
+        "helm_iters_per_step": agg["helm_iters"] / args.steps,
+        "setup_s": t_setup,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nd.N * 8,
+                "d2h_bytes_per_step": 2 * nd.N * 8},
+        "roofline": {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "bytes_per_row": bytes_row, "rows": nd.M, "peak_kind": peak_kind,
+                     "launches_timed": agg["spmv_launches"], "us_per_launch": per_launch_ms * 1e3},
+        "spmv": spmv,
+        "clocks": sampler.summary() if sampler else None,
+    }
+    for name in res:
+        rr = res[name]
+        out[name] = {"steps_per_s": args.steps / (rr["ms"] * 1e-3),
+                     "ms_per_step": rr["ms"] / args.steps,
+                     "poisson_iters_per_step": rr["agg"]["poisson_iters"] / args.steps,
+                     "refinements_per_step": rr["agg"]["refinements"] / args.steps,
+                     "e2e_steps_per_s": args.steps / (rr["e2e_ms"] * 1e-3)}
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = cpu_baseline_record(nd.M)
+        except Exception as e:  # reported, never fatal
+            out["cpu_baseline"] = {"error": str(e)[:300]}
+    return out
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    n_sample = 60
+    t0 = time.time()
+    r = oracle_sample(n=n_sample, steps=args.steps, warm=args.warmup, re=args.re, dt=args.dt)
+    M_target = args.n * args.n
+    value = (1.0 / r["step_s"]) * (r["M"] / M_target)
+    sample = (f"CPU oracle fractional steps on a {n_sample}x{n_sample} P-lattice cavity "
+              f"(M={r['M']}, N={r['N']}), {args.steps} timed after {args.warmup} warm-up, "
+              f"scaled to M={M_target} by node count; one thread")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["step_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"lid-driven cavity Re={args.re:g}, jittered "
+                                   f"{args.n}x{args.n} P-lattice (sampled)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.time() - t0}
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

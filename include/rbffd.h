@@ -149,6 +149,8 @@ int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, d
  *                 0 = wall data only, 1 = wall data + dt * tangential part of
  *                 D^(V,P) p~_j (default), 2 = + dt * the full D^(V,P) p~_j
  * overwrite_bc    1 = set wall V-nodes to the wall data after the correction
+ * profile         1 = time every SpMV launch of the pressure solves with CUDA
+ *                 events on `stream` (reported in rbffd_stats); 0 = off
  */
 typedef struct rbffd_flow {
   int64_t N, M, ld_v, ld_p;
@@ -170,6 +172,7 @@ typedef struct rbffd_flow {
   int32_t max_iter;
   int32_t km_mode;
   int32_t overwrite_bc;
+  int32_t profile;
 } rbffd_flow;
 
 /* Solver state at step j (all FP64 device arrays owned by the caller). */
@@ -189,6 +192,9 @@ typedef struct rbffd_stats {
   int64_t refinements;      /* FP64 refinement sweeps (MIXED)                 */
   double helm_relres;       /* last relative residual, viscous solve         */
   double poisson_relres;    /* last relative residual, pressure solve        */
+  int64_t launches;         /* kernels launched by this call                  */
+  int64_t spmv_launches;    /* profile: timed SpMV launches of the pressure solves */
+  double spmv_ms;           /* profile: their summed durations, milliseconds  */
 } rbffd_stats;
 
 /*

@@ -24,6 +24,8 @@
 // FP64 precision: BiCGSTAB in FP64.  MIXED: FP64 iterative refinement whose
 // corrections come from FP32 BiCGSTAB on FP32 copies of the scaled operators.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -34,7 +36,17 @@ namespace rbffd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kNV = 4;  // values reduced per kernel
+constexpr int kNV = 6;  // values reduced per kernel
+
+// RBFFD_TRACE=1 in the environment prints one line per solve and refinement
+// sweep to stderr (iterations, residuals, status).
+bool trace_on() {
+  static const bool on = [] {
+    const char* e = getenv("RBFFD_TRACE");
+    return e && *e && *e != '0';
+  }();
+  return on;
+}
 
 struct KScal {
   double rho[2], alpha[2], omega[2], beta[2];
@@ -46,7 +58,8 @@ struct KScal {
   int iters;
   int maxit;
   int done;
-  int status;  // 0 ok, 1 breakdown, 2 non-finite
+  int status;  // 0 ok, 2 non-finite, 1/3/4 breakdown at (rh,v) = 0 / (t,t) = 0 / rho or
+               // omega = 0, 5 residual grew beyond 1e4 ||b||
 };
 
 __device__ __forceinline__ float2 split2(double x) {
@@ -112,23 +125,34 @@ __global__ void __launch_bounds__(kThreads) k_sum(const TV* __restrict__ x, int6
     else
       part += (float)x[i];
   }
-  double v[kNV] = {partd + (double)part, 0, 0, 0};
+  double v[kNV] = {partd + (double)part, 0, 0, 0, 0, 0};
   grid_reduce<kNV>(v, gr, sh, [&](double* t) { *out = t[0]; });
 }
 
+// sign pattern of a restarted shadow residual (a 32-bit integer hash of i and the seed)
+__device__ __forceinline__ float shadow_sign(int64_t i, uint32_t seed) {
+  uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return (h & 1u) ? 1.f : -1.f;
+}
+
+// r = b - A x ; p = r ; shadow residual rh = r (seed 0) or r with seeded signs
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_init(KOp<TW, TV> op, Vecs<TV, NRHS> x, Vecs<TV, NRHS> b, Vecs<TV, NRHS> r,
            Vecs<TV, NRHS> rh, Vecs<TV, NRHS> p, const double* sigma_x, KScal* sc, GridReduce gr,
-           double tol2, int maxit) {
+           double tol2, int maxit, uint32_t seed) {
   using A = typename Acc<TW>::t;
   __shared__ double sh[kNV * kThreads / 32];
-  A prr[2] = {0, 0}, pbb[2] = {0, 0}, psum = 0;
+  A prr[2] = {0, 0}, pbb[2] = {0, 0}, prh[2] = {0, 0}, psum = 0;
   const A sig = RANK1 ? (A)*sigma_x : (A)0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
        i += (int64_t)gridDim.x * kThreads) {
     A acc[NRHS];
     gather_rows<K, NRHS>(op, i, (const TV* const*)x.v, acc);
+    const A sgn = seed ? (A)shadow_sign(i, seed) : (A)1;
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
       A ax = acc[q];
@@ -137,15 +161,17 @@ __global__ void __launch_bounds__(kThreads)
       const A bi = (A)b.v[q][i];
       const A ri = bi - ax;
       r.v[q][i] = (TV)ri;
-      rh.v[q][i] = (TV)ri;
+      rh.v[q][i] = (TV)(sgn * ri);
       p.v[q][i] = (TV)ri;
       prr[q] += ri * ri;
       pbb[q] += bi * bi;
+      prh[q] += sgn * ri * ri;
       if (RANK1) psum += ri;
     }
   }
-  double v[kNV] = {(double)prr[0], (double)pbb[0], NRHS > 1 ? (double)prr[1] : (double)psum,
-                   NRHS > 1 ? (double)pbb[1] : 0.0};
+  double v[kNV] = {(double)prr[0], (double)pbb[0], (double)prr[1],
+                   (double)pbb[1], (double)prh[0], (double)prh[1]};
+  if (RANK1) v[5] = (double)psum;  // NRHS == 1 here: slot 5 carries sum(r)
   grid_reduce<kNV>(v, gr, sh, [&](double* t) {
     sc->tol2 = tol2;
     sc->maxit = maxit;
@@ -154,18 +180,19 @@ __global__ void __launch_bounds__(kThreads)
     int any = 0;
     for (int q = 0; q < NRHS; ++q) {
       const double rr = t[2 * q], bb = t[2 * q + 1];
+      const double rho = q == 0 ? t[4] : t[5];
       sc->rr[q] = rr;
       sc->bb[q] = bb;
-      sc->rho[q] = rr;
+      sc->rho[q] = rho;
       sc->alpha[q] = 1.0;
       sc->omega[q] = 1.0;
       sc->half[q] = 0;
       if (!isfinite(rr)) sc->status = 2;
-      sc->active[q] = (isfinite(rr) && rr > tol2 * bb) ? 1 : 0;
+      sc->active[q] = (isfinite(rr) && rr > tol2 * bb && rho != 0.0) ? 1 : 0;
       any |= sc->active[q];
     }
     for (int q = NRHS; q < 2; ++q) sc->active[q] = 0;
-    if (RANK1) sc->sum_p = t[2];
+    if (RANK1) sc->sum_p = t[5];
     sc->done = (any && maxit > 0) ? 0 : 1;
   });
 }
@@ -193,7 +220,7 @@ __global__ void __launch_bounds__(kThreads)
       pd[q] += (A)rh.v[q][i] * y;
     }
   }
-  double vv[kNV] = {(double)pd[0], (double)pd[1], 0, 0};
+  double vv[kNV] = {(double)pd[0], (double)pd[1], 0, 0, 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
     for (int q = 0; q < NRHS; ++q) {
       if (!sc->active[q]) continue;
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(kThreads)
       if (RANK1) psum += si;
     }
   }
-  double vv[kNV] = {(double)pss[0], (double)pss[1], (double)psum, 0};
+  double vv[kNV] = {(double)pss[0], (double)pss[1], (double)psum, 0, 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
     for (int q = 0; q < NRHS; ++q)
       if (sc->active[q] && t[q] <= sc->tol2 * sc->bb[q]) sc->half[q] = 1;
@@ -267,7 +294,7 @@ __global__ void __launch_bounds__(kThreads)
       ptt[q] += y * y;
     }
   }
-  double vv[kNV] = {(double)pts[0], (double)ptt[0], (double)pts[1], (double)ptt[1]};
+  double vv[kNV] = {(double)pts[0], (double)ptt[0], (double)pts[1], (double)ptt[1], 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
     for (int q = 0; q < NRHS; ++q) {
       if (!sc->active[q] || sc->half[q]) continue;
@@ -275,7 +302,7 @@ __global__ void __launch_bounds__(kThreads)
       if (!(t2 > 0.0) || !isfinite(ts)) {
         sc->omega[q] = 0.0;
         sc->active[q] = 0;
-        sc->status = isfinite(t2) ? 1 : 2;
+        sc->status = isfinite(t2) ? 3 : 2;
         continue;
       }
       sc->omega[q] = ts / t2;
@@ -320,7 +347,7 @@ __global__ void __launch_bounds__(kThreads)
       prr[q] += ri * ri;
     }
   }
-  double vv[kNV] = {(double)prh[0], (double)prr[0], (double)prh[1], (double)prr[1]};
+  double vv[kNV] = {(double)prh[0], (double)prr[0], (double)prh[1], (double)prr[1], 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
     sc->iters += 1;
     int any = 0;
@@ -333,12 +360,17 @@ __global__ void __launch_bounds__(kThreads)
         sc->active[q] = 0;
         continue;
       }
+      if (rr > 1e8 * sc->bb[q] && sc->bb[q] > 0.0) {  // the recurrence has blown up
+        sc->status = 5;
+        sc->active[q] = 0;
+        continue;
+      }
       if (sc->half[q] || rr <= sc->tol2 * sc->bb[q]) {
         sc->active[q] = 0;
         continue;
       }
       if (rho_new == 0.0 || sc->omega[q] == 0.0) {
-        sc->status = 1;
+        sc->status = 4;
         sc->active[q] = 0;
         continue;
       }
@@ -377,7 +409,7 @@ __global__ void __launch_bounds__(kThreads)
       if (RANK1) psum += pi;
     }
   }
-  double vv[kNV] = {(double)psum, 0, 0, 0};
+  double vv[kNV] = {(double)psum, 0, 0, 0, 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
     if (RANK1) sc->sum_p = tt[0];
   });
@@ -407,7 +439,7 @@ __global__ void __launch_bounds__(kThreads)
       pbb[q] += bi * bi;
     }
   }
-  double vv[kNV] = {prr[0], pbb[0], prr[1], pbb[1]};
+  double vv[kNV] = {prr[0], pbb[0], prr[1], pbb[1], 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
     for (int j = 0; j < kNV; ++j) out4[j] = t[j];
   });
@@ -722,6 +754,13 @@ __global__ void k_build_helm(int64_t N, int64_t ld, int k, const double* __restr
   }
 }
 
+__global__ void k_scale_by_inv_abs(int64_t n, double* __restrict__ x, const double* sum) {
+  const double s = *sum != 0.0 ? 1.0 / fabs(*sum) : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
 __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -746,20 +785,30 @@ struct StepPlan {
   // stage vectors
   double *us = nullptr, *vs = nullptr, *ru = nullptr, *rv = nullptr, *uss = nullptr,
          *vss = nullptr, *pb = nullptr, *px = nullptr;
+  int64_t px_step = -1;  // step index whose pressure solve left its solution in px
   float2 *u2 = nullptr, *v2 = nullptr, *us2 = nullptr, *vs2 = nullptr, *uss2 = nullptr,
          *vss2 = nullptr, *pt2 = nullptr, *px2 = nullptr;
   // Krylov work (6 vectors x 2 right sides) in FP64 and FP32
-  double* kw64[6][2] = {};
-  float* kw32[6][2] = {};
+  double* kw64[7][2] = {};
+  float* kw32[7][2] = {};
   float *e32[2] = {}, *r32[2] = {};
   double* r64[2] = {};
   KScal* sc = nullptr;
-  double* dscal = nullptr;  // [0]: sum, [1..4]: residual norms
+  double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
+  int64_t launches = 0;     // kernels launched by rbffd_step on this plan
+  // optional per-launch timing of the pressure-solve SpMV kernels
+  static constexpr int kEv = 512;
+  cudaEvent_t ev[kEv] = {};
+  int ev_used = 0;
+  double spmv_ms = 0.0;
+  int64_t spmv_launches = 0;
   GridReduce gr{};
 };
 
 void step_plan_free(StepPlan* p) {
   if (!p) return;
+  for (int i = 0; i < StepPlan::kEv; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   for (void* a : p->allocs) cudaFree(a);
   delete p;
 }
@@ -815,7 +864,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   TRY(palloc(ctx, p, &p->vss, f.N));
   TRY(palloc(ctx, p, &p->pb, f.M));
   TRY(palloc(ctx, p, &p->px, f.M));
-  for (int a = 0; a < 6; ++a)
+  for (int a = 0; a < 7; ++a)
     for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw64[a][b], nmax));
   TRY(palloc(ctx, p, &p->sc, 1));
   TRY(palloc(ctx, p, &p->dscal, 8));
@@ -826,6 +875,9 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.pp_dx,
                                                  f.pp_dy, f.p_bc, f.p_nx, f.p_ny, p->Lw, p->es,
                                                  p->scale);
+  // normalise the rank-one column so that the constant mode has eigenvalue 1
+  k_sum<double><<<p->grid, kThreads, 0, st>>>(p->es, f.M, p->gr, p->dscal);
+  k_scale_by_inv_abs<<<p->grid, kThreads, 0, st>>>(f.M, p->es, p->dscal);
   k_build_helm<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bc, a, p->Hw);
   TRY(check_cuda(ctx, cudaGetLastError(), "plan kernels"));
   if (p->mix) {
@@ -848,7 +900,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     TRY(palloc(ctx, p, &p->vss2, f.N));
     TRY(palloc(ctx, p, &p->pt2, f.M));
     TRY(palloc(ctx, p, &p->px2, f.M));
-    for (int a2 = 0; a2 < 6; ++a2)
+    for (int a2 = 0; a2 < 7; ++a2)
       for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw32[a2][b], nmax));
     for (int b = 0; b < 2; ++b) {
       TRY(palloc(ctx, p, &p->e32[b], nmax));
@@ -865,14 +917,26 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
 struct SolveResult {
   int iters = 0;
   double relres = 0.0;
-  int status = 0;  // 0 ok, 1 breakdown, 2 non-finite
+  int status = 0;  // as KScal::status
   bool converged = false;
 };
+
+// Add up the durations of the recorded SpMV launches (the stream is idle here).
+void collect_events(StepPlan* P) {
+  for (int i = 0; i + 1 < P->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]) == cudaSuccess) {
+      P->spmv_ms += ms;
+      P->spmv_launches += 1;
+    }
+  }
+  P->ev_used = 0;
+}
 
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
-             cudaStream_t st) {
+             cudaStream_t st, bool prof = false, uint32_t seed_base = 0) {
   Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
@@ -886,44 +950,82 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   }
   const int G = P->grid;
   double* sigx = P->dscal;
-  if (RANK1) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx);
-  k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
-                                                  tol * tol, maxit);
-  int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
-  if (rc) return rc;
   KScal* h = (KScal*)ctx->host_pinned;
-  int issued = 0, chunk = 4;
-  for (;;) {
-    rc = check_cuda(ctx, cudaMemcpyAsync(h, P->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st),
-                    "scalar copy");
-    if (rc) return rc;
-    rc = check_cuda(ctx, cudaStreamSynchronize(st), "bicgstab sync");
-    if (rc) return rc;
-    if (h->done || issued >= maxit) break;
-    const int n = std::min(chunk, maxit - issued);
-    for (int it = 0; it < n; ++it) {
-      k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr);
-      k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr);
-      k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr);
-      k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
-      k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr);
-    }
-    rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
-    if (rc) return rc;
-    issued += n;
-    chunk = std::min(chunk * 2, 64);
-  }
-  res->iters = h->iters;
-  res->status = h->status;
-  double worst = 0.0;
-  bool conv = true;
+  int total = 0;
   for (int q = 0; q < NRHS; ++q) {
-    const double rel = h->bb[q] > 0 ? sqrt(h->rr[q] / h->bb[q]) : sqrt(h->rr[q]);
-    worst = fmax(worst, rel);
-    if (!(h->rr[q] <= h->tol2 * h->bb[q])) conv = false;
+    int rc = check_cuda(ctx, cudaMemcpyAsync(work[6][q], x[q], sizeof(TV) * op.n,
+                                             cudaMemcpyDeviceToDevice, st),
+                        "save x0");
+    if (rc) return rc;
   }
-  res->relres = worst;
-  res->converged = conv;
+  // A breakdown of the recurrences (a zero inner product) restarts the method
+  // from the current iterate with a fresh shadow residual.
+  for (int restart = 0;; ++restart) {
+    if (RANK1) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx);
+    k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
+                                                    tol * tol, maxit - total,
+                                                    (restart || seed_base)
+                                                        ? 0x51ED27u + 977u * seed_base + restart
+                                                        : 0u);
+    P->launches += RANK1 ? 2 : 1;
+    int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
+    if (rc) return rc;
+    int issued = 0, chunk = 4;
+    const int budget = maxit - total;
+    for (;;) {
+      rc = check_cuda(ctx, cudaMemcpyAsync(h, P->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st),
+                      "scalar copy");
+      if (rc) return rc;
+      rc = check_cuda(ctx, cudaStreamSynchronize(st), "bicgstab sync");
+      if (rc) return rc;
+      if (prof) collect_events(P);
+      if (h->done || issued >= budget) break;
+      int n = std::min(chunk, budget - issued);
+      if (prof) n = std::min(n, StepPlan::kEv / 4);
+      for (int it = 0; it < n; ++it) {
+        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
+        k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr);
+        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
+        k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr);
+        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
+        k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr);
+        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
+        k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
+        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr);
+      }
+      P->launches += 5 * n;
+      rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
+      if (rc) return rc;
+      issued += n;
+      chunk = std::min(chunk * 2, 64);
+    }
+    total += h->iters;
+    double worst = 0.0;
+    bool conv = true;
+    for (int q = 0; q < NRHS; ++q) {
+      const double rel = h->bb[q] > 0 ? sqrt(h->rr[q] / h->bb[q]) : sqrt(h->rr[q]);
+      worst = fmax(worst, rel);
+      if (!(h->rr[q] <= h->tol2 * h->bb[q])) conv = false;
+    }
+    res->iters = total;
+    res->status = h->status;
+    res->relres = worst;
+    res->converged = conv;
+    if (trace_on())
+      fprintf(stderr, "[rbffd] bicgstab %s nrhs=%d restart=%d iters=%d relres=%.3e status=%d\n",
+              sizeof(TV) == 8 ? "fp64" : "fp32", NRHS, restart, h->iters, worst, h->status);
+    const bool breakdown = h->status == 1 || h->status == 3 || h->status == 4;
+    const bool diverged = h->status == 5;
+    if (conv || !(breakdown || diverged) || total >= maxit || restart >= 50) break;
+    if (diverged) {  // start again from the initial iterate
+      for (int q = 0; q < NRHS; ++q) {
+        rc = check_cuda(ctx, cudaMemcpyAsync(x[q], work[6][q], sizeof(TV) * op.n,
+                                             cudaMemcpyDeviceToDevice, st),
+                        "restore x0");
+        if (rc) return rc;
+      }
+    }
+  }
   return RBFFD_OK;
 }
 
@@ -931,7 +1033,8 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
 template <int K, int NRHS, bool RANK1>
 int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
            const KOp<float, float>& op32, double* const* x, const double* const* b, double tol,
-           double inner_tol, int maxit, SolveResult* res, int* sweeps, cudaStream_t st) {
+           double inner_tol, int maxit, SolveResult* res, int* sweeps, cudaStream_t st,
+           bool prof = false) {
   Vecs<double, NRHS> X, B, R;
   Vecs<float, NRHS> R32, E32;
   for (int q = 0; q < NRHS; ++q) {
@@ -942,7 +1045,8 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     E32.v[q] = P->e32[q];
   }
   const int G = P->grid;
-  int used = 0;
+  int used = 0, failures = 0, retries = 0;
+  double prev_rel = INFINITY, last_nrm[2] = {0, 0};
   res->iters = 0;
   res->status = 0;
   *sweeps = 0;
@@ -951,6 +1055,7 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     if (RANK1) k_sum<double><<<G, kThreads, 0, st>>>(x[0], op64.n, P->gr, P->dscal);
     k_residual64<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op64, X, B, R, P->dscal, P->dscal + 1,
                                                          P->gr);
+    P->launches += RANK1 ? 2 : 1;
     int rc = check_cuda(ctx, cudaGetLastError(), "residual");
     if (rc) return rc;
     rc = check_cuda(ctx, cudaMemcpyAsync(h, P->dscal + 1, 4 * sizeof(double),
@@ -960,33 +1065,52 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     rc = check_cuda(ctx, cudaStreamSynchronize(st), "residual sync");
     if (rc) return rc;
     double worst = 0.0, nrm[2] = {0, 0};
-    bool conv = true;
+    bool conv = true, finite = true;
     for (int q = 0; q < NRHS; ++q) {
       const double rr = h[2 * q], bb = h[2 * q + 1];
-      if (!std::isfinite(rr)) {
-        res->status = 2;
-        res->relres = NAN;
-        res->converged = false;
-        return RBFFD_OK;
-      }
+      if (!std::isfinite(rr)) finite = false;
       nrm[q] = sqrt(rr);
       const double rel = bb > 0 ? sqrt(rr / bb) : sqrt(rr);
       worst = fmax(worst, rel);
       if (!(rr <= tol * tol * bb)) conv = false;
     }
+    if (sweep > 0 && (!finite || !(worst < prev_rel))) {
+      // the last correction made things worse: undo it and solve again
+      k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, -last_nrm[0],
+                                              NRHS > 1 ? -last_nrm[NRHS - 1] : 0.0);
+      P->launches += 1;
+      rc = check_cuda(ctx, cudaGetLastError(), "undo correction");
+      if (rc) return rc;
+      ++retries;
+      if (++failures > 6 || used >= maxit) {
+        res->relres = prev_rel;
+        res->converged = false;
+        res->status = finite ? 5 : 2;
+        return RBFFD_OK;
+      }
+      continue;  // recompute the residual of the restored iterate
+    }
+    if (trace_on())
+      fprintf(stderr, "[rbffd] refine nrhs=%d sweep=%d relres=%.3e used=%d\n", NRHS, sweep, worst,
+              used);
+    failures = 0;
+    prev_rel = worst;
     res->relres = worst;
     res->converged = conv;
-    if (conv || used >= maxit || sweep >= 40) return RBFFD_OK;
+    if (conv || used >= maxit || sweep >= 60) return RBFFD_OK;
     ++*sweeps;
     const double i0 = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
     const double i1 = NRHS > 1 && nrm[NRHS - 1] > 0 ? 1.0 / nrm[NRHS - 1] : 0.0;
     k_to32<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, R32, E32, i0, i1);
+    P->launches += 2;  // with the correction below
     SolveResult inner;
     rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
-                                                maxit - used, &inner, st);
+                                                maxit - used, &inner, st, prof, retries);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
+    last_nrm[0] = nrm[0];
+    last_nrm[1] = nrm[1];
     k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, nrm[0], NRHS > 1 ? nrm[NRHS - 1] : 0.0);
     rc = check_cuda(ctx, cudaGetLastError(), "correction");
     if (rc) return rc;
@@ -1011,6 +1135,16 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     k_split<<<G, kThreads, 0, st>>>(f.N, s->u, P->u2);
     k_split<<<G, kThreads, 0, st>>>(f.N, s->v, P->v2);
     k_split<<<G, kThreads, 0, st>>>(f.M, s->pt, P->pt2);
+    P->launches += 3;
+  }
+  const int64_t launches0 = P->launches;
+  P->spmv_ms = 0.0;
+  P->spmv_launches = 0;
+  if (f.profile && !P->ev[0]) {
+    for (int i = 0; i < StepPlan::kEv; ++i) {
+      int rc = check_cuda(ctx, cudaEventCreate(&P->ev[i]), "event create");
+      if (rc) return rc;
+    }
   }
   KOp<double, double> H64{f.vv_idx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
   KOp<double, double> L64{f.pp_idx, P->Lw, f.ld_p, f.M, k, 0, P->es};
@@ -1026,6 +1160,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                    f.v_ny, gu,     gv,     a,        f.dt,   f.km_mode, P->ru, P->rv,
                    P->uss, P->vss};
     k_helm_rhs<K, MIX><<<G, kThreads, 0, st>>>(ha);
+    P->launches += 2 + (MIX ? 2 : 0) + 4 + (MIX ? 1 : 0);  // stage kernels of this step
     int rc = check_cuda(ctx, cudaGetLastError(), "stage 1-2 kernels");
     if (rc) return rc;
     double* hx[2] = {P->uss, P->vss};
@@ -1047,8 +1182,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     if (hr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite viscous solve");
     if (!hr.converged)
       return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
-                       "viscous solve: relative residual %.3e after %d iterations", hr.relres,
-                       hr.iters);
+                       "viscous solve: relative residual %.3e after %d iterations (status %d)",
+                       hr.relres, hr.iters, hr.status);
     if (MIX) {
       k_split<<<G, kThreads, 0, st>>>(f.N, P->uss, P->uss2);
       k_split<<<G, kThreads, 0, st>>>(f.N, P->vss, P->vss2);
@@ -1056,19 +1191,22 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, pdx,      pdy,          P->uss,
                P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb};
     k_divergence<K, MIX><<<G, kThreads, 0, st>>>(da);
-    rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
-                                         cudaMemcpyDeviceToDevice, st),
-                    "warm start");
-    if (rc) return rc;
+    if (P->px_step != s->j) {  // warm start from the state's p~ unless px is current
+      rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
+                                           cudaMemcpyDeviceToDevice, st),
+                      "warm start");
+      if (rc) return rc;
+    }
     double* px[1] = {P->px};
     const double* pbv[1] = {P->pb};
     SolveResult pr;
+    const bool prof = f.profile != 0;
     if (MIX)
       rc = refine<K, 1, true>(ctx, P, L64, L32, px, pbv, f.tol, f.inner_tol, f.max_iter, &pr,
-                              &sweeps, st);
+                              &sweeps, st, prof);
     else
       rc = bicgstab<K, 1, true, double, double>(ctx, P, L64, px, pbv, P->kw64, f.tol, f.max_iter,
-                                                &pr, st);
+                                                &pr, st, prof);
     if (rc) return rc;
     if (stats) {
       stats->poisson_iters += pr.iters;
@@ -1078,8 +1216,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     if (pr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite pressure solve");
     if (!pr.converged)
       return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
-                       "pressure solve: relative residual %.3e after %d iterations", pr.relres,
-                       pr.iters);
+                       "pressure solve: relative residual %.3e after %d iterations (status %d)",
+                       pr.relres, pr.iters, pr.status);
     k_sum<double><<<G, kThreads, 0, st>>>(P->px, f.M, P->gr, P->dscal);
     if (MIX) k_split<<<G, kThreads, 0, st>>>(f.M, P->px, P->px2);
     PresArgs pa{f.M, f.ld_p, k, f.pp_idx, plap, P->px, P->px2, P->dscal, a, s->pt, s->p, P->pt2};
@@ -1091,9 +1229,16 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     rc = check_cuda(ctx, cudaGetLastError(), "stage 3 kernels");
     if (rc) return rc;
     s->j += 1;
+    P->px_step = s->j;
     if (stats) stats->steps += 1;
   }
-  return check_cuda(ctx, cudaStreamSynchronize(st), "step sync");
+  int rc = check_cuda(ctx, cudaStreamSynchronize(st), "step sync");
+  if (stats) {
+    stats->launches = P->launches - launches0;
+    stats->spmv_launches = P->spmv_launches;
+    stats->spmv_ms = P->spmv_ms;
+  }
+  return rc;
 }
 
 }  // namespace

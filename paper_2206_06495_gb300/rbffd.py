@@ -61,7 +61,7 @@ class FlowC(C.Structure):
                 ("p_bc", C.c_void_p), ("p_nx", C.c_void_p), ("p_ny", C.c_void_p),
                 ("Re", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("max_iter", C.c_int32),
-                ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32)]
+                ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32), ("profile", C.c_int32)]
 
 
 class StateC(C.Structure):
@@ -73,7 +73,8 @@ class StateC(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("helm_iters", C.c_int64), ("poisson_iters", C.c_int64),
                 ("refinements", C.c_int64), ("helm_relres", C.c_double),
-                ("poisson_relres", C.c_double)]
+                ("poisson_relres", C.c_double), ("launches", C.c_int64),
+                ("spmv_launches", C.c_int64), ("spmv_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -215,10 +216,11 @@ class Flow:
     dt: float
     precision: int = PREC_FP64
     tol: float = 1e-12
-    inner_tol: float = 1e-4
+    inner_tol: float = 1e-3
     max_iter: int = 20000
     km_mode: int = 1
     overwrite_bc: int = 1
+    profile: int = 0
     _c: FlowC = field(default=None, repr=False)
 
     def cstruct(self) -> FlowC:
@@ -233,7 +235,7 @@ class Flow:
                      p_bc=p("p_bc"), p_nx=p("p_nx"), p_ny=p("p_ny"),
                      Re=self.Re, dt=self.dt, precision=self.precision, tol=self.tol,
                      inner_tol=self.inner_tol, max_iter=self.max_iter, km_mode=self.km_mode,
-                     overwrite_bc=self.overwrite_bc)
+                     overwrite_bc=self.overwrite_bc, profile=self.profile)
 
 
 def flow_from_nodes(ctx: Context, nodes, Re: float, dt: float, device="cuda", **kw) -> Flow:
