@@ -220,11 +220,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     res = {}
     sampler = ClockSampler(local) if rank == 0 else None
+    failed = {}
     for name, flow in flows.items():
         st = R.State.zeros(flow)
         flow.profile = 0
-        for _ in range(args.warmup):
-            R.step(ctx, flow, st, gu, gv, 1)
+        try:
+            for _ in range(args.warmup):
+                R.step(ctx, flow, st, gu, gv, 1)
+        except R.RbffdError as e:
+            failed[name] = str(e)[:300]
+            continue
         flow.profile = 1
         barrier()
         if sampler and not sampler.rows:
@@ -233,10 +238,14 @@ def run_ours(args):
         agg = {"poisson_iters": 0, "helm_iters": 0, "launches": 0, "spmv_ms": 0.0,
                "spmv_launches": 0, "refinements": 0}
         e0.record(stream)
-        for _ in range(args.steps):
-            s = R.step(ctx, flow, st, gu, gv, 1)
-            for k in agg:
-                agg[k] += s[k]
+        try:
+            for _ in range(args.steps):
+                s = R.step(ctx, flow, st, gu, gv, 1)
+                for k in agg:
+                    agg[k] += s[k]
+        except R.RbffdError as e:
+            failed[name] = str(e)[:300]
+            continue
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -304,6 +313,8 @@ def run_ours(args):
 
     if rank != 0:
         return None
+    if not res:
+        return {"metric": METRIC, "value": None, "unit": UNIT, "error": failed}
     head = "mixed" if "mixed" in res else "fp64"
     r = res[head]
     steps_total = args.steps * world
@@ -342,6 +353,7 @@ def run_ours(args):
                      "launches_timed": agg["spmv_launches"], "us_per_launch": per_launch_ms * 1e3},
         "spmv": spmv,
         "clocks": sampler.summary() if sampler else None,
+        "failed": failed,
     }
     for name in res:
         rr = res[name]
