@@ -107,6 +107,27 @@ int rbffd_build_weights(rbffd_ctx* ctx, const double* ax, const double* ay, int6
                         int32_t* idx, double* w, int64_t ld, int64_t* bad_node,
                         cudaStream_t stream);
 
+/*
+ * rbffd_build_weights_masked - as rbffd_build_weights with two stencil rules
+ * used for one-sided boundary operators (Section 2.2's nearest-n rule applied
+ * to a subset of the beta-nodes):
+ * beta_mask   device uint8[n_beta] or NULL: only beta-nodes with a nonzero
+ *             entry are stencil candidates
+ * alpha_self  device int32[n_alpha] or NULL: when given, slot 0 of row i is
+ *             beta-node alpha_self[i] (normally the alpha-node itself, present
+ *             in the beta set but masked out) and slots 1..n-1 are the n-1
+ *             nearest candidates
+ * Both tables are checked on the host (INVALID_ARG if fewer than the needed
+ * candidates pass the mask or an alpha_self entry is out of range).
+ * Used for the pressure rows of boundary P-nodes: the node itself followed by
+ * its n-1 nearest interior P-nodes.  Synchronises `stream`.
+ */
+int rbffd_build_weights_masked(rbffd_ctx* ctx, const double* ax, const double* ay,
+                               int64_t n_alpha, const double* bx, const double* by,
+                               int64_t n_beta, const uint8_t* beta_mask,
+                               const int32_t* alpha_self, uint32_t op_mask, int32_t* idx,
+                               double* w, int64_t ld, int64_t* bad_node, cudaStream_t stream);
+
 /* One ELL operator (see the conventions above). */
 typedef struct rbffd_ell {
   const int32_t* idx; /* int32[n * ld]                                       */
@@ -138,8 +159,15 @@ int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, d
  *   v_bc[i] != 0   V-node i lies on a wall; u, v there are Dirichlet data
  *   v_nx, v_ny     outward wall normal at wall V-nodes (unit length)
  *   p_bc[i] != 0   P-node i is a boundary node: its pressure row is the
- *                  homogeneous Neumann row p_nx D_x + p_ny D_y
+ *                  homogeneous Neumann row p_nx D_x + p_ny D_y built on the
+ *                  one-sided stencil pn_* below
  *   p_nx, p_ny     outward normal at boundary P-nodes
+ *   nb_p, ld_b     number of boundary P-nodes; leading dimension of pn_*
+ *   pn_rows        int32[nb_p]: the P-node of each Neumann row (every P-node
+ *                  with p_bc != 0 appears exactly once)
+ *   pn_idx, pn_dx, pn_dy  one-sided P -> P stencils of those nodes (slot 0 =
+ *                  the node, then its nearest interior P-nodes), as built by
+ *                  rbffd_build_weights_masked
  * Re, dt          Reynolds number and time step; a = dt / (2 Re)
  * precision       RBFFD_PREC_FP64 or RBFFD_PREC_MIXED
  * tol             relative residual of both implicit solves (scaled systems)
@@ -166,6 +194,10 @@ typedef struct rbffd_flow {
   const double *v_nx, *v_ny;
   const uint8_t* p_bc;
   const double *p_nx, *p_ny;
+  int64_t nb_p, ld_b;
+  const int32_t* pn_rows;
+  const int32_t* pn_idx;
+  const double *pn_dx, *pn_dy;
   double Re, dt;
   int32_t precision;
   double tol, inner_tol;

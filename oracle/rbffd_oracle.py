@@ -27,7 +27,10 @@ Readings of points the paper leaves open (each one is listed in the design doc):
   R3 k-NN ties: sort by (squared distance, index); squared distance is
      dx*dx + dy*dy with each operation rounded (no fused multiply-add).
   R4 pressure Poisson: boundary P-rows are replaced by a homogeneous Neumann
-     row n_x D_x + n_y D_y; the constant null space is removed by bordering
+     row n_x D_x + n_y D_y whose stencil is the boundary node itself followed
+     by its n-1 nearest interior P-nodes (a one-sided stencil that does not
+     lean on the other wall nodes, which carry no normal information); the
+     constant null space is removed by bordering
      [L e; 1^T 0][p; lam] = [b; 0], where e is 1 on interior P-rows and 0 on
      boundary rows (the multiplier absorbs the incompatibility of the
      non-symmetric L in the interior rows only; the Neumann rows stay
@@ -57,11 +60,14 @@ ALL_OPS = (OP_INTERP, OP_DX, OP_DY, OP_LAP)
 # --------------------------------------------------------------------------
 # Stencils (Section 2.2: row i uses the n nearest beta-nodes of alpha-node i)
 # --------------------------------------------------------------------------
-def knn(ax, ay, bx, by, k: int, chunk: int = 256) -> np.ndarray:
+def knn(ax, ay, bx, by, k: int, chunk: int = 256, beta_mask=None, alpha_self=None) -> np.ndarray:
     """Indices of the k nearest beta-nodes of every alpha-node, nearest first.
 
     Brute force over all beta-nodes; ordering key (d^2, index) with
     d^2 = dx*dx + dy*dy evaluated one rounded operation at a time.
+    beta_mask: only beta-nodes with a nonzero mask are candidates.
+    alpha_self: beta index of each alpha-node; when given, slot 0 is that
+    node and the other k-1 slots are the nearest masked beta-nodes.
     Returns int64 [n_alpha, k].
     """
     ax = np.asarray(ax, np.float64)
@@ -69,14 +75,23 @@ def knn(ax, ay, bx, by, k: int, chunk: int = 256) -> np.ndarray:
     bx = np.asarray(bx, np.float64)
     by = np.asarray(by, np.float64)
     nb = bx.size
-    if k > nb:
+    kk = k - (1 if alpha_self is not None else 0)
+    allowed = np.ones(nb, bool) if beta_mask is None else np.asarray(beta_mask) != 0
+    if kk > int(allowed.sum()):
         raise ValueError("stencil size exceeds the number of beta-nodes")
     out = np.empty((ax.size, k), np.int64)
+    if alpha_self is not None:
+        out[:, 0] = np.asarray(alpha_self)
+        inner = knn(ax, ay, bx, by, kk, chunk, beta_mask, None) if kk > 0 else None
+        if kk > 0:
+            out[:, 1:] = inner
+        return out
     cols = np.arange(nb)
     for s in range(0, ax.size, chunk):
         dx = bx[None, :] - ax[s:s + chunk, None]
         dy = by[None, :] - ay[s:s + chunk, None]
         d2 = dx * dx + dy * dy
+        d2[:, ~allowed] = np.inf
         for r in range(d2.shape[0]):
             row = d2[r]
             kth = np.partition(row, k - 1)[k - 1]
@@ -262,6 +277,8 @@ class Operators:
     pp_y: sp.csr_matrix
     vp_x: sp.csr_matrix  # D^(V,P): P-values -> V-nodes
     vp_y: sp.csr_matrix
+    pn_x: sp.csr_matrix  # P -> boundary P-nodes, one-sided Neumann stencils (R4)
+    pn_y: sp.csr_matrix
     raw: dict
 
 
@@ -273,26 +290,35 @@ def build_operators(nodes, k: int = 28, m: int = 7, q: int = 3) -> Operators:
     i_pv, w_pv = build_weights(px, py, vx, vy, k, m, q, (OP_DX, OP_DY))
     i_pp, w_pp = build_weights(px, py, px, py, k, m, q, (OP_DX, OP_DY, OP_LAP))
     i_vp, w_vp = build_weights(vx, vy, px, py, k, m, q, (OP_DX, OP_DY))
-    raw = {"vv": (i_vv, w_vv), "pv": (i_pv, w_pv), "pp": (i_pp, w_pp), "vp": (i_vp, w_vp)}
+    bnd = np.nonzero(nodes.p_boundary)[0]
+    i_pn = knn(px[bnd], py[bnd], px, py, k, beta_mask=~nodes.p_boundary, alpha_self=bnd)
+    _, w_pn = build_weights(px[bnd], py[bnd], px, py, k, m, q, (OP_DX, OP_DY), idx=i_pn)
+    rows = np.repeat(bnd, k)
+    pn_x = sp.csr_matrix((w_pn[OP_DX].ravel(), (rows, i_pn.ravel())), shape=(M, M))
+    pn_y = sp.csr_matrix((w_pn[OP_DY].ravel(), (rows, i_pn.ravel())), shape=(M, M))
+    raw = {"vv": (i_vv, w_vv), "pv": (i_pv, w_pv), "pp": (i_pp, w_pp), "vp": (i_vp, w_vp),
+           "pn": (bnd, i_pn, w_pn)}
     return Operators(
         vv_x=csr(i_vv, w_vv[OP_DX], N), vv_y=csr(i_vv, w_vv[OP_DY], N),
         vv_lap=csr(i_vv, w_vv[OP_LAP], N),
         pv_x=csr(i_pv, w_pv[OP_DX], N), pv_y=csr(i_pv, w_pv[OP_DY], N),
         pp_lap=csr(i_pp, w_pp[OP_LAP], M), pp_x=csr(i_pp, w_pp[OP_DX], M),
         pp_y=csr(i_pp, w_pp[OP_DY], M),
-        vp_x=csr(i_vp, w_vp[OP_DX], M), vp_y=csr(i_vp, w_vp[OP_DY], M), raw=raw)
+        vp_x=csr(i_vp, w_vp[OP_DX], M), vp_y=csr(i_vp, w_vp[OP_DY], M),
+        pn_x=pn_x, pn_y=pn_y, raw=raw)
 
 
 def poisson_matrix(ops: Operators, p_boundary, p_nx, p_ny) -> sp.csr_matrix:
     """Bordered pressure matrix [[L, e], [1^T, 0]] of reading R4.
 
     L = D^(P,P)_Lap (Eq. pressure_Poisson) with every boundary P-row replaced
-    by n_x D^(P,P)_x + n_y D^(P,P)_y; e = indicator of interior P-rows.
+    by n_x D_x + n_y D_y on the one-sided Neumann stencil of that node (R4);
+    e = indicator of interior P-rows.
     """
     M = ops.pp_lap.shape[0]
     bnd = sp.diags(p_boundary.astype(float))
     inn = sp.diags((~p_boundary).astype(float))
-    L = inn @ ops.pp_lap + bnd @ (sp.diags(p_nx) @ ops.pp_x + sp.diags(p_ny) @ ops.pp_y)
+    L = inn @ ops.pp_lap + bnd @ (sp.diags(p_nx) @ ops.pn_x + sp.diags(p_ny) @ ops.pn_y)
     e = sp.csr_matrix((~p_boundary).astype(float)[:, None])
     one = sp.csr_matrix(np.ones((1, M)))
     return sp.bmat([[L, e], [one, None]], format="csc")

@@ -1,6 +1,7 @@
 // C ABI: context lifetime, error reporting, argument validation.
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -90,10 +91,11 @@ const char* rbffd_last_error(const rbffd_ctx* ctx) {
   return ctx->err.c_str();
 }
 
-int rbffd_build_weights(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,
-                        const double* bx, const double* by, int64_t n_beta, uint32_t op_mask,
-                        int32_t* idx, double* w, int64_t ld, int64_t* bad_node,
-                        cudaStream_t stream) {
+static int build_weights_impl(rbffd_ctx* ctx, const double* ax, const double* ay,
+                              int64_t n_alpha, const double* bx, const double* by, int64_t n_beta,
+                              const uint8_t* beta_mask, const int32_t* alpha_self,
+                              uint32_t op_mask, int32_t* idx, double* w, int64_t ld,
+                              int64_t* bad_node, cudaStream_t stream) {
   if (!ctx) return RBFFD_ERR_INVALID_ARG;
   ctx->err.clear();
   if (bad_node) *bad_node = -1;
@@ -112,9 +114,52 @@ int rbffd_build_weights(rbffd_ctx* ctx, const double* ax, const double* ay, int6
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null array pointer");
   if (ld < n_alpha || ld % 32)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "ld must be >= n_alpha and a multiple of 32");
-  int rc = knn_build(ctx, ax, ay, n_alpha, bx, by, n_beta, k, idx, ld, stream);
+  if (beta_mask || alpha_self) {
+    // both tables are small set-up inputs: check them on the host before any kernel reads them
+    if (beta_mask) {
+      std::vector<uint8_t> m((size_t)n_beta);
+      int rc = check_cuda(ctx, cudaMemcpyAsync(m.data(), beta_mask, (size_t)n_beta,
+                                               cudaMemcpyDeviceToHost, stream), "mask copy");
+      if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(stream), "mask sync");
+      if (rc) return rc;
+      int64_t cnt = 0;
+      for (uint8_t v : m) cnt += v != 0;
+      if (cnt < k - (alpha_self ? 1 : 0))
+        return set_error(ctx, RBFFD_ERR_INVALID_ARG, "only %lld beta-nodes pass the mask",
+                         (long long)cnt);
+    }
+    if (alpha_self) {
+      std::vector<int32_t> a((size_t)n_alpha);
+      int rc = check_cuda(ctx, cudaMemcpyAsync(a.data(), alpha_self, sizeof(int32_t) * n_alpha,
+                                               cudaMemcpyDeviceToHost, stream), "self copy");
+      if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(stream), "self sync");
+      if (rc) return rc;
+      for (int32_t v : a)
+        if (v < 0 || v >= n_beta)
+          return set_error(ctx, RBFFD_ERR_INVALID_ARG, "alpha_self entry %d out of range", v);
+    }
+  }
+  int rc = knn_build(ctx, ax, ay, n_alpha, bx, by, n_beta, beta_mask, alpha_self, k, idx, ld,
+                     stream);
   if (rc) return rc;
   return weights_build(ctx, ax, ay, n_alpha, bx, by, idx, ld, op_mask, w, bad_node, stream);
+}
+
+int rbffd_build_weights(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,
+                        const double* bx, const double* by, int64_t n_beta, uint32_t op_mask,
+                        int32_t* idx, double* w, int64_t ld, int64_t* bad_node,
+                        cudaStream_t stream) {
+  return build_weights_impl(ctx, ax, ay, n_alpha, bx, by, n_beta, nullptr, nullptr, op_mask, idx,
+                            w, ld, bad_node, stream);
+}
+
+int rbffd_build_weights_masked(rbffd_ctx* ctx, const double* ax, const double* ay,
+                               int64_t n_alpha, const double* bx, const double* by,
+                               int64_t n_beta, const uint8_t* beta_mask,
+                               const int32_t* alpha_self, uint32_t op_mask, int32_t* idx,
+                               double* w, int64_t ld, int64_t* bad_node, cudaStream_t stream) {
+  return build_weights_impl(ctx, ax, ay, n_alpha, bx, by, n_beta, beta_mask, alpha_self, op_mask,
+                            idx, w, ld, bad_node, stream);
 }
 
 int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
@@ -143,11 +188,13 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
   const rbffd_flow& f = *flow;
   if (n_steps < 0) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "negative n_steps");
   if (f.N < ctx->prm.n || f.M < ctx->prm.n || f.ld_v < f.N || f.ld_p < f.M || f.ld_v % 32 ||
-      f.ld_p % 32 || f.N > INT32_MAX || f.M > INT32_MAX)
+      f.ld_p % 32 || f.N > INT32_MAX || f.M > INT32_MAX || f.nb_p < 0 || f.nb_p > f.M ||
+      (f.nb_p > 0 && (f.ld_b < f.nb_p || f.ld_b % 32)))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad node counts or leading dimensions");
   if (!f.vv_idx || !f.vv_dx || !f.vv_dy || !f.vv_lap || !f.pv_idx || !f.pv_dx || !f.pv_dy ||
       !f.pp_idx || !f.pp_dx || !f.pp_dy || !f.pp_lap || !f.vp_idx || !f.vp_dx || !f.vp_dy ||
-      !f.v_bc || !f.v_nx || !f.v_ny || !f.p_bc || !f.p_nx || !f.p_ny)
+      !f.v_bc || !f.v_nx || !f.v_ny || !f.p_bc || !f.p_nx || !f.p_ny ||
+      (f.nb_p > 0 && (!f.pn_rows || !f.pn_idx || !f.pn_dx || !f.pn_dy)))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null operator or boundary array");
   if (!state->u || !state->v || !state->cu_prev || !state->cv_prev || !state->pt || !state->p)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");

@@ -117,7 +117,8 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // entry points implemented per translation unit
 int knn_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
-              const double* by, int64_t nb, int k, int32_t* idx, int64_t ld, cudaStream_t st);
+              const double* by, int64_t nb, const uint8_t* beta_mask,
+              const int32_t* alpha_self, int k, int32_t* idx, int64_t ld, cudaStream_t st);
 int weights_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
                   const double* by, const int32_t* idx, int64_t ld, uint32_t op_mask, double* w,
                   int64_t* bad_node, cudaStream_t st);

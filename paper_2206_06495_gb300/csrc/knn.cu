@@ -72,10 +72,14 @@ __device__ __forceinline__ int cell_of(double v, double v0, double inv, int g) {
 }
 
 __global__ void bucket_count(const double* __restrict__ bx, const double* __restrict__ by,
-                             int64_t nb, Grid g, int* __restrict__ cell_id,
-                             int* __restrict__ counts) {
+                             int64_t nb, const uint8_t* __restrict__ mask, Grid g,
+                             int* __restrict__ cell_id, int* __restrict__ counts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (mask && !mask[i]) {
+      cell_id[i] = -1;
+      continue;
+    }
     int cx = cell_of(bx[i], g.x0, g.inv_cell, g.gx);
     int cy = cell_of(by[i], g.y0, g.inv_cell, g.gy);
     int c = cy * g.gx + cx;
@@ -141,7 +145,9 @@ __global__ void bucket_scatter(int64_t nb, const int* __restrict__ cell_id,
                                int* __restrict__ cursor, int* __restrict__ cell_pts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int pos = atomicAdd(&cursor[cell_id[i]], 1);
+    const int c = cell_id[i];
+    if (c < 0) continue;
+    int pos = atomicAdd(&cursor[c], 1);
     cell_pts[pos] = (int)i;
   }
 }
@@ -150,14 +156,21 @@ __device__ __forceinline__ bool better(double d, int j, double bd, int bj) {
   return d < bd || (d == bd && j < bj);
 }
 
+// Optional forms: beta_mask excludes beta-nodes whose mask is 0 (they were
+// never bucketed); alpha_self puts a given beta index in slot 0 and searches
+// the remaining k-1 slots.
 template <int KMAX>
 __global__ void __launch_bounds__(128) knn_query(
     const double* __restrict__ ax, const double* __restrict__ ay, int64_t na,
     const double* __restrict__ bx, const double* __restrict__ by,
-    const int* __restrict__ cell_start, const int* __restrict__ cell_pts, Grid g, int k,
-    int32_t* __restrict__ idx, int64_t ld) {
+    const int* __restrict__ cell_start, const int* __restrict__ cell_pts, Grid g, int k_all,
+    const int32_t* __restrict__ alpha_self, int32_t* __restrict__ idx, int64_t ld) {
+  const int off = alpha_self ? 1 : 0;
+  const int k = k_all - off;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < na;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (alpha_self) idx[i] = alpha_self[i];
+    if (k == 0) continue;
     const double qx = ax[i], qy = ay[i];
     const int cx = cell_of(qx, g.x0, g.inv_cell, g.gx);
     const int cy = cell_of(qy, g.y0, g.inv_cell, g.gy);
@@ -213,14 +226,15 @@ __global__ void __launch_bounds__(128) knn_query(
         if (bd[k - 1] < lb * lb * (1.0 - 1e-12)) break;
       }
     }
-    for (int s = 0; s < k; ++s) idx[s * ld + i] = bi[s];
+    for (int s = 0; s < k; ++s) idx[(s + off) * ld + i] = bi[s];
   }
 }
 
 }  // namespace
 
 int knn_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
-              const double* by, int64_t nb, int k, int32_t* idx, int64_t ld, cudaStream_t st) {
+              const double* by, int64_t nb, const uint8_t* beta_mask,
+              const int32_t* alpha_self, int k, int32_t* idx, int64_t ld, cudaStream_t st) {
   const int sms = sm_count();
   // --- bounding box
   const int bb_blocks = 64;  // partials fit the pinned status buffer
@@ -296,16 +310,18 @@ int knn_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, co
   rc = check_cuda(ctx, cudaMemsetAsync(d_cnt, 0, sizeof(int) * (cells + 1), st), "memset");
   if (rc) return rc;
   const int gblocks = 4 * sms;
-  bucket_count<<<gblocks, 256, 0, st>>>(bx, by, nb, g, d_cid, d_cnt);
+  bucket_count<<<gblocks, 256, 0, st>>>(bx, by, nb, beta_mask, g, d_cid, d_cnt);
   scan_blocks<<<scan_blocks_n, kScanBlock, 0, st>>>(d_cnt, d_start, cells, d_tot);
   scan_totals<<<1, kScanBlock, 0, st>>>(d_tot, scan_blocks_n);
   scan_add<<<scan_blocks_n, kScanBlock, 0, st>>>(d_start, cells, d_tot, d_cur, cells, (int)nb);
   bucket_scatter<<<gblocks, 256, 0, st>>>(nb, d_cid, d_cur, d_pts);
   const int qblocks = (int)std::min<int64_t>((na + 127) / 128, (int64_t)sms * 32);
   if (k <= 32)
-    knn_query<32><<<qblocks, 128, 0, st>>>(ax, ay, na, bx, by, d_start, d_pts, g, k, idx, ld);
+    knn_query<32><<<qblocks, 128, 0, st>>>(ax, ay, na, bx, by, d_start, d_pts, g, k, alpha_self,
+                                           idx, ld);
   else
-    knn_query<64><<<qblocks, 128, 0, st>>>(ax, ay, na, bx, by, d_start, d_pts, g, k, idx, ld);
+    knn_query<64><<<qblocks, 128, 0, st>>>(ax, ay, na, bx, by, d_start, d_pts, g, k, alpha_self,
+                                           idx, ld);
   return check_cuda(ctx, cudaGetLastError(), "knn kernels");
 }
 

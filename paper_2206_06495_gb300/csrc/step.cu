@@ -714,31 +714,65 @@ __global__ void __launch_bounds__(kThreads) k_correct(CorrArgs a) {
 }
 
 // --------------------------------------------------------------- set-up
-// Scaled pressure operator: Lw = S L, es = -S e (see the file comment)
+// Row map of the one-sided Neumann operator: bmap[P-node] = its Neumann row.
+// Rows outside [0, M) or repeated nodes raise the error flag.
+__global__ void k_scatter_rows(int64_t nb, int64_t M, const int32_t* __restrict__ rows,
+                               int32_t* __restrict__ bmap, int* __restrict__ err) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[b];
+    if (r < 0 || r >= M) {
+      atomicOr(err, 1);
+      continue;
+    }
+    if (atomicCAS(&bmap[r], -1, (int32_t)b) != -1) atomicOr(err, 1);
+  }
+}
+
+// Scaled pressure operator (see the file comment): Lidx/Lw = rows of L
+// (interior: D^(P,P)_Lap on pp_idx; boundary: n_x D_x + n_y D_y on the
+// one-sided stencil pn_idx), each divided by its diagonal; es = -S e.
 __global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __restrict__ idx,
-                                const double* __restrict__ lap, const double* __restrict__ dx,
-                                const double* __restrict__ dy, const uint8_t* __restrict__ p_bc,
+                                const double* __restrict__ lap, const uint8_t* __restrict__ p_bc,
+                                const int32_t* __restrict__ bmap, int64_t ld_b,
+                                const int32_t* __restrict__ pn_idx,
+                                const double* __restrict__ pn_dx, const double* __restrict__ pn_dy,
                                 const double* __restrict__ nx, const double* __restrict__ ny,
-                                double* __restrict__ Lw, double* __restrict__ es,
-                                double* __restrict__ scale) {
+                                int32_t* __restrict__ Lidx, double* __restrict__ Lw,
+                                double* __restrict__ es, double* __restrict__ scale,
+                                int* __restrict__ err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool bnd = p_bc[i] != 0;
+    const int32_t b = bnd ? bmap[i] : -1;
+    if (bnd && b < 0) {  // a boundary node without a Neumann row
+      atomicOr(err, 2);
+      for (int s = 0; s < k; ++s) {
+        Lidx[s * ld + i] = (int32_t)i;
+        Lw[s * ld + i] = s == 0 ? 1.0 : 0.0;
+      }
+      es[i] = 0.0;
+      scale[i] = 1.0;
+      continue;
+    }
     double diag = 0.0, sabs = 0.0;
     for (int s = 0; s < k; ++s) {
-      const double w = bnd ? nx[i] * dx[s * ld + i] + ny[i] * dy[s * ld + i] : lap[s * ld + i];
+      int32_t c;
+      double w;
+      if (bnd) {
+        c = pn_idx[s * ld_b + b];
+        w = nx[i] * pn_dx[s * ld_b + b] + ny[i] * pn_dy[s * ld_b + b];
+      } else {
+        c = idx[s * ld + i];
+        w = lap[s * ld + i];
+      }
       sabs += fabs(w);
-      if (idx[s * ld + i] == (int32_t)i) diag += w;
+      if (c == (int32_t)i) diag += w;
+      Lidx[s * ld + i] = c;
+      Lw[s * ld + i] = w;
     }
-    double sc;
-    if (bnd || diag == 0.0)
-      sc = sabs > 0.0 ? 1.0 / sabs : 1.0;
-    else
-      sc = 1.0 / diag;
-    for (int s = 0; s < k; ++s) {
-      const double w = bnd ? nx[i] * dx[s * ld + i] + ny[i] * dy[s * ld + i] : lap[s * ld + i];
-      Lw[s * ld + i] = sc * w;
-    }
+    const double sc = diag != 0.0 ? 1.0 / diag : (sabs > 0.0 ? 1.0 / sabs : 1.0);
+    for (int s = 0; s < k; ++s) Lw[s * ld + i] *= sc;
     es[i] = bnd ? 0.0 : -sc;
     scale[i] = sc;
   }
@@ -778,6 +812,9 @@ struct StepPlan {
   bool mix = false;
   std::vector<void*> allocs;
   // derived operators
+  int32_t* Lidx = nullptr;
+  int32_t* bmap = nullptr;
+  int* err = nullptr;
   double *Lw = nullptr, *es = nullptr, *scale = nullptr, *Hw = nullptr;
   float *Lw32 = nullptr, *es32 = nullptr, *Hw32 = nullptr;
   float *vv_dx32 = nullptr, *vv_dy32 = nullptr, *vv_lap32 = nullptr, *pv_dx32 = nullptr,
@@ -853,6 +890,9 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     }                            \
   } while (0)
   TRY(palloc(ctx, p, &p->Lw, np));
+  TRY(palloc(ctx, p, &p->Lidx, np));
+  TRY(palloc(ctx, p, &p->bmap, f.M));
+  TRY(palloc(ctx, p, &p->err, 1));
   TRY(palloc(ctx, p, &p->es, f.M));
   TRY(palloc(ctx, p, &p->scale, f.M));
   TRY(palloc(ctx, p, &p->Hw, nv));
@@ -872,14 +912,30 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   TRY(palloc(ctx, p, &p->gr.counter, 1));
   TRY(check_cuda(ctx, cudaMemsetAsync(p->gr.counter, 0, sizeof(unsigned int), st), "memset"));
   const double a = f.dt / (2.0 * f.Re);
-  k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.pp_dx,
-                                                 f.pp_dy, f.p_bc, f.p_nx, f.p_ny, p->Lw, p->es,
-                                                 p->scale);
+  TRY(check_cuda(ctx, cudaMemsetAsync(p->err, 0, sizeof(int), st), "memset"));
+  TRY(check_cuda(ctx, cudaMemsetAsync(p->bmap, 0xff, sizeof(int32_t) * f.M, st), "memset"));
+  k_scatter_rows<<<p->grid, kThreads, 0, st>>>(f.nb_p, f.M, f.pn_rows, p->bmap, p->err);
+  k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.p_bc,
+                                                 p->bmap, f.ld_b, f.pn_idx, f.pn_dx, f.pn_dy,
+                                                 f.p_nx, f.p_ny, p->Lidx, p->Lw, p->es,
+                                                 p->scale, p->err);
   // normalise the rank-one column so that the constant mode has eigenvalue 1
   k_sum<double><<<p->grid, kThreads, 0, st>>>(p->es, f.M, p->gr, p->dscal);
   k_scale_by_inv_abs<<<p->grid, kThreads, 0, st>>>(f.M, p->es, p->dscal);
   k_build_helm<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bc, a, p->Hw);
   TRY(check_cuda(ctx, cudaGetLastError(), "plan kernels"));
+  {
+    int herr = 0;
+    TRY(check_cuda(ctx, cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st),
+                   "plan status"));
+    TRY(check_cuda(ctx, cudaStreamSynchronize(st), "plan sync"));
+    if (herr) {
+      step_plan_free(p);
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                       "Neumann rows (pn_rows) must list every boundary P-node once (code %d)",
+                       herr);
+    }
+  }
   if (p->mix) {
     TRY(to32(ctx, p, p->Lw, np, &p->Lw32, st));
     TRY(to32(ctx, p, p->es, f.M, &p->es32, st));
@@ -1147,9 +1203,9 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     }
   }
   KOp<double, double> H64{f.vv_idx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
-  KOp<double, double> L64{f.pp_idx, P->Lw, f.ld_p, f.M, k, 0, P->es};
+  KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, k, 0, P->es};
   KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr};
-  KOp<float, float> L32{f.pp_idx, P->Lw32, f.ld_p, f.M, k, 0, P->es32};
+  KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es32};
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
                 P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,

@@ -59,6 +59,8 @@ class FlowC(C.Structure):
                 ("vp_idx", C.c_void_p), ("vp_dx", C.c_void_p), ("vp_dy", C.c_void_p),
                 ("v_bc", C.c_void_p), ("v_nx", C.c_void_p), ("v_ny", C.c_void_p),
                 ("p_bc", C.c_void_p), ("p_nx", C.c_void_p), ("p_ny", C.c_void_p),
+                ("nb_p", C.c_int64), ("ld_b", C.c_int64), ("pn_rows", C.c_void_p),
+                ("pn_idx", C.c_void_p), ("pn_dx", C.c_void_p), ("pn_dy", C.c_void_p),
                 ("Re", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("max_iter", C.c_int32),
                 ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32), ("profile", C.c_int32)]
@@ -92,6 +94,10 @@ PROTOTYPES = {
                                       C.c_void_p, C.c_void_p, C.c_int64, C.c_uint32,
                                       C.c_void_p, C.c_void_p, C.c_int64,
                                       C.POINTER(C.c_int64), C.c_void_p]),
+    "rbffd_build_weights_masked": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                             C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                             C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
+                                             C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "rbffd_apply_op": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "rbffd_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC), C.c_void_p,
@@ -192,6 +198,26 @@ def build_weights(ctx: Context, ax, ay, bx, by, op_mask: int, ld: int | None = N
     return idx, w, -1
 
 
+def build_weights_masked(ctx: Context, ax, ay, bx, by, op_mask: int, beta_mask=None,
+                         alpha_self=None, ld: int | None = None):
+    """rbffd_build_weights_masked (see build_weights); beta_mask uint8 [n_beta],
+    alpha_self int32 [n_alpha], either may be None."""
+    torch = _torch()
+    na = ax.numel()
+    ld = round_up(max(na, 1)) if ld is None else ld
+    nops = len(ops_of(op_mask))
+    idx = torch.empty((ctx.n, ld), dtype=torch.int32, device=ax.device)
+    w = torch.empty((nops, ctx.n, ld), dtype=torch.float64, device=ax.device)
+    bad = C.c_int64(-1)
+    rc = lib().rbffd_build_weights_masked(ctx.handle, _ptr(ax), _ptr(ay), na, _ptr(bx), _ptr(by),
+                                          bx.numel(), _ptr(beta_mask), _ptr(alpha_self), op_mask,
+                                          _ptr(idx), _ptr(w), ld, C.byref(bad), _stream())
+    if rc == ERR_SINGULAR_STENCIL:
+        return idx, w, int(bad.value)
+    ctx.check(rc)
+    return idx, w, -1
+
+
 def apply_op(ctx: Context, idx, w, n_rows: int, n_cols: int, x, y=None, alpha: float = 1.0,
              beta: float = 0.0):
     """rbffd_apply_op: y = alpha * D x + beta * y.  w: [n, ld] float64 or float32."""
@@ -233,6 +259,8 @@ class Flow:
                      vp_idx=p("vp_idx"), vp_dx=p("vp_dx"), vp_dy=p("vp_dy"),
                      v_bc=p("v_bc"), v_nx=p("v_nx"), v_ny=p("v_ny"),
                      p_bc=p("p_bc"), p_nx=p("p_nx"), p_ny=p("p_ny"),
+                     nb_p=t["pn_rows"].numel(), ld_b=t["pn_idx"].shape[1],
+                     pn_rows=p("pn_rows"), pn_idx=p("pn_idx"), pn_dx=p("pn_dx"), pn_dy=p("pn_dy"),
                      Re=self.Re, dt=self.dt, precision=self.precision, tol=self.tol,
                      inner_tol=self.inner_tol, max_iter=self.max_iter, km_mode=self.km_mode,
                      overwrite_bc=self.overwrite_bc, profile=self.profile)
@@ -263,6 +291,16 @@ def flow_from_nodes(ctx: Context, nodes, Re: float, dt: float, device="cuda", **
     if bad >= 0:
         raise RbffdError(ERR_SINGULAR_STENCIL, f"P->V stencil {bad}")
     t["vp_idx"], t["vp_dx"], t["vp_dy"] = i, w[0], w[1]
+    # one-sided Neumann stencils of boundary P-nodes: the node, then its
+    # nearest interior P-nodes
+    bnd = np.nonzero(nodes.p_boundary)[0]
+    rows = d(bnd.astype(np.int32))
+    interior = d((~nodes.p_boundary).astype(np.uint8))
+    i, w, bad = build_weights_masked(ctx, px[rows.long()], py[rows.long()], px, py,
+                                     OP_DX | OP_DY, beta_mask=interior, alpha_self=rows)
+    if bad >= 0:
+        raise RbffdError(ERR_SINGULAR_STENCIL, f"Neumann stencil {bad}")
+    t["pn_rows"], t["pn_idx"], t["pn_dx"], t["pn_dy"] = rows, i, w[0].contiguous(), w[1].contiguous()
     t["v_bc"] = d(nodes.v_boundary.astype(np.uint8))
     t["v_nx"], t["v_ny"] = d(nodes.v_nx), d(nodes.v_ny)
     t["p_bc"] = d(nodes.p_boundary.astype(np.uint8))

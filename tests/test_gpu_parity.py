@@ -90,6 +90,37 @@ def test_weights_other_params(R):
             assert rel.max() < 1e-9, (n, m, q, op, rel.max())
 
 
+def test_masked_one_sided_stencils_match_oracle(R, ctx):
+    """Boundary P-nodes: slot 0 = the node, then its 27 nearest interior P-nodes."""
+    nd = ns.jittered_cavity(15, 8)
+    bnd = np.nonzero(nd.p_boundary)[0]
+    rows = _d(bnd.astype(np.int32))
+    idx, w, bad = R.build_weights_masked(ctx, _d(nd.px[bnd]), _d(nd.py[bnd]), _d(nd.px),
+                                         _d(nd.py), R.OP_DX | R.OP_DY,
+                                         beta_mask=_d((~nd.p_boundary).astype(np.uint8)),
+                                         alpha_self=rows)
+    assert bad == -1
+    gi = idx.cpu().numpy()[:, : bnd.size].T.astype(np.int64)
+    ref = O.knn(nd.px[bnd], nd.py[bnd], nd.px, nd.py, 28, beta_mask=~nd.p_boundary,
+                alpha_self=bnd)
+    assert np.array_equal(gi, ref)
+    _, W = O.build_weights(nd.px[bnd], nd.py[bnd], nd.px, nd.py, 28, 7, 3, (O.OP_DX, O.OP_DY),
+                           idx=ref)
+    for o, op in enumerate((O.OP_DX, O.OP_DY)):
+        got = w[o].cpu().numpy()[:, : bnd.size].T
+        assert (np.abs(got - W[op]).max(1) / np.abs(W[op]).max(1)).max() < 1e-10
+
+
+def test_masked_rejects_too_few_candidates(R, ctx):
+    nd = ns.jittered_cavity(6, 9)  # 36 P-nodes, 16 interior
+    bnd = np.nonzero(nd.p_boundary)[0]
+    with pytest.raises(R.RbffdError) as e:
+        R.build_weights_masked(ctx, _d(nd.px[bnd]), _d(nd.py[bnd]), _d(nd.px), _d(nd.py),
+                               R.OP_DX, beta_mask=_d((~nd.p_boundary).astype(np.uint8)),
+                               alpha_self=_d(bnd.astype(np.int32)))
+    assert e.value.code == R.ERR_INVALID_ARG
+
+
 def test_singular_stencil_reported(R, ctx):
     """Duplicate beta-nodes make the systems that contain both singular."""
     nd = ns.jittered_cavity(10, 6)

@@ -250,23 +250,28 @@ def test_taylor_green_time_refinement():
     assert np.all(errs[:-1] / errs[1:] > 1.8), errs
 
 
-def test_projection_reduces_divergence(ops20):
-    """P7 / R13: after the correction the interior divergence is far below
-    that of the intermediate field, and shrinks under refinement."""
+def test_projection_reduces_divergence():
+    """P7 / R13: on the smooth Taylor-Green flow the correction removes most of
+    the divergence of the intermediate field, increasingly so under refinement
+    (the projection is not exact because D^(P,P)_Lap differs from
+    D^(P,V) D^(V,P))."""
+    Re, dt = 10.0, 0.005
     ratios = []
-    for n in (20, 40):
-        nd = ns.jittered_cavity(n, 0)
-        fs = O.FractionalStep(nd, Re=100.0, dt=2e-3)
-        st = fs.initial_state()
-        gu, gv = O.lid_bc(nd)
-        for _ in range(20):
+    for n in (17, 33):
+        nd = ns.jittered_cavity(n, 0, length=np.pi)
+        fs = O.FractionalStep(nd, Re=Re, dt=dt)
+        u0, v0, _ = _tg(nd.vx, nd.vy, 0.0, Re)
+        st = fs.initial_state(u0, v0)
+        for j in range(5):
+            gu, gv, _ = _tg(nd.vx, nd.vy, (j + 1) * dt, Re)
             st = fs.step(st, gu, gv)
+        gu, gv, _ = _tg(nd.vx, nd.vy, 6 * dt, Re)
         _, _, uss, vss, F = fs.intermediate(st, gu, gv)
         st2 = fs.step(st, gu, gv)
         inner = ~nd.p_boundary
         div = fs.ops.pv_x @ st2.u + fs.ops.pv_y @ st2.v
         ratios.append(np.linalg.norm(div[inner]) / np.linalg.norm(F[inner]))
-    assert ratios[0] < 0.6 and ratios[1] < 0.6 * ratios[0], ratios
+    assert ratios[0] < 0.2 and ratios[1] < 0.5 * ratios[0], ratios
 
 
 def test_bordered_poisson_compatible_rhs_has_zero_multiplier(ops20, cavity20):
