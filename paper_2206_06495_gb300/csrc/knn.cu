@@ -131,14 +131,15 @@ __global__ void scan_totals(int* block_tot, int nblocks) {
 }
 
 __global__ void scan_add(int* __restrict__ out, int n, const int* __restrict__ block_off,
-                         int* __restrict__ cursor, int total_cells, int nb) {
+                         int* __restrict__ cursor, const int* __restrict__ counts) {
   int i = blockIdx.x * kScanBlock + threadIdx.x;
   if (i < n) {
     int v = out[i] + block_off[blockIdx.x];
     out[i] = v;
     cursor[i] = v;
+    // sentinel: end of the last cell = number of bucketed (unmasked) points
+    if (i == n - 1) out[n] = v + counts[i];
   }
-  if (i == 0) out[total_cells] = nb;  // sentinel end of the last cell
 }
 
 __global__ void bucket_scatter(int64_t nb, const int* __restrict__ cell_id,
@@ -313,7 +314,7 @@ int knn_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, co
   bucket_count<<<gblocks, 256, 0, st>>>(bx, by, nb, beta_mask, g, d_cid, d_cnt);
   scan_blocks<<<scan_blocks_n, kScanBlock, 0, st>>>(d_cnt, d_start, cells, d_tot);
   scan_totals<<<1, kScanBlock, 0, st>>>(d_tot, scan_blocks_n);
-  scan_add<<<scan_blocks_n, kScanBlock, 0, st>>>(d_start, cells, d_tot, d_cur, cells, (int)nb);
+  scan_add<<<scan_blocks_n, kScanBlock, 0, st>>>(d_start, cells, d_tot, d_cur, d_cnt);
   bucket_scatter<<<gblocks, 256, 0, st>>>(nb, d_cid, d_cur, d_pts);
   const int qblocks = (int)std::min<int64_t>((na + 127) / 128, (int64_t)sms * 32);
   if (k <= 32)

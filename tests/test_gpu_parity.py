@@ -90,9 +90,10 @@ def test_weights_other_params(R):
             assert rel.max() < 1e-9, (n, m, q, op, rel.max())
 
 
-def test_masked_one_sided_stencils_match_oracle(R, ctx):
+@pytest.mark.parametrize("n", [15, 20, 37])
+def test_masked_one_sided_stencils_match_oracle(R, ctx, n):
     """Boundary P-nodes: slot 0 = the node, then its 27 nearest interior P-nodes."""
-    nd = ns.jittered_cavity(15, 8)
+    nd = ns.jittered_cavity(n, 8)
     bnd = np.nonzero(nd.p_boundary)[0]
     rows = _d(bnd.astype(np.int32))
     idx, w, bad = R.build_weights_masked(ctx, _d(nd.px[bnd]), _d(nd.py[bnd]), _d(nd.px),
