@@ -204,12 +204,12 @@ def run_ours(args):
             continue
         if not flows:
             base = R.flow_from_nodes(ctx, nd, Re=args.re, dt=args.dt, precision=prec,
-                                     tol=args.tol, inner_tol=1e-3, max_iter=args.max_iter)
+                                     tol=args.tol, inner_tol=1e-2, max_iter=args.max_iter)
             flows[name] = base
         else:
             b0 = next(iter(flows.values()))
             flows[name] = R.Flow(N=b0.N, M=b0.M, tensors=b0.tensors, Re=args.re, dt=args.dt,
-                                 precision=prec, tol=args.tol, inner_tol=1e-3,
+                                 precision=prec, tol=args.tol, inner_tol=1e-2,
                                  max_iter=args.max_iter)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup

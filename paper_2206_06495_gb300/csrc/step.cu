@@ -37,6 +37,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNV = 6;  // values reduced per kernel
+// Iterations of one FP32 inner solve before the refinement loop restarts it
+// from the FP64 residual (bounds the drift of the FP32 recurrences).
+constexpr int kInnerCap = 600;
 
 // RBFFD_TRACE=1 in the environment prints one line per solve and refinement
 // sweep to stderr (iterations, residuals, status).
@@ -1161,7 +1164,8 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     P->launches += 2;  // with the correction below
     SolveResult inner;
     rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
-                                                maxit - used, &inner, st, prof, retries);
+                                                std::min(maxit - used, kInnerCap), &inner, st,
+                                                prof, retries);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;

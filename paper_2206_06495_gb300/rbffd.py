@@ -242,7 +242,7 @@ class Flow:
     dt: float
     precision: int = PREC_FP64
     tol: float = 1e-12
-    inner_tol: float = 1e-3
+    inner_tol: float = 1e-2
     max_iter: int = 20000
     km_mode: int = 1
     overwrite_bc: int = 1
