@@ -114,9 +114,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_traffic(kernel_key: str):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+def profiled_traffic(kernel_key: str, rows: int):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, scaled
+    to `rows`, or None when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     src = os.path.join(ROOT, "paper_2206_06495_gb300", "csrc", "step.cu")
     try:
@@ -124,7 +124,7 @@ def profiled_traffic(kernel_key: str):
         for line in open(path):
             line = line.split("#")[0].split()
             if len(line) >= 4 and line[0] == kernel_key and line[3] == sha:
-                return float(line[1]) / float(line[2])
+                return float(line[1]) / float(line[2]) * rows
     except OSError:
         pass
     return None
@@ -329,7 +329,7 @@ def run_ours(args):
         bytes_row, key = 12 * k + 32, "k_spmv_fp64_rank1"
     per_launch_ms = agg["spmv_ms"] / max(agg["spmv_launches"], 1)
     achieved = nd.M * bytes_row / (per_launch_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(key)
+    traffic = profiled_traffic(key, nd.M)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
