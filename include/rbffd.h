@@ -128,6 +128,27 @@ int rbffd_build_weights_masked(rbffd_ctx* ctx, const double* ax, const double* a
                                const int32_t* alpha_self, uint32_t op_mask, int32_t* idx,
                                double* w, int64_t ld, int64_t* bad_node, cudaStream_t stream);
 
+/*
+ * rbffd_build_weights_noalloc - rbffd_build_weights for callers that cannot
+ * allocate GPU memory (for instance code inside a host framework that owns the
+ * whole device memory pool, or a loop with a fixed memory budget that cannot
+ * pay for cudaMalloc/cudaFree).  The paper has no counterpart; this is a
+ * deployment variant of the same computation and returns the same idx and w.
+ * It takes no context and allocates nothing: its k-NN buckets and status
+ * word live in a 2 MiB device array that every GPU loading the library holds
+ * until the process exits.  The first call on each device looks up that
+ * array's device address (make that first call before any stream capture).
+ * p may be NULL for (28, 7, 3).  n_beta may not exceed 65,536 (INVALID_ARG
+ * beyond).  Every call uses the same array and overwrites what the previous
+ * call left there; calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Errors are
+ * returned as codes only (no message).  Synchronises `stream`.
+ */
+int rbffd_build_weights_noalloc(const rbffd_params* p, const double* ax, const double* ay,
+                                int64_t n_alpha, const double* bx, const double* by,
+                                int64_t n_beta, uint32_t op_mask, int32_t* idx, double* w,
+                                int64_t ld, int64_t* bad_node, cudaStream_t stream);
+
 /* One ELL operator (see the conventions above). */
 typedef struct rbffd_ell {
   const int32_t* idx; /* int32[n * ld]                                       */

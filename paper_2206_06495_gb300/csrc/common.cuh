@@ -127,5 +127,14 @@ int spmv_apply(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, doubl
 int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st);
 void step_plan_free(struct StepPlan* p);
+// allocation-free variants on caller-provided device scratch (status codes only)
+size_t knn_scratch_bytes(int64_t nb, int64_t max_cells);
+int knn_build_scratch(const double* ax, const double* ay, int64_t na, const double* bx,
+                      const double* by, int64_t nb, int k, int32_t* idx, int64_t ld,
+                      void* scratch, size_t scratch_bytes, int64_t max_cells, cudaStream_t st);
+int weights_build_scratch(int n, int m, int q, const double* ax, const double* ay, int64_t na,
+                          const double* bx, const double* by, const int32_t* idx, int64_t ld,
+                          uint32_t op_mask, double* w, unsigned long long* d_bad,
+                          int64_t* bad_node, cudaStream_t st);
 
 }  // namespace rbffd

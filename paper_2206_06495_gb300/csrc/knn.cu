@@ -327,3 +327,102 @@ int knn_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, co
 }
 
 }  // namespace rbffd
+
+namespace rbffd {
+
+// Scratch bytes the search below needs for n_beta beta-nodes when the bucket
+// grid is limited to max_cells cells.
+size_t knn_scratch_bytes(int64_t nb, int64_t max_cells) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const int64_t scan_blocks_n = (max_cells + kScanBlock - 1) / kScanBlock;
+  return up(sizeof(double) * 4 * 64) + up(sizeof(int) * nb) + 2 * up(sizeof(int) * (max_cells + 1)) +
+         up(sizeof(int) * max_cells) + up(sizeof(int) * nb) + up(sizeof(int) * (scan_blocks_n + 1));
+}
+
+// The stencil search of knn_build on caller-provided device scratch: no
+// allocation, no context.  The bucket grid is coarsened until it has at most
+// max_cells cells (the result does not depend on the grid).  Returns an
+// RBFFD status code.
+int knn_build_scratch(const double* ax, const double* ay, int64_t na, const double* bx,
+                      const double* by, int64_t nb, int k, int32_t* idx, int64_t ld,
+                      void* scratch, size_t scratch_bytes, int64_t max_cells, cudaStream_t st) {
+  const int sms = sm_count();
+  const int bb_blocks = 64;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  char* b = (char*)scratch;
+  const size_t o_bb = carve(sizeof(double) * 4 * bb_blocks);
+  double* d_bb = (double*)(b + o_bb);
+  bbox_partial<<<bb_blocks, 256, 0, st>>>(ax, ay, na, bx, by, nb, d_bb);
+  double h_bb[4 * 64];
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h_bb, d_bb, sizeof(h_bb), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RBFFD_ERR_CUDA;
+  double x0 = DBL_MAX, y0 = DBL_MAX, x1 = -DBL_MAX, y1 = -DBL_MAX;
+  for (int q = 0; q < bb_blocks; ++q) {
+    x0 = fmin(x0, h_bb[4 * q + 0]);
+    y0 = fmin(y0, h_bb[4 * q + 1]);
+    x1 = fmax(x1, h_bb[4 * q + 2]);
+    y1 = fmax(y1, h_bb[4 * q + 3]);
+  }
+  if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(x1) || !std::isfinite(y1))
+    return RBFFD_ERR_NONFINITE;
+  double w = x1 - x0, h = y1 - y0;
+  const double span = fmax(fmax(w, h), 1e-300);
+  if (w < 1e-9 * span) w = 1e-9 * span;
+  if (h < 1e-9 * span) h = 1e-9 * span;
+  double cell = sqrt(w * h * 2.0 / (double)nb);
+  Grid g;
+  for (;;) {
+    const double gx = ceil(w / cell), gy = ceil(h / cell);
+    if (gx * gy <= (double)max_cells && gx < 1e8 && gy < 1e8) {
+      g.gx = (int)fmax(gx, 1.0);
+      g.gy = (int)fmax(gy, 1.0);
+      break;
+    }
+    cell *= 1.5;
+  }
+  g.x0 = x0;
+  g.y0 = y0;
+  g.cell = cell;
+  g.inv_cell = 1.0 / cell;
+  const int cells = g.gx * g.gy;
+  const int scan_blocks_n = (cells + kScanBlock - 1) / kScanBlock;
+  const size_t o_cid = carve(sizeof(int) * nb);
+  const size_t o_cnt = carve(sizeof(int) * (cells + 1));
+  const size_t o_start = carve(sizeof(int) * (cells + 1));
+  const size_t o_cur = carve(sizeof(int) * cells);
+  const size_t o_pts = carve(sizeof(int) * nb);
+  const size_t o_tot = carve(sizeof(int) * (scan_blocks_n + 1));
+  if (off > scratch_bytes) return RBFFD_ERR_INVALID_ARG;
+  int* d_cid = (int*)(b + o_cid);
+  int* d_cnt = (int*)(b + o_cnt);
+  int* d_start = (int*)(b + o_start);
+  int* d_cur = (int*)(b + o_cur);
+  int* d_pts = (int*)(b + o_pts);
+  int* d_tot = (int*)(b + o_tot);
+  // the scratch keeps the previous call's contents: the counters start at zero
+  if (cudaMemsetAsync(d_cnt, 0, sizeof(int) * (cells + 1), st) != cudaSuccess)
+    return RBFFD_ERR_CUDA;
+  const int gblocks = 4 * sms;
+  bucket_count<<<gblocks, 256, 0, st>>>(bx, by, nb, nullptr, g, d_cid, d_cnt);
+  scan_blocks<<<scan_blocks_n, kScanBlock, 0, st>>>(d_cnt, d_start, cells, d_tot);
+  scan_totals<<<1, kScanBlock, 0, st>>>(d_tot, scan_blocks_n);
+  scan_add<<<scan_blocks_n, kScanBlock, 0, st>>>(d_start, cells, d_tot, d_cur, d_cnt);
+  bucket_scatter<<<gblocks, 256, 0, st>>>(nb, d_cid, d_cur, d_pts);
+  const int qblocks = (int)std::min<int64_t>((na + 127) / 128, (int64_t)sms * 32);
+  if (k <= 32)
+    knn_query<32><<<qblocks, 128, 0, st>>>(ax, ay, na, bx, by, d_start, d_pts, g, k, nullptr,
+                                           idx, ld);
+  else
+    knn_query<64><<<qblocks, 128, 0, st>>>(ax, ay, na, bx, by, d_start, d_pts, g, k, nullptr,
+                                           idx, ld);
+  return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ERR_CUDA;
+}
+
+}  // namespace rbffd

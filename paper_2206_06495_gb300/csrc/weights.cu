@@ -261,3 +261,49 @@ int weights_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na
 }
 
 }  // namespace rbffd
+
+namespace rbffd {
+
+// The weight solves of weights_build with the singular-stencil status word in
+// caller-provided device memory (no context, no allocation).  Returns an
+// RBFFD status code; bad_node (host, may be null) as in weights_build.
+int weights_build_scratch(int n, int m, int q, const double* ax, const double* ay, int64_t na,
+                          const double* bx, const double* by, const int32_t* idx, int64_t ld,
+                          uint32_t op_mask, double* w, unsigned long long* d_bad,
+                          int64_t* bad_node, cudaStream_t st) {
+  const int np = q < 0 ? 0 : (q + 1) * (q + 2) / 2;
+  const int S = n + np;
+  int opv[4] = {0, 0, 0, 0};
+  int nrhs = 0;
+  for (int b = 0; b < 4; ++b)
+    if (op_mask & (1u << b)) opv[nrhs++] = b;
+  const int LD = (S % 2) ? S : S + 1;
+  const size_t per_warp = sizeof(double) * ((size_t)LD * (S + nrhs) + 2 * kMaxStencil);
+  const int wpb =
+      (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / per_warp));
+  const size_t smem = per_warp * wpb;
+  if (cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return RBFFD_ERR_CUDA;
+  // the status word keeps the previous call's value: reset it
+  if (cudaMemsetAsync(d_bad, 0xff, sizeof(unsigned long long), st) != cudaSuccess)
+    return RBFFD_ERR_CUDA;
+  const int sms = sm_count();
+  const int64_t need = (na + wpb - 1) / wpb;
+  const int blocks = (int)std::min<int64_t>(need, (int64_t)sms * 16);
+  weights_kernel<<<blocks, wpb * 32, smem, st>>>(ax, ay, na, bx, by, idx, ld, n, m, q, nrhs,
+                                                 make_int4(opv[0], opv[1], opv[2], opv[3]), LD,
+                                                 w, d_bad);
+  unsigned long long h_bad = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RBFFD_ERR_CUDA;
+  if (h_bad != ~0ull) {
+    if (bad_node) *bad_node = (int64_t)h_bad;
+    return RBFFD_ERR_SINGULAR_STENCIL;
+  }
+  return RBFFD_OK;
+}
+
+}  // namespace rbffd

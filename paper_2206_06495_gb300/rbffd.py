@@ -98,6 +98,10 @@ PROTOTYPES = {
                                              C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                              C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                                              C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
+    "rbffd_build_weights_noalloc": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p,
+                                              C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
+                                              C.c_uint32, C.c_void_p, C.c_void_p, C.c_int64,
+                                              C.POINTER(C.c_int64), C.c_void_p]),
     "rbffd_apply_op": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "rbffd_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC), C.c_void_p,
