@@ -880,7 +880,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   p->N = f.N;
   p->M = f.M;
   p->mix = f.precision == RBFFD_PREC_MIXED;
-  p->grid = sm_count() * 4;
+  p->grid = sm_count() * 8;  // 8 blocks of 256 per SM: full occupancy at 32 registers
   const int64_t nv = f.ld_v * p->k, np = f.ld_p * p->k;
   const int64_t nmax = f.N > f.M ? f.N : f.M;
   int rc = 0;
