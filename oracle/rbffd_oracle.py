@@ -363,6 +363,20 @@ class FractionalStep:
         self.Pb = poisson_matrix(self.ops, self.pb, nodes.p_nx, nodes.p_ny)
         self.H_lu = spla.splu(self.H)
         self.P_lu = spla.splu(self.Pb)
+        self._HT_lu = None
+        self._PT_lu = None
+
+    @property
+    def HT_lu(self):
+        if self._HT_lu is None:
+            self._HT_lu = spla.splu(self.H.T.tocsc())
+        return self._HT_lu
+
+    @property
+    def PT_lu(self):
+        if self._PT_lu is None:
+            self._PT_lu = spla.splu(self.Pb.T.tocsc())
+        return self._PT_lu
 
     def initial_state(self, u0=None, v0=None) -> FlowState:
         N, M = self.nodes.N, self.nodes.M
@@ -416,6 +430,90 @@ class FractionalStep:
         vss = self.H_lu.solve(rv)
         F = o.pv_x @ uss + o.pv_y @ vss
         return cu, cv, uss, vss, F
+
+
+@dataclass
+class AdjointState:
+    """Adjoint variables of a FlowState: dJ/du, dJ/dv, dJ/dC_{j-1}(u),
+    dJ/dC_{j-1}(v), dJ/dp~ (the pressure p is not fed back, so it has none)."""
+    u: np.ndarray
+    v: np.ndarray
+    cu_prev: np.ndarray
+    cv_prev: np.ndarray
+    pt: np.ndarray
+
+
+def adjoint_step(fs: "FractionalStep", st_in: FlowState, lam: AdjointState, km_mode: int = 1):
+    """Reverse-mode derivative of one step of FractionalStep.step.
+
+    st_in: the forward state the step started from (step j); lam: adjoints of
+    the step's outputs.  Returns (adjoints of the inputs, dJ/dgu, dJ/dgv) where
+    gu, gv are the wall data of the step.  Every transpose is the explicit
+    transpose of the oracle's CSR matrix; the transposed solves use the LU
+    factors of H^T and of the bordered matrix's transpose.
+    """
+    o, dt, a = fs.ops, fs.dt, fs.a
+    w = fs.vb
+    inner = ~w
+    N = st_in.u.size
+    lgu = np.zeros(N)
+    lgv = np.zeros(N)
+    lun = lam.u.copy()
+    lvn = lam.v.copy()
+    if fs.overwrite_bc:
+        lgu[w] += lun[w]
+        lgv[w] += lvn[w]
+        lun[w] = 0.0
+        lvn[w] = 0.0
+    # correction u_{j+1} = u** - dt G_x p~
+    luss = lun.copy()
+    lvss = lvn.copy()
+    lpt = lam.pt - dt * (o.vp_x.T @ lun + o.vp_y.T @ lvn)
+    # pressure solve: [p~; lam] = B^-1 [b; 0], b = F/dt inside, 0 on boundary rows
+    z = fs.PT_lu.solve(np.concatenate([lpt, [0.0]]))[:-1]
+    lF = np.where(fs.pb, 0.0, z / dt)
+    luss += o.pv_x.T @ lF
+    lvss += o.pv_y.T @ lF
+    # Crank-Nicolson solves u** = H^-1 r_u
+    lru = fs.HT_lu.solve(luss)
+    lrv = fs.HT_lu.solve(lvss)
+    lgu[w] += lru[w]
+    lgv[w] += lrv[w]
+    lpt_in = np.zeros_like(lam.pt)
+    if km_mode == 1:
+        mu = np.where(w, fs.tx * lru + fs.ty * lrv, 0.0) * dt
+        lpt_in += o.vp_x.T @ (fs.tx * mu) + o.vp_y.T @ (fs.ty * mu)
+    elif km_mode == 2:
+        lpt_in += dt * (o.vp_x.T @ np.where(w, lru, 0.0) + o.vp_y.T @ np.where(w, lrv, 0.0))
+    lri = np.where(inner, lru, 0.0)
+    lrvi = np.where(inner, lrv, 0.0)
+    lus = lri + a * (o.vv_lap.T @ lri)
+    lvs = lrvi + a * (o.vv_lap.T @ lrvi)
+    # Adams-Bashforth combination u* = u + dt (3/2 C_j - 1/2 C_{j-1})
+    lu = lus.copy()
+    lv = lvs.copy()
+    lcu = 1.5 * dt * lus + lam.cu_prev
+    lcv = 1.5 * dt * lvs + lam.cv_prev
+    if st_in.j == 0:
+        lcu += -0.5 * dt * lus
+        lcv += -0.5 * dt * lvs
+        lcup = np.zeros(N)
+        lcvp = np.zeros(N)
+    else:
+        lcup = -0.5 * dt * lus
+        lcvp = -0.5 * dt * lvs
+    # convection C(q) = -[u o D_x q + v o D_y q]
+    u, v = st_in.u, st_in.v
+    dxu, dyu = o.vv_x @ u, o.vv_y @ u
+    dxv, dyv = o.vv_x @ v, o.vv_y @ v
+    lu += -(dxu * lcu) - o.vv_x.T @ (u * lcu) - o.vv_y.T @ (v * lcu) - dxv * lcv
+    lv += -(dyu * lcu) - dyv * lcv - o.vv_x.T @ (u * lcv) - o.vv_y.T @ (v * lcv)
+    return AdjointState(u=lu, v=lv, cu_prev=lcup, cv_prev=lcvp, pt=lpt_in), lgu, lgv
+
+
+def kinetic_energy(st: FlowState) -> float:
+    """J = 1/2 sum over V-nodes of u^2 + v^2 (unweighted)."""
+    return 0.5 * float(st.u @ st.u + st.v @ st.v)
 
 
 def lid_bc(nodes, lid_u=1.0):

@@ -313,3 +313,86 @@ def test_cavity_runs_stably_and_keeps_wall_data(cavity20, ops20):
     vb = nd.v_boundary
     assert np.array_equal(st.u[vb], gu[vb]) and np.array_equal(st.v[vb], gv[vb])
     assert abs(st.pt.mean()) < 1e-12
+
+
+# ---------------------------------------------------------------- adjoint
+def _adj_setup(km_mode=1, seed=0):
+    nd = ns.jittered_cavity(12, 4)
+    fs = O.FractionalStep(nd, Re=400.0, dt=2e-3)
+    rng = np.random.default_rng(seed)
+    lid = nd.v_wall == ns.WALL_TOP
+    g0 = np.zeros(nd.N)
+    g0[lid] = 1 + 0.05 * rng.standard_normal(lid.sum())
+    u0 = np.zeros(nd.N)
+    inner = ~nd.v_boundary
+    u0[inner] = 0.01 * rng.standard_normal(inner.sum())
+    return nd, fs, g0, u0
+
+
+def _adj_run(fs, nd, gu, u0, steps):
+    st = fs.initial_state(u0, np.zeros(nd.N))
+    sts = [st]
+    for _ in range(steps):
+        st = fs.step(st, gu, np.zeros(nd.N))
+        sts.append(st)
+    return sts
+
+
+def test_adjoint_matches_central_differences():
+    """P9: gradients of J = 1/2 sum(u^2 + v^2) after 8 steps with respect to
+    per-node lid velocity and to the initial velocity, from the discrete
+    adjoint, against central differences of the forward solver (eps 1e-6)."""
+    nd, fs, g0, u0 = _adj_setup()
+    steps = 8
+    sts = _adj_run(fs, nd, g0, u0, steps)
+    lam = O.AdjointState(sts[-1].u.copy(), sts[-1].v.copy(), np.zeros(nd.N), np.zeros(nd.N),
+                         np.zeros(nd.M))
+    G = np.zeros(nd.N)
+    for j in range(steps - 1, -1, -1):
+        lam, lgu, _ = O.adjoint_step(fs, sts[j], lam)
+        G += lgu
+    eps = 1e-6
+    lid = np.nonzero(nd.v_wall == ns.WALL_TOP)[0][:3]
+    inner = np.nonzero(~nd.v_boundary)[0][[0, 7, 40]]
+    for k in lid:
+        gp, gm = g0.copy(), g0.copy()
+        gp[k] += eps
+        gm[k] -= eps
+        fd = (O.kinetic_energy(_adj_run(fs, nd, gp, u0, steps)[-1])
+              - O.kinetic_energy(_adj_run(fs, nd, gm, u0, steps)[-1])) / (2 * eps)
+        assert abs(G[k] - fd) <= 1e-6 * abs(fd), (k, G[k], fd)
+    for k in inner:
+        up, um = u0.copy(), u0.copy()
+        up[k] += eps
+        um[k] -= eps
+        fd = (O.kinetic_energy(_adj_run(fs, nd, g0, up, steps)[-1])
+              - O.kinetic_energy(_adj_run(fs, nd, g0, um, steps)[-1])) / (2 * eps)
+        assert abs(lam.u[k] - fd) <= 1e-6 * max(abs(fd), 1e-3), (k, lam.u[k], fd)
+
+
+def test_adjoint_dot_product_identity():
+    """<J_step dx, y> = <dx, J_step^T y> for the linearised step: perturb the
+    input state along a random direction, compare the change of a random
+    linear functional of the output with the adjoint's prediction."""
+    nd, fs, g0, u0 = _adj_setup(seed=3)
+    sts = _adj_run(fs, nd, g0, u0, 3)
+    st = sts[2]
+    rng = np.random.default_rng(9)
+    du = rng.standard_normal(nd.N) * (~nd.v_boundary)
+    dpt = rng.standard_normal(nd.M)
+    yu, yv = rng.standard_normal(nd.N), rng.standard_normal(nd.N)
+    ypt = rng.standard_normal(nd.M)
+
+    def functional(s):
+        out = fs.step(s, g0, np.zeros(nd.N))
+        return yu @ out.u + yv @ out.v + ypt @ out.pt
+
+    eps = 1e-6
+    sp_ = O.FlowState(st.u + eps * du, st.v, st.cu_prev, st.cv_prev, st.pt + eps * dpt, st.p,
+                      0.0, st.j)
+    sm_ = O.FlowState(st.u - eps * du, st.v, st.cu_prev, st.cv_prev, st.pt - eps * dpt, st.p,
+                      0.0, st.j)
+    fd = (functional(sp_) - functional(sm_)) / (2 * eps)
+    lam, _, _ = O.adjoint_step(fs, st, O.AdjointState(yu, yv, np.zeros(nd.N), np.zeros(nd.N), ypt))
+    pred = lam.u @ du + lam.pt @ dpt
+    assert abs(pred - fd) <= 1e-6 * abs(fd), (pred, fd)
