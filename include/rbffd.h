@@ -268,6 +268,33 @@ typedef struct rbffd_stats {
 int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const double* gu,
                const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream);
 
+/* Adjoint variables of a state (FP64 device arrays owned by the caller):
+ * dJ/du, dJ/dv (N), dJ/dC_{j-1}(u), dJ/dC_{j-1}(v) (N), dJ/dp~ (M). */
+typedef struct rbffd_adjoint {
+  double *u, *v, *cu_prev, *cv_prev, *pt;
+} rbffd_adjoint;
+
+/*
+ * rbffd_adjoint_step - reverse-mode derivative of one rbffd_step step (the
+ * discrete adjoint of Section 3's three stages under the same readings: Kim &
+ * Moin wall term per km_mode, wall overwrite, AB2 start, bordered pressure).
+ * fwd    the forward state the step started from (step j; only u, v and j are
+ *        read: the step is linear in everything else)
+ * lam    in: adjoints of the step's outputs (state j+1); out: adjoints of its
+ *        inputs (state j), in place
+ * grad_gu, grad_gv  device double[N]: the adjoint of the step's wall data
+ *        g_{j+1} is ADDED to them (wall entries only)
+ * The operators of the step are transposed once per flow description (kept in
+ * the context).  Transposed solves use the flow's tol and max_iter.  FP64.
+ * A training loop stores checkpoints of forward states and recomputes the
+ * states between them before walking backwards.  Errors: as rbffd_step.
+ * Synchronises `stream`; stats (HOST, may be NULL) receives the iteration
+ * counts of the transposed solves.
+ */
+int rbffd_adjoint_step(rbffd_ctx* ctx, const rbffd_flow* flow, const rbffd_state* fwd,
+                       rbffd_adjoint* lam, double* grad_gu, double* grad_gv, rbffd_stats* stats,
+                       cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

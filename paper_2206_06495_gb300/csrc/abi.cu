@@ -178,15 +178,9 @@ int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, d
   return spmv_apply(ctx, D, x, y, alpha, beta, xy_dtype, stream);
 }
 
-int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const double* gu,
-               const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream) {
-  if (!ctx) return RBFFD_ERR_INVALID_ARG;
-  ctx->err.clear();
-  if (stats) memset(stats, 0, sizeof(*stats));
-  if (!flow || !state || !gu || !gv)
-    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+static int check_flow(rbffd_ctx* ctx, const rbffd_flow* flow) {
+  if (!flow) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null flow");
   const rbffd_flow& f = *flow;
-  if (n_steps < 0) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "negative n_steps");
   if (f.N < ctx->prm.n || f.M < ctx->prm.n || f.ld_v < f.N || f.ld_p < f.M || f.ld_v % 32 ||
       f.ld_p % 32 || f.N > INT32_MAX || f.M > INT32_MAX || f.nb_p < 0 || f.nb_p > f.M ||
       (f.nb_p > 0 && (f.ld_b < f.nb_p || f.ld_b % 32)))
@@ -196,14 +190,44 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
       !f.v_bc || !f.v_nx || !f.v_ny || !f.p_bc || !f.p_nx || !f.p_ny ||
       (f.nb_p > 0 && (!f.pn_rows || !f.pn_idx || !f.pn_dx || !f.pn_dy)))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null operator or boundary array");
-  if (!state->u || !state->v || !state->cu_prev || !state->cv_prev || !state->pt || !state->p)
-    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
   if (!(f.Re > 0) || !(f.dt > 0) || !(f.tol > 0) || f.max_iter < 1 ||
       (f.precision != RBFFD_PREC_FP64 && f.precision != RBFFD_PREC_MIXED) || f.km_mode < 0 ||
       f.km_mode > 2 || (f.precision == RBFFD_PREC_MIXED && !(f.inner_tol > 0 && f.inner_tol < 1)))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad Re, dt, tolerances or modes");
+  return RBFFD_OK;
+}
+
+int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const double* gu,
+               const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!flow || !state || !gu || !gv)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  if (n_steps < 0) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "negative n_steps");
+  int rc = check_flow(ctx, flow);
+  if (rc) return rc;
+  if (!state->u || !state->v || !state->cu_prev || !state->cv_prev || !state->pt || !state->p)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
   if (n_steps == 0) return RBFFD_OK;
   return step_run(ctx, flow, state, gu, gv, n_steps, stats, stream);
+}
+
+int rbffd_adjoint_step(rbffd_ctx* ctx, const rbffd_flow* flow, const rbffd_state* fwd,
+                       rbffd_adjoint* lam, double* grad_gu, double* grad_gv, rbffd_stats* stats,
+                       cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!flow || !fwd || !lam || !grad_gu || !grad_gv)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  int rc = check_flow(ctx, flow);
+  if (rc) return rc;
+  if (!fwd->u || !fwd->v || fwd->j < 0)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad forward state");
+  if (!lam->u || !lam->v || !lam->cu_prev || !lam->cv_prev || !lam->pt)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null adjoint array");
+  return adjoint_run(ctx, flow, fwd, lam, grad_gu, grad_gv, stats, stream);
 }
 
 }  // extern "C"

@@ -127,6 +127,8 @@ int spmv_apply(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, doubl
 int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st);
 void step_plan_free(struct StepPlan* p);
+int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* f, const rbffd_state* s, rbffd_adjoint* lam,
+                double* grad_gu, double* grad_gv, rbffd_stats* stats, cudaStream_t st);
 // allocation-free variants on caller-provided device scratch (status codes only)
 size_t knn_scratch_bytes(int64_t nb, int64_t max_cells);
 int knn_build_scratch(const double* ax, const double* ay, int64_t na, const double* bx,

@@ -77,8 +77,9 @@ struct KOp {
   int64_t ld;
   int64_t n;
   int k;
-  int diag1;     // add x_i (identity part of H)
-  const TV* es;  // rank-one column, or null
+  int diag1;       // add x_i (identity part of H)
+  const TV* es;    // rank-one column, or null
+  const TV* rdot;  // rank-one row (y += es * (rdot . x)); null = all ones
 };
 
 template <typename T>
@@ -115,18 +116,21 @@ struct Vecs {
 };
 
 // ----------------------------------------------------------- Krylov kernels
+// sum_i x_i, or sum_i c_i x_i when c is given
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_sum(const TV* __restrict__ x, int64_t n,
-                                                  GridReduce gr, double* out) {
+                                                  GridReduce gr, double* out,
+                                                  const TV* __restrict__ c = nullptr) {
   __shared__ double sh[kNV * kThreads / 32];
   float part = 0.f;
   double partd = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
+    const TV xi = c ? c[i] * x[i] : x[i];
     if (sizeof(TV) == 8)
-      partd += (double)x[i];
+      partd += (double)xi;
     else
-      part += (float)x[i];
+      part += (float)xi;
   }
   double v[kNV] = {partd + (double)part, 0, 0, 0, 0, 0};
   grid_reduce<kNV>(v, gr, sh, [&](double* t) { *out = t[0]; });
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kThreads)
       prr[q] += ri * ri;
       pbb[q] += bi * bi;
       prh[q] += sgn * ri * ri;
-      if (RANK1) psum += ri;
+      if (RANK1) psum += op.rdot ? (A)op.rdot[i] * ri : ri;
     }
   }
   double v[kNV] = {(double)prr[0], (double)pbb[0], (double)prr[1],
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_s(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> v, Vecs<TV, NRHS> s, KScal* sc,
-               GridReduce gr) {
+               GridReduce gr, const TV* __restrict__ rdot) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kThreads)
       const A si = r.v[q][i] - al[q] * v.v[q][i];
       s.v[q][i] = si;
       pss[q] += si * si;
-      if (RANK1) psum += si;
+      if (RANK1) psum += rdot ? rdot[i] * si : si;
     }
   }
   double vv[kNV] = {(double)pss[0], (double)pss[1], (double)psum, 0, 0, 0};
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_p(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, KScal* sc,
-               GridReduce gr) {
+               GridReduce gr, const TV* __restrict__ rdot) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(kThreads)
       if (!act[q]) continue;
       const A pi = r.v[q][i] + be[q] * (p.v[q][i] - om[q] * v.v[q][i]);
       p.v[q][i] = pi;
-      if (RANK1) psum += pi;
+      if (RANK1) psum += rdot ? rdot[i] * pi : pi;
     }
   }
   double vv[kNV] = {(double)psum, 0, 0, 0, 0, 0};
@@ -835,6 +839,7 @@ struct StepPlan {
   double* r64[2] = {};
   KScal* sc = nullptr;
   double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
+  struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
   int64_t launches = 0;     // kernels launched by rbffd_step on this plan
   // optional per-launch timing of the pressure-solve SpMV kernels
   static constexpr int kEv = 512;
@@ -845,8 +850,11 @@ struct StepPlan {
   GridReduce gr{};
 };
 
+void adjoint_plan_free(struct AdjointPlan* a);
+
 void step_plan_free(StepPlan* p) {
   if (!p) return;
+  adjoint_plan_free(p->adj);
   for (int i = 0; i < StepPlan::kEv; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   for (void* a : p->allocs) cudaFree(a);
@@ -1020,7 +1028,7 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   // A breakdown of the recurrences (a zero inner product) restarts the method
   // from the current iterate with a fresh shadow residual.
   for (int restart = 0;; ++restart) {
-    if (RANK1) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx);
+    if (RANK1) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx, op.rdot);
     k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
                                                     tol * tol, maxit - total,
                                                     (restart || seed_base)
@@ -1045,12 +1053,12 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr);
+        k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
-        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr);
+        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot);
       }
       P->launches += 5 * n;
       rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
@@ -1111,7 +1119,7 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
   *sweeps = 0;
   double* h = (double*)ctx->host_pinned + 64;
   for (int sweep = 0;; ++sweep) {
-    if (RANK1) k_sum<double><<<G, kThreads, 0, st>>>(x[0], op64.n, P->gr, P->dscal);
+    if (RANK1) k_sum<double><<<G, kThreads, 0, st>>>(x[0], op64.n, P->gr, P->dscal, op64.rdot);
     k_residual64<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op64, X, B, R, P->dscal, P->dscal + 1,
                                                          P->gr);
     P->launches += RANK1 ? 2 : 1;
@@ -1321,6 +1329,507 @@ int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* 
                : run_steps<28, false>(ctx, P, *f, s, gu, gv, n_steps, stats, st);
   return mix ? run_steps<0, true>(ctx, P, *f, s, gu, gv, n_steps, stats, st)
              : run_steps<0, false>(ctx, P, *f, s, gu, gv, n_steps, stats, st);
+}
+
+}  // namespace rbffd
+
+// ===================================================================== adjoint
+//
+// Reverse-mode derivative of one fractional step (rbffd_adjoint_step).  Every
+// transposed operator is stored as an ELL matrix of its own (built once per
+// plan): the entries of each column of the forward operator are gathered into
+// one row, ordered by forward row so the result does not depend on the order
+// in which the build's atomics ran.  Transposed products are then plain
+// gathers, like the forward ones.  The transposed pressure solve uses
+// K = L^T - gamma 1 e^T: its solution z satisfies e^T z = 0 and L^T z = l - mean(l),
+// which is the first block of the transposed bordered system
+// [L^T 1; e^T 0] [z; z0] = [l; 0].
+namespace rbffd {
+
+struct TEll {
+  int32_t* idx = nullptr;   // transposed column = forward row
+  int32_t* slot = nullptr;  // forward slot of each entry, -1 for padding
+  int* counts = nullptr;
+  int width = 0;
+  int64_t ld = 0, n = 0;
+};
+
+struct AdjointPlan {
+  std::vector<void*> allocs;
+  TEll tvv, tpv, tvp, tl;
+  double *DxT = nullptr, *DyT = nullptr, *LapT = nullptr, *HwT = nullptr;
+  double *PxT = nullptr, *PyT = nullptr, *GxT = nullptr, *GyT = nullptr, *LT = nullptr;
+  double *e = nullptr, *es_t = nullptr;
+  double *luss, *lvss, *lru, *lrv, *t1, *t2, *t3, *t4, *lus, *lvs, *lcu, *lcv;
+  double *lpt, *z, *rhs;
+};
+
+void adjoint_plan_free(AdjointPlan* a) {
+  if (!a) return;
+  for (void* p : a->allocs) cudaFree(p);
+  delete a;
+}
+
+namespace {
+
+__global__ void k_t_count(int64_t n_rows, int64_t ld, int k, const int32_t* __restrict__ idx,
+                          int* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int s = 0; s < k; ++s) atomicAdd(&counts[idx[s * ld + i]], 1);
+}
+
+__global__ void k_t_max(int64_t n, const int* __restrict__ counts, int* __restrict__ mx) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, counts[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+__global__ void k_t_fill(int64_t n_rows, int64_t ld, int k, const int32_t* __restrict__ idx,
+                         int* __restrict__ cursor, int64_t ldt, int32_t* __restrict__ tidx,
+                         int32_t* __restrict__ tslot) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int s = 0; s < k; ++s) {
+      const int32_t c = idx[s * ld + i];
+      const int pos = atomicAdd(&cursor[c], 1);
+      tidx[pos * ldt + c] = (int32_t)i;
+      tslot[pos * ldt + c] = s;
+    }
+}
+
+// order each transposed row by forward row; pad with (self, -1)
+__global__ void k_t_sort_pad(int64_t n_cols, int64_t ldt, int width, const int* __restrict__ counts,
+                             int32_t* __restrict__ tidx, int32_t* __restrict__ tslot) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cols;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int m = counts[c];
+    for (int a = 1; a < m; ++a) {
+      const int32_t r = tidx[a * ldt + c], q = tslot[a * ldt + c];
+      int b = a;
+      while (b > 0 && tidx[(b - 1) * ldt + c] > r) {
+        tidx[b * ldt + c] = tidx[(b - 1) * ldt + c];
+        tslot[b * ldt + c] = tslot[(b - 1) * ldt + c];
+        --b;
+      }
+      tidx[b * ldt + c] = r;
+      tslot[b * ldt + c] = q;
+    }
+    for (int a = m; a < width; ++a) {
+      tidx[a * ldt + c] = (int32_t)c;
+      tslot[a * ldt + c] = -1;
+    }
+  }
+}
+
+// tw[a][c] = alpha * w[slot][row] * rowmul[row] * colmul[c]  (multipliers optional)
+__global__ void k_t_weights(int64_t n_cols, int64_t ldt, int width, const int32_t* __restrict__ tidx,
+                            const int32_t* __restrict__ tslot, const double* __restrict__ w,
+                            int64_t ld, const double* __restrict__ rowmul,
+                            const double* __restrict__ colmul, double alpha,
+                            double* __restrict__ tw) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cols;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const double cm = colmul ? colmul[c] : 1.0;
+    for (int a = 0; a < width; ++a) {
+      const int32_t q = tslot[a * ldt + c];
+      double v = 0.0;
+      if (q >= 0) {
+        const int32_t r = tidx[a * ldt + c];
+        v = alpha * w[q * ld + r] * (rowmul ? rowmul[r] : 1.0) * cm;
+      }
+      tw[a * ldt + c] = v;
+    }
+  }
+}
+
+__global__ void k_adj_setup_vec(int64_t M, const uint8_t* __restrict__ p_bc,
+                                const double* __restrict__ scale, double* __restrict__ e,
+                                double* __restrict__ inv_scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    e[i] = p_bc[i] ? 0.0 : 1.0;
+    inv_scale[i] = 1.0 / scale[i];
+  }
+}
+
+__global__ void k_adj_es(int64_t M, const double* __restrict__ scale, const double* sum,
+                         double* __restrict__ es_t) {
+  const double g = *sum != 0.0 ? 1.0 / fabs(*sum) : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x)
+    es_t[i] = -scale[i] * g;
+}
+
+__device__ __forceinline__ double tgather(const int32_t* __restrict__ idx,
+                                          const double* __restrict__ w, int64_t ld, int width,
+                                          int64_t i, const double* __restrict__ x) {
+  double acc = 0.0;
+  for (int s = 0; s < width; ++s) acc += w[s * ld + i] * x[idx[s * ld + i]];
+  return acc;
+}
+
+// wall rows of the correction: the overwrite sends their adjoint to the wall data
+__global__ void k_adj_mask(int64_t N, const double* __restrict__ lun, const double* __restrict__ lvn,
+                           const uint8_t* __restrict__ v_bc, int overwrite, double* __restrict__ gu,
+                           double* __restrict__ gv, double* __restrict__ luss,
+                           double* __restrict__ lvss) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double a = lun[i], b = lvn[i];
+    if (overwrite && v_bc[i]) {
+      gu[i] += a;
+      gv[i] += b;
+      a = 0.0;
+      b = 0.0;
+    }
+    luss[i] = a;
+    lvss[i] = b;
+  }
+}
+
+// l~_j = l_pt_out,j - dt (G_x^T l_u** + G_y^T l_v**)_j
+__global__ void k_adj_pt(int64_t M, TEll t, const double* __restrict__ GxT,
+                         const double* __restrict__ GyT, const double* __restrict__ luss,
+                         const double* __restrict__ lvss, const double* __restrict__ lpt_out,
+                         double dt, double* __restrict__ lpt) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+       j += (int64_t)gridDim.x * blockDim.x)
+    lpt[j] = lpt_out[j] - dt * (tgather(t.idx, GxT, t.ld, t.width, j, luss) +
+                                tgather(t.idx, GyT, t.ld, t.width, j, lvss));
+}
+
+__global__ void k_adj_prhs(int64_t M, const double* __restrict__ lpt, const double* sum,
+                           const double* __restrict__ scale, double* __restrict__ rhs,
+                           double* __restrict__ z0) {
+  const double mean = *sum / (double)M;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    rhs[j] = scale[j] * (lpt[j] - mean);
+    z0[j] = 0.0;
+  }
+}
+
+// l_u** += D^(P,V)_x^T (e o z / dt), likewise v
+__global__ void k_adj_div(int64_t N, TEll t, const double* __restrict__ PxT,
+                          const double* __restrict__ PyT, const double* __restrict__ ze,
+                          double* __restrict__ luss, double* __restrict__ lvss) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    luss[i] += tgather(t.idx, PxT, t.ld, t.width, i, ze);
+    lvss[i] += tgather(t.idx, PyT, t.ld, t.width, i, ze);
+  }
+}
+
+__global__ void k_adj_ze(int64_t M, const double* __restrict__ z, const double* __restrict__ e,
+                         double inv_dt, double* __restrict__ ze) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+       j += (int64_t)gridDim.x * blockDim.x)
+    ze[j] = z[j] * e[j] * inv_dt;
+}
+
+// wall rows of the viscous right side: wall data and the Kim & Moin term
+__global__ void k_adj_wall(int64_t N, const double* __restrict__ lru, const double* __restrict__ lrv,
+                           const uint8_t* __restrict__ v_bc, const double* __restrict__ nx,
+                           const double* __restrict__ ny, int km, double dt,
+                           double* __restrict__ gu, double* __restrict__ gv,
+                           double* __restrict__ t1, double* __restrict__ t2,
+                           double* __restrict__ t3, double* __restrict__ t4) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = lru[i], b = lrv[i];
+    if (v_bc[i]) {
+      gu[i] += a;
+      gv[i] += b;
+      t1[i] = 0.0;
+      t2[i] = 0.0;
+      if (km == 1) {
+        const double tx = -ny[i], ty = nx[i];
+        const double mu = dt * (tx * a + ty * b);
+        t3[i] = tx * mu;
+        t4[i] = ty * mu;
+      } else if (km == 2) {
+        t3[i] = dt * a;
+        t4[i] = dt * b;
+      } else {
+        t3[i] = 0.0;
+        t4[i] = 0.0;
+      }
+    } else {
+      t1[i] = a;
+      t2[i] = b;
+      t3[i] = 0.0;
+      t4[i] = 0.0;
+    }
+  }
+}
+
+__global__ void k_adj_ptin(int64_t M, TEll t, const double* __restrict__ GxT,
+                           const double* __restrict__ GyT, const double* __restrict__ t3,
+                           const double* __restrict__ t4, double* __restrict__ lpt_in) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+       j += (int64_t)gridDim.x * blockDim.x)
+    lpt_in[j] = tgather(t.idx, GxT, t.ld, t.width, j, t3) + tgather(t.idx, GyT, t.ld, t.width, j, t4);
+}
+
+// l_u* = l_r + a Lap^T l_r (interior rows of the viscous right side)
+__global__ void k_adj_us(int64_t N, TEll t, const double* __restrict__ LapT,
+                         const double* __restrict__ t1, const double* __restrict__ t2, double a,
+                         double* __restrict__ lus, double* __restrict__ lvs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    lus[i] = t1[i] + a * tgather(t.idx, LapT, t.ld, t.width, i, t1);
+    lvs[i] = t2[i] + a * tgather(t.idx, LapT, t.ld, t.width, i, t2);
+  }
+}
+
+// Adams-Bashforth: adjoints of C_j and of the input C_{j-1}; products for the convection adjoint
+__global__ void k_adj_ab2(int64_t N, const double* __restrict__ lus, const double* __restrict__ lvs,
+                          double* __restrict__ lcu_io, double* __restrict__ lcv_io, int first,
+                          double dt, const double* __restrict__ u, const double* __restrict__ v,
+                          double* __restrict__ lcu, double* __restrict__ lcv,
+                          double* __restrict__ t1, double* __restrict__ t2,
+                          double* __restrict__ t3, double* __restrict__ t4) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = lus[i], b = lvs[i];
+    double cu = 1.5 * dt * a + lcu_io[i];
+    double cv = 1.5 * dt * b + lcv_io[i];
+    if (first) {
+      cu += -0.5 * dt * a;
+      cv += -0.5 * dt * b;
+      lcu_io[i] = 0.0;
+      lcv_io[i] = 0.0;
+    } else {
+      lcu_io[i] = -0.5 * dt * a;
+      lcv_io[i] = -0.5 * dt * b;
+    }
+    lcu[i] = cu;
+    lcv[i] = cv;
+    t1[i] = u[i] * cu;
+    t2[i] = v[i] * cu;
+    t3[i] = u[i] * cv;
+    t4[i] = v[i] * cv;
+  }
+}
+
+// convection C(q) = -[u o D_x q + v o D_y q] (adjoint with respect to u, v)
+__global__ void k_adj_conv(int64_t N, int64_t ld, int k, const int32_t* __restrict__ idx,
+                           const double* __restrict__ Dx, const double* __restrict__ Dy, TEll t,
+                           const double* __restrict__ DxT, const double* __restrict__ DyT,
+                           const double* __restrict__ u, const double* __restrict__ v,
+                           const double* __restrict__ lus, const double* __restrict__ lvs,
+                           const double* __restrict__ lcu, const double* __restrict__ lcv,
+                           const double* __restrict__ t1, const double* __restrict__ t2,
+                           const double* __restrict__ t3, const double* __restrict__ t4,
+                           double* __restrict__ lu, double* __restrict__ lv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double dxu = 0, dyu = 0, dxv = 0, dyv = 0;
+    for (int s = 0; s < k; ++s) {
+      const int32_t j = idx[s * ld + i];
+      const double wx = Dx[s * ld + i], wy = Dy[s * ld + i];
+      dxu += wx * u[j];
+      dyu += wy * u[j];
+      dxv += wx * v[j];
+      dyv += wy * v[j];
+    }
+    const double ci = lcu[i], cj = lcv[i];
+    lu[i] = lus[i] - dxu * ci - tgather(t.idx, DxT, t.ld, t.width, i, t1) -
+            tgather(t.idx, DyT, t.ld, t.width, i, t2) - dxv * cj;
+    lv[i] = lvs[i] - dyu * ci - dyv * cj - tgather(t.idx, DxT, t.ld, t.width, i, t3) -
+            tgather(t.idx, DyT, t.ld, t.width, i, t4);
+  }
+}
+
+int palloc_a(rbffd_ctx* ctx, AdjointPlan* a, void** out, size_t bytes) {
+  void* ptr = nullptr;
+  int rc = check_cuda(ctx, cudaMalloc(&ptr, bytes > 0 ? bytes : 1), "adjoint alloc");
+  if (rc) return rc;
+  a->allocs.push_back(ptr);
+  *out = ptr;
+  return RBFFD_OK;
+}
+
+// transposed structure of an ELL operator with n_rows rows into n_cols columns
+int build_transpose(rbffd_ctx* ctx, AdjointPlan* a, const int32_t* idx, int64_t n_rows, int64_t ld,
+                    int k, int64_t n_cols, int grid, TEll* t, cudaStream_t st) {
+  int rc = palloc_a(ctx, a, (void**)&t->counts, sizeof(int) * (n_cols + 1));
+  if (rc) return rc;
+  int* mx = t->counts + n_cols;
+  rc = check_cuda(ctx, cudaMemsetAsync(t->counts, 0, sizeof(int) * (n_cols + 1), st), "memset");
+  if (rc) return rc;
+  k_t_count<<<grid, 256, 0, st>>>(n_rows, ld, k, idx, t->counts);
+  k_t_max<<<grid, 256, 0, st>>>(n_cols, t->counts, mx);
+  int hmax = 0;
+  rc = check_cuda(ctx, cudaMemcpyAsync(&hmax, mx, sizeof(int), cudaMemcpyDeviceToHost, st), "max");
+  if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(st), "transpose sync");
+  if (rc) return rc;
+  t->width = hmax > 0 ? hmax : 1;
+  t->ld = round_up(n_cols, 32);
+  t->n = n_cols;
+  rc = palloc_a(ctx, a, (void**)&t->idx, sizeof(int32_t) * t->width * t->ld);
+  if (!rc) rc = palloc_a(ctx, a, (void**)&t->slot, sizeof(int32_t) * t->width * t->ld);
+  int* cursor = nullptr;
+  if (!rc) rc = palloc_a(ctx, a, (void**)&cursor, sizeof(int) * n_cols);
+  if (rc) return rc;
+  rc = check_cuda(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * n_cols, st), "memset");
+  if (rc) return rc;
+  k_t_fill<<<grid, 256, 0, st>>>(n_rows, ld, k, idx, cursor, t->ld, t->idx, t->slot);
+  k_t_sort_pad<<<grid, 256, 0, st>>>(n_cols, t->ld, t->width, t->counts, t->idx, t->slot);
+  return check_cuda(ctx, cudaGetLastError(), "transpose kernels");
+}
+
+int t_weights(rbffd_ctx* ctx, AdjointPlan* a, const TEll& t, const double* w, int64_t ld,
+              const double* rowmul, const double* colmul, double alpha, double** out, int grid,
+              cudaStream_t st) {
+  int rc = palloc_a(ctx, a, (void**)out, sizeof(double) * t.width * t.ld);
+  if (rc) return rc;
+  k_t_weights<<<grid, 256, 0, st>>>(t.n, t.ld, t.width, t.idx, t.slot, w, ld, rowmul, colmul,
+                                    alpha, *out);
+  return check_cuda(ctx, cudaGetLastError(), "transpose weights");
+}
+
+int build_adjoint_plan(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, cudaStream_t st) {
+  AdjointPlan* a = new AdjointPlan();
+  const int G = P->grid, k = P->k;
+  int rc = 0;
+#define TRYA(x)                \
+  do {                         \
+    rc = (x);                  \
+    if (rc) {                  \
+      adjoint_plan_free(a);    \
+      return rc;               \
+    }                          \
+  } while (0)
+  TRYA(build_transpose(ctx, a, f.vv_idx, f.N, f.ld_v, k, f.N, G, &a->tvv, st));
+  TRYA(build_transpose(ctx, a, f.pv_idx, f.M, f.ld_p, k, f.N, G, &a->tpv, st));
+  TRYA(build_transpose(ctx, a, f.vp_idx, f.N, f.ld_v, k, f.M, G, &a->tvp, st));
+  TRYA(build_transpose(ctx, a, P->Lidx, f.M, f.ld_p, k, f.M, G, &a->tl, st));
+  double* inv_scale = nullptr;
+  TRYA(palloc_a(ctx, a, (void**)&a->e, sizeof(double) * f.M));
+  TRYA(palloc_a(ctx, a, (void**)&inv_scale, sizeof(double) * f.M));
+  TRYA(palloc_a(ctx, a, (void**)&a->es_t, sizeof(double) * f.M));
+  k_adj_setup_vec<<<G, 256, 0, st>>>(f.M, f.p_bc, P->scale, a->e, inv_scale);
+  TRYA(t_weights(ctx, a, a->tvv, f.vv_dx, f.ld_v, nullptr, nullptr, 1.0, &a->DxT, G, st));
+  TRYA(t_weights(ctx, a, a->tvv, f.vv_dy, f.ld_v, nullptr, nullptr, 1.0, &a->DyT, G, st));
+  TRYA(t_weights(ctx, a, a->tvv, f.vv_lap, f.ld_v, nullptr, nullptr, 1.0, &a->LapT, G, st));
+  TRYA(t_weights(ctx, a, a->tvv, P->Hw, f.ld_v, nullptr, nullptr, 1.0, &a->HwT, G, st));
+  TRYA(t_weights(ctx, a, a->tpv, f.pv_dx, f.ld_p, nullptr, nullptr, 1.0, &a->PxT, G, st));
+  TRYA(t_weights(ctx, a, a->tpv, f.pv_dy, f.ld_p, nullptr, nullptr, 1.0, &a->PyT, G, st));
+  TRYA(t_weights(ctx, a, a->tvp, f.vp_dx, f.ld_v, nullptr, nullptr, 1.0, &a->GxT, G, st));
+  TRYA(t_weights(ctx, a, a->tvp, f.vp_dy, f.ld_v, nullptr, nullptr, 1.0, &a->GyT, G, st));
+  // S L^T: unscale the forward rows (1/s_row), scale the transposed rows (s_col)
+  TRYA(t_weights(ctx, a, a->tl, P->Lw, f.ld_p, inv_scale, P->scale, 1.0, &a->LT, G, st));
+  // rank-one column -gamma S 1 with gamma = 1/|sum over interior rows of s|
+  k_sum<double><<<G, kThreads, 0, st>>>(P->scale, f.M, P->gr, P->dscal, a->e);
+  k_adj_es<<<G, 256, 0, st>>>(f.M, P->scale, P->dscal, a->es_t);
+  TRYA(check_cuda(ctx, cudaGetLastError(), "adjoint set-up"));
+  double** vecN[] = {&a->luss, &a->lvss, &a->lru, &a->lrv, &a->t1,  &a->t2,
+                     &a->t3,   &a->t4,   &a->lus, &a->lvs, &a->lcu, &a->lcv};
+  for (double** v : vecN) TRYA(palloc_a(ctx, a, (void**)v, sizeof(double) * f.N));
+  TRYA(palloc_a(ctx, a, (void**)&a->lpt, sizeof(double) * f.M));
+  TRYA(palloc_a(ctx, a, (void**)&a->z, sizeof(double) * f.M));
+  TRYA(palloc_a(ctx, a, (void**)&a->rhs, sizeof(double) * f.M));
+#undef TRYA
+  P->adj = a;
+  return RBFFD_OK;
+}
+
+}  // namespace
+
+int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* fp, const rbffd_state* s, rbffd_adjoint* lam,
+                double* grad_gu, double* grad_gv, rbffd_stats* stats, cudaStream_t st) {
+  const rbffd_flow& f = *fp;
+  if (ctx->plan && memcmp(&ctx->plan->key, fp, sizeof(rbffd_flow)) != 0) {
+    cudaStreamSynchronize(st);
+    step_plan_free(ctx->plan);
+    ctx->plan = nullptr;
+  }
+  if (!ctx->plan) {
+    int rc = build_plan(ctx, f, &ctx->plan, st);
+    if (rc) return rc;
+  }
+  StepPlan* P = ctx->plan;
+  if (!P->adj) {
+    int rc = build_adjoint_plan(ctx, P, f, st);
+    if (rc) return rc;
+  }
+  AdjointPlan* A = P->adj;
+  const int G = P->grid;
+  const double a = f.dt / (2.0 * f.Re);
+  // correction and its wall overwrite
+  k_adj_mask<<<G, kThreads, 0, st>>>(f.N, lam->u, lam->v, f.v_bc, f.overwrite_bc, grad_gu,
+                                     grad_gv, A->luss, A->lvss);
+  k_adj_pt<<<G, kThreads, 0, st>>>(f.M, A->tvp, A->GxT, A->GyT, A->luss, A->lvss, lam->pt, f.dt,
+                                   A->lpt);
+  // transposed pressure solve
+  k_sum<double><<<G, kThreads, 0, st>>>(A->lpt, f.M, P->gr, P->dscal);
+  k_adj_prhs<<<G, kThreads, 0, st>>>(f.M, A->lpt, P->dscal, P->scale, A->rhs, A->z);
+  P->launches += 4;
+  int rc = check_cuda(ctx, cudaGetLastError(), "adjoint kernels");
+  if (rc) return rc;
+  KOp<double, double> LT{A->tl.idx, A->LT, A->tl.ld, f.M, A->tl.width, 0, A->es_t, A->e};
+  double* zx[1] = {A->z};
+  const double* zb[1] = {A->rhs};
+  SolveResult pr;
+  rc = bicgstab<0, 1, true, double, double>(ctx, P, LT, zx, zb, P->kw64, f.tol, f.max_iter, &pr,
+                                            st);
+  if (rc) return rc;
+  if (stats) {
+    stats->poisson_iters += pr.iters;
+    stats->poisson_relres = pr.relres;
+  }
+  if (pr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite adjoint pressure solve");
+  if (!pr.converged)
+    return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
+                     "adjoint pressure solve: relative residual %.3e after %d iterations",
+                     pr.relres, pr.iters);
+  k_adj_ze<<<G, kThreads, 0, st>>>(f.M, A->z, A->e, 1.0 / f.dt, A->rhs);
+  k_adj_div<<<G, kThreads, 0, st>>>(f.N, A->tpv, A->PxT, A->PyT, A->rhs, A->luss, A->lvss);
+  // transposed viscous solves, two right sides; start from the right sides
+  rc = check_cuda(ctx, cudaMemcpyAsync(A->lru, A->luss, sizeof(double) * f.N,
+                                       cudaMemcpyDeviceToDevice, st), "copy");
+  if (!rc) rc = check_cuda(ctx, cudaMemcpyAsync(A->lrv, A->lvss, sizeof(double) * f.N,
+                                                cudaMemcpyDeviceToDevice, st), "copy");
+  if (rc) return rc;
+  KOp<double, double> HT{A->tvv.idx, A->HwT, A->tvv.ld, f.N, A->tvv.width, 1, nullptr, nullptr};
+  double* hx[2] = {A->lru, A->lrv};
+  const double* hb[2] = {A->luss, A->lvss};
+  SolveResult hr;
+  rc = bicgstab<0, 2, false, double, double>(ctx, P, HT, hx, hb, P->kw64, f.tol, f.max_iter, &hr,
+                                             st);
+  if (rc) return rc;
+  if (stats) {
+    stats->helm_iters += hr.iters;
+    stats->helm_relres = hr.relres;
+  }
+  if (hr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite adjoint viscous solve");
+  if (!hr.converged)
+    return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
+                     "adjoint viscous solve: relative residual %.3e after %d iterations",
+                     hr.relres, hr.iters);
+  k_adj_wall<<<G, kThreads, 0, st>>>(f.N, A->lru, A->lrv, f.v_bc, f.v_nx, f.v_ny, f.km_mode, f.dt,
+                                     grad_gu, grad_gv, A->t1, A->t2, A->t3, A->t4);
+  k_adj_ptin<<<G, kThreads, 0, st>>>(f.M, A->tvp, A->GxT, A->GyT, A->t3, A->t4, lam->pt);
+  k_adj_us<<<G, kThreads, 0, st>>>(f.N, A->tvv, A->LapT, A->t1, A->t2, a, A->lus, A->lvs);
+  k_adj_ab2<<<G, kThreads, 0, st>>>(f.N, A->lus, A->lvs, lam->cu_prev, lam->cv_prev,
+                                    s->j == 0 ? 1 : 0, f.dt, s->u, s->v, A->lcu, A->lcv, A->t1,
+                                    A->t2, A->t3, A->t4);
+  k_adj_conv<<<G, kThreads, 0, st>>>(f.N, f.ld_v, P->k, f.vv_idx, f.vv_dx, f.vv_dy, A->tvv, A->DxT,
+                                     A->DyT, s->u, s->v, A->lus, A->lvs, A->lcu, A->lcv, A->t1,
+                                     A->t2, A->t3, A->t4, lam->u, lam->v);
+  P->launches += 7;
+  rc = check_cuda(ctx, cudaGetLastError(), "adjoint kernels");
+  if (rc) return rc;
+  rc = check_cuda(ctx, cudaStreamSynchronize(st), "adjoint sync");
+  if (stats) {
+    stats->steps += 1;
+  }
+  return rc;
 }
 
 }  // namespace rbffd

@@ -72,6 +72,11 @@ class StateC(C.Structure):
                 ("j", C.c_int64)]
 
 
+class AdjointC(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("cu_prev", C.c_void_p),
+                ("cv_prev", C.c_void_p), ("pt", C.c_void_p)]
+
+
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("helm_iters", C.c_int64), ("poisson_iters", C.c_int64),
                 ("refinements", C.c_int64), ("helm_relres", C.c_double),
@@ -106,6 +111,9 @@ PROTOTYPES = {
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "rbffd_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC), C.c_void_p,
                              C.c_void_p, C.c_int32, C.POINTER(Stats), C.c_void_p]),
+    "rbffd_adjoint_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC),
+                                     C.POINTER(AdjointC), C.c_void_p, C.c_void_p,
+                                     C.POINTER(Stats), C.c_void_p]),
 }
 
 
@@ -341,6 +349,41 @@ def step(ctx: Context, flow: Flow, state: State, gu, gv, n_steps: int = 1) -> di
                           C.byref(st), _stream())
     state.j = sc.j
     ctx.check(rc)
+    return st.as_dict()
+
+
+@dataclass
+class Adjoint:
+    """Adjoint variables of a State (dJ/du, dJ/dv, dJ/dC_{j-1}, dJ/dp~)."""
+    u: object
+    v: object
+    cu_prev: object
+    cv_prev: object
+    pt: object
+
+    @staticmethod
+    def zeros(flow: Flow, device="cuda"):
+        torch = _torch()
+        z = lambda n: torch.zeros(n, dtype=torch.float64, device=device)  # noqa: E731
+        return Adjoint(z(flow.N), z(flow.N), z(flow.N), z(flow.N), z(flow.M))
+
+
+def _state_c(state: State) -> StateC:
+    return StateC(u=_ptr(state.u).value, v=_ptr(state.v).value,
+                  cu_prev=_ptr(state.cu_prev).value, cv_prev=_ptr(state.cv_prev).value,
+                  pt=_ptr(state.pt).value, p=_ptr(state.p).value, j=state.j)
+
+
+def adjoint_step(ctx: Context, flow: Flow, fwd: State, lam: Adjoint, grad_gu, grad_gv) -> dict:
+    """rbffd_adjoint_step: lam (adjoints of step j+1) -> adjoints of step j, in
+    place; the step's wall-data adjoint is added to grad_gu, grad_gv."""
+    fc = flow.cstruct()
+    sc = _state_c(fwd)
+    ac = AdjointC(u=_ptr(lam.u).value, v=_ptr(lam.v).value, cu_prev=_ptr(lam.cu_prev).value,
+                  cv_prev=_ptr(lam.cv_prev).value, pt=_ptr(lam.pt).value)
+    st = Stats()
+    ctx.check(lib().rbffd_adjoint_step(ctx.handle, C.byref(fc), C.byref(sc), C.byref(ac),
+                                       _ptr(grad_gu), _ptr(grad_gv), C.byref(st), _stream()))
     return st.as_dict()
 
 
