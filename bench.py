@@ -324,7 +324,8 @@ def run_ours(args):
     # roofline of the dominant kernel: the SpMV of the pressure solve
     k = 28
     if head == "mixed":
-        bytes_row, key = 8 * k + 16, "k_spmv_fp32_rank1"
+        # FP32 weights, split (hi, lo) FP32 gathers, FP64 output, rh and rank-one column
+        bytes_row, key = 8 * k + 32, "k_spmv_ff_rank1"
     else:
         bytes_row, key = 12 * k + 32, "k_spmv_fp64_rank1"
     per_launch_ms = agg["spmv_ms"] / max(agg["spmv_launches"], 1)

@@ -37,9 +37,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNV = 6;  // values reduced per kernel
-// Iterations of one FP32 inner solve before the refinement loop restarts it
-// from the FP64 residual (bounds the drift of the FP32 recurrences).
-constexpr int kInnerCap = 600;
 
 // RBFFD_TRACE=1 in the environment prints one line per solve and refinement
 // sweep to stderr (iterations, residuals, status).
@@ -93,11 +90,12 @@ struct Acc<float> {
   using t = float;
 };
 
-// sum_s w[s][i] * x[idx[s][i]] for one or two vectors sharing the stencil
+// sum_s w[s][i] * x[idx[s][i]] for one or two vectors sharing the stencil,
+// accumulated in the precision of the vectors
 template <int K, int NRHS, typename TW, typename TV>
 __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, const TV* const* x,
-                                            typename Acc<TW>::t* acc) {
-  using A = typename Acc<TW>::t;
+                                            typename Acc<TV>::t* acc) {
+  using A = typename Acc<TV>::t;
 #pragma unroll
   for (int r = 0; r < NRHS; ++r) acc[r] = 0;
   const int k = K > 0 ? K : op.k;
@@ -114,6 +112,62 @@ template <typename TV, int NRHS>
 struct Vecs {
   TV* v[NRHS];
 };
+
+// Split FP32 copies (hi, lo) of the vectors an FP32-weight operator gathers
+// inside an FP64 Krylov solve (null when the operator is not FP32 x FP64).
+template <int NRHS>
+struct Split {
+  float2* v[NRHS];
+};
+
+template <typename TW, typename TV>
+struct IsFF {
+  static constexpr bool value = false;
+};
+template <>
+struct IsFF<float, double> {
+  static constexpr bool value = true;
+};
+
+// exact product and sum of two floats (Dekker / Knuth), for float-float sums
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// sum_s w[s][i] * x[idx[s][i]] with FP32 weights and x split into (hi, lo):
+// the products and the running sum are kept as float-float pairs, so the
+// result carries about 44 bits although every operation is FP32.
+template <int K, int NRHS>
+__device__ __forceinline__ void gather_ff(const KOp<float, double>& op, int64_t i,
+                                          const float2* const* x2, double* acc) {
+  float sh[NRHS], sl[NRHS];
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) sh[r] = sl[r] = 0.f;
+  const int k = K > 0 ? K : op.k;
+#pragma unroll(K > 0 ? K : 1)
+  for (int s = 0; s < k; ++s) {
+    const int j = op.idx[s * op.ld + i];
+    const float w = op.w[s * op.ld + i];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      const float2 xj = x2[r][j];
+      float p, e, t, te;
+      two_prod(w, xj.x, p, e);
+      e = fmaf(w, xj.y, e);
+      two_sum(sh[r], p, t, te);
+      sh[r] = t;
+      sl[r] += te + e;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = (double)sh[r] + (double)sl[r];
+}
 
 // ----------------------------------------------------------- Krylov kernels
 // sum_i x_i, or sum_i c_i x_i when c is given
@@ -150,8 +204,8 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_init(KOp<TW, TV> op, Vecs<TV, NRHS> x, Vecs<TV, NRHS> b, Vecs<TV, NRHS> r,
            Vecs<TV, NRHS> rh, Vecs<TV, NRHS> p, const double* sigma_x, KScal* sc, GridReduce gr,
-           double tol2, int maxit, uint32_t seed) {
-  using A = typename Acc<TW>::t;
+           double tol2, int maxit, uint32_t seed, Split<NRHS> p2) {
+  using A = typename Acc<TV>::t;
   __shared__ double sh[kNV * kThreads / 32];
   A prr[2] = {0, 0}, pbb[2] = {0, 0}, prh[2] = {0, 0}, psum = 0;
   const A sig = RANK1 ? (A)*sigma_x : (A)0;
@@ -170,6 +224,7 @@ __global__ void __launch_bounds__(kThreads)
       r.v[q][i] = (TV)ri;
       rh.v[q][i] = (TV)(sgn * ri);
       p.v[q][i] = (TV)ri;
+      if (IsFF<TW, TV>::value) p2.v[q][i] = split2((double)ri);
       prr[q] += ri * ri;
       pbb[q] += bi * bi;
       prh[q] += sgn * ri * ri;
@@ -208,8 +263,8 @@ __global__ void __launch_bounds__(kThreads)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
-             GridReduce gr) {
-  using A = typename Acc<TW>::t;
+             GridReduce gr, Split<NRHS> p2) {
+  using A = typename Acc<TV>::t;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_p : (A)0;
@@ -217,7 +272,10 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
        i += (int64_t)gridDim.x * kThreads) {
     A acc[NRHS];
-    gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
+    if constexpr (IsFF<TW, TV>::value)
+      gather_ff<K, NRHS>(op, i, (const float2* const*)p2.v, acc);
+    else
+      gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
       A y = acc[q];
@@ -246,7 +304,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_s(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> v, Vecs<TV, NRHS> s, KScal* sc,
-               GridReduce gr, const TV* __restrict__ rdot) {
+               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> s2) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -265,6 +323,7 @@ __global__ void __launch_bounds__(kThreads)
       if (!act[q]) continue;
       const A si = r.v[q][i] - al[q] * v.v[q][i];
       s.v[q][i] = si;
+      if (s2.v[0]) s2.v[q][i] = split2((double)si);
       pss[q] += si * si;
       if (RANK1) psum += rdot ? rdot[i] * si : si;
     }
@@ -280,8 +339,9 @@ __global__ void __launch_bounds__(kThreads)
 // t = A s ; reduce (t, s), (t, t)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
-    k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr) {
-  using A = typename Acc<TW>::t;
+    k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr,
+             Split<NRHS> s2) {
+  using A = typename Acc<TV>::t;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_s : (A)0;
@@ -289,7 +349,10 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
        i += (int64_t)gridDim.x * kThreads) {
     A acc[NRHS];
-    gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
+    if constexpr (IsFF<TW, TV>::value)
+      gather_ff<K, NRHS>(op, i, (const float2* const*)s2.v, acc);
+    else
+      gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
       A y = acc[q];
@@ -393,7 +456,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_p(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, KScal* sc,
-               GridReduce gr, const TV* __restrict__ rdot) {
+               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> p2) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -413,6 +476,7 @@ __global__ void __launch_bounds__(kThreads)
       if (!act[q]) continue;
       const A pi = r.v[q][i] + be[q] * (p.v[q][i] - om[q] * v.v[q][i]);
       p.v[q][i] = pi;
+      if (p2.v[0]) p2.v[q][i] = split2((double)pi);
       if (RANK1) psum += rdot ? rdot[i] * pi : pi;
     }
   }
@@ -837,6 +901,8 @@ struct StepPlan {
   float* kw32[7][2] = {};
   float *e32[2] = {}, *r32[2] = {};
   double* r64[2] = {};
+  double *e64[2] = {}, *b64[2] = {};     // FP64 correction and right side of inner solves
+  float2 *p2[2] = {}, *s2[2] = {};       // split copies gathered by FP32-weight SpMVs
   KScal* sc = nullptr;
   double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
   struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
@@ -973,6 +1039,10 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       TRY(palloc(ctx, p, &p->e32[b], nmax));
       TRY(palloc(ctx, p, &p->r32[b], nmax));
       TRY(palloc(ctx, p, &p->r64[b], nmax));
+      TRY(palloc(ctx, p, &p->e64[b], nmax));
+      TRY(palloc(ctx, p, &p->b64[b], nmax));
+      TRY(palloc(ctx, p, &p->p2[b], nmax));
+      TRY(palloc(ctx, p, &p->s2[b], nmax));
     }
   }
 #undef TRY
@@ -1003,8 +1073,14 @@ void collect_events(StepPlan* P) {
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
-             cudaStream_t st, bool prof = false, uint32_t seed_base = 0) {
+             cudaStream_t st, bool prof = false, uint32_t seed_base = 0,
+             float2* const* p2s = nullptr, float2* const* s2s = nullptr) {
   Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
+  Split<NRHS> P2, S2;
+  for (int q = 0; q < NRHS; ++q) {
+    P2.v[q] = p2s ? p2s[q] : nullptr;
+    S2.v[q] = s2s ? s2s[q] : nullptr;
+  }
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
     B.v[q] = (TV*)b[q];
@@ -1033,7 +1109,8 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
                                                     tol * tol, maxit - total,
                                                     (restart || seed_base)
                                                         ? 0x51ED27u + 977u * seed_base + restart
-                                                        : 0u);
+                                                        : 0u,
+                                                    P2);
     P->launches += RANK1 ? 2 : 1;
     int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
     if (rc) return rc;
@@ -1051,14 +1128,16 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (prof) n = std::min(n, StepPlan::kEv / 4);
       for (int it = 0; it < n; ++it) {
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr);
+        k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot);
+        k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
+                                                        S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr);
+        k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr, S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
-        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot);
+        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
+                                                        P2);
       }
       P->launches += 5 * n;
       rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
@@ -1096,20 +1175,47 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   return RBFFD_OK;
 }
 
-// FP64 iterative refinement around FP32 BiCGSTAB corrections
+// FP64 iterative refinement: the residual uses the FP64 operator; each
+// correction solves the FP32-weight operator with FP64 BiCGSTAB recurrences,
+// its SpMVs gathering split FP32 copies with float-float sums (FP32 pipes,
+// 4-byte weights).  A correction that does not lower the FP64 residual is
+// undone and the inner solve repeated with another shadow residual.
+template <int NRHS>
+__global__ void k_scale_zero(int64_t n, Vecs<double, NRHS> r, Vecs<double, NRHS> b,
+                             Vecs<double, NRHS> e, double inv0, double inv1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    b.v[0][i] = r.v[0][i] * inv0;
+    e.v[0][i] = 0.0;
+    if (NRHS > 1) {
+      b.v[NRHS - 1][i] = r.v[NRHS - 1][i] * inv1;
+      e.v[NRHS - 1][i] = 0.0;
+    }
+  }
+}
+
+template <int NRHS>
+__global__ void k_addcorr64(int64_t n, Vecs<double, NRHS> x, Vecs<double, NRHS> e, double n0,
+                            double n1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x.v[0][i] += n0 * e.v[0][i];
+    if (NRHS > 1) x.v[NRHS - 1][i] += n1 * e.v[NRHS - 1][i];
+  }
+}
+
 template <int K, int NRHS, bool RANK1>
 int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
-           const KOp<float, float>& op32, double* const* x, const double* const* b, double tol,
+           const KOp<float, double>& op32, double* const* x, const double* const* b, double tol,
            double inner_tol, int maxit, SolveResult* res, int* sweeps, cudaStream_t st,
            bool prof = false) {
-  Vecs<double, NRHS> X, B, R;
-  Vecs<float, NRHS> R32, E32;
+  Vecs<double, NRHS> X, B, R, B64, E64;
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
     B.v[q] = (double*)b[q];
     R.v[q] = P->r64[q];
-    R32.v[q] = P->r32[q];
-    E32.v[q] = P->e32[q];
+    B64.v[q] = P->b64[q];
+    E64.v[q] = P->e64[q];
   }
   const int G = P->grid;
   int used = 0, failures = 0, retries = 0;
@@ -1143,8 +1249,8 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     }
     if (sweep > 0 && (!finite || !(worst < prev_rel))) {
       // the last correction made things worse: undo it and solve again
-      k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, -last_nrm[0],
-                                              NRHS > 1 ? -last_nrm[NRHS - 1] : 0.0);
+      k_addcorr64<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E64, -last_nrm[0],
+                                                NRHS > 1 ? -last_nrm[NRHS - 1] : 0.0);
       P->launches += 1;
       rc = check_cuda(ctx, cudaGetLastError(), "undo correction");
       if (rc) return rc;
@@ -1168,18 +1274,19 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     ++*sweeps;
     const double i0 = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
     const double i1 = NRHS > 1 && nrm[NRHS - 1] > 0 ? 1.0 / nrm[NRHS - 1] : 0.0;
-    k_to32<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, R32, E32, i0, i1);
+    k_scale_zero<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, B64, E64, i0, i1);
     P->launches += 2;  // with the correction below
     SolveResult inner;
-    rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
-                                                std::min(maxit - used, kInnerCap), &inner, st,
-                                                prof, retries);
+    rc = bicgstab<K, NRHS, RANK1, float, double>(ctx, P, op32, E64.v, B64.v, P->kw64, inner_tol,
+                                                 maxit - used, &inner, st, prof, retries, P->p2,
+                                                 P->s2);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
     last_nrm[0] = nrm[0];
     last_nrm[1] = nrm[1];
-    k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, nrm[0], NRHS > 1 ? nrm[NRHS - 1] : 0.0);
+    k_addcorr64<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E64, nrm[0],
+                                              NRHS > 1 ? nrm[NRHS - 1] : 0.0);
     rc = check_cuda(ctx, cudaGetLastError(), "correction");
     if (rc) return rc;
   }
@@ -1216,8 +1323,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   }
   KOp<double, double> H64{f.vv_idx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
   KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, k, 0, P->es};
-  KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr};
-  KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es32};
+  KOp<float, double> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
+  KOp<float, double> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es, nullptr};
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
                 P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,
