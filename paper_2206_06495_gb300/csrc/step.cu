@@ -60,6 +60,7 @@ struct KScal {
   int done;
   int status;  // 0 ok, 2 non-finite, 1/3/4 breakdown at (rh,v) = 0 / (t,t) = 0 / rho or
                // omega = 0, 5 residual grew beyond 1e4 ||b||
+  int stage_err;  // nonzero: a tile copy did not complete within the bounded wait
 };
 
 __device__ __forceinline__ float2 split2(double x) {
@@ -106,6 +107,88 @@ __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, co
 #pragma unroll
     for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
   }
+}
+
+// ------------------------------------------------ staged ELL tiles (bulk copies)
+// A block stages the idx and weight columns of 256 consecutive rows into
+// shared memory: one contiguous segment per stencil slot, moved by
+// cp.async.bulk copies that complete on an mbarrier.  The threads then gather
+// x for their own row with every address already on chip, so the streaming
+// part of the SpMV never waits on the gathers.
+constexpr int kTileRows = 256;
+constexpr long long kSpinLimit = 1ll << 22;  // bounded mbarrier wait (a tile lands in microseconds)
+
+template <int K, typename TW>
+struct EllStage {
+  int32_t idx[K * kTileRows];
+  TW w[K * kTileRows];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Stage rows [row0, row0 + 256) of (idx, w); every thread returns once the
+// copies have landed, or false after kSpinLimit polls (then *err is set).
+template <int K, typename TW>
+__device__ __forceinline__ bool stage_tile(EllStage<K, TW>* tile, uint64_t* bar, uint32_t& phase,
+                                           const int32_t* __restrict__ gidx,
+                                           const TW* __restrict__ gw, int64_t ld, int64_t row0,
+                                           int* err) {
+  __syncthreads();  // every thread is done with the previous tile
+  if (threadIdx.x == 0) {
+    const int64_t left = ld - row0;
+    const uint32_t rows = (uint32_t)(left < kTileRows ? left : kTileRows);  // multiple of 32
+    const uint32_t bi = rows * 4u, bw = rows * (uint32_t)sizeof(TW);
+    mbar_expect_tx(bar, (uint32_t)K * (bi + bw));
+#pragma unroll 4
+    for (int s = 0; s < K; ++s) {
+      bulk_g2s(&tile->idx[s * kTileRows], gidx + s * ld + row0, bi, bar);
+      bulk_g2s(&tile->w[s * kTileRows], gw + s * ld + row0, bw, bar);
+    }
+  }
+  long long spins = 0;
+  bool ok;
+  while (!(ok = mbar_try_wait(bar, phase)) && ++spins < kSpinLimit) {
+  }
+  // one verdict for the whole block, so every thread leaves the loop together
+  if (!__syncthreads_and(ok ? 1 : 0)) {
+    if (threadIdx.x == 0) atomicOr(err, 4);
+    // give the copies in flight one more bounded chance to land before the block leaves
+    spins = 0;
+    while (!mbar_try_wait(bar, phase) && ++spins < kSpinLimit) {
+    }
+    return false;
+  }
+  phase ^= 1u;
+  return true;
 }
 
 template <typename TV, int NRHS>
@@ -163,6 +246,47 @@ __device__ __forceinline__ void gather_ff(const KOp<float, double>& op, int64_t 
       two_sum(sh[r], p, t, te);
       sh[r] = t;
       sl[r] += te + e;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = (double)sh[r] + (double)sl[r];
+}
+
+// the same sums with idx and w read from a staged tile
+template <int K, int NRHS, typename TW, typename TV>
+__device__ __forceinline__ void gather_tile(const EllStage<K, TW>* t, int tid, const TV* const* x,
+                                            typename Acc<TV>::t* acc) {
+  using A = typename Acc<TV>::t;
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = 0;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int j = t->idx[s * kTileRows + tid];
+    const A w = (A)t->w[s * kTileRows + tid];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
+  }
+}
+
+template <int K, int NRHS>
+__device__ __forceinline__ void gather_tile_ff(const EllStage<K, float>* t, int tid,
+                                               const float2* const* x2, double* acc) {
+  float sh[NRHS], sl[NRHS];
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) sh[r] = sl[r] = 0.f;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int j = t->idx[s * kTileRows + tid];
+    const float w = t->w[s * kTileRows + tid];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      const float2 xj = x2[r][j];
+      float p, e, u, ue;
+      two_prod(w, xj.x, p, e);
+      e = fmaf(w, xj.y, e);
+      two_sum(sh[r], p, u, ue);
+      sh[r] = u;
+      sl[r] += ue + e;
     }
   }
 #pragma unroll
@@ -239,6 +363,7 @@ __global__ void __launch_bounds__(kThreads)
     sc->maxit = maxit;
     sc->iters = 0;
     sc->status = 0;
+    sc->stage_err = 0;
     int any = 0;
     for (int q = 0; q < NRHS; ++q) {
       const double rr = t[2 * q], bb = t[2 * q + 1];
@@ -259,7 +384,8 @@ __global__ void __launch_bounds__(kThreads)
   });
 }
 
-// v = A p ; reduce (rh, v)
+// v = A p ; reduce (rh, v).  K > 0: rows come in staged tiles (dynamic shared
+// memory holds one EllStage); K == 0: rows are read directly.
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
@@ -269,13 +395,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double sh[kNV * kThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_p : (A)0;
   A pd[2] = {0, 0};
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
-       i += (int64_t)gridDim.x * kThreads) {
-    A acc[NRHS];
-    if constexpr (IsFF<TW, TV>::value)
-      gather_ff<K, NRHS>(op, i, (const float2* const*)p2.v, acc);
-    else
-      gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
+  auto finish_row = [&](int64_t i, A* acc) {
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
       A y = acc[q];
@@ -284,9 +404,42 @@ __global__ void __launch_bounds__(kThreads)
       v.v[q][i] = (TV)y;
       pd[q] += (A)rh.v[q][i] * y;
     }
+  };
+  if constexpr (K > 0) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
+    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+      const int64_t row0 = tix * kTileRows;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      const int64_t i = row0 + threadIdx.x;
+      if (i < op.n) {
+        A acc[NRHS];
+        if constexpr (IsFF<TW, TV>::value)
+          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)p2.v, acc);
+        else
+          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)p.v, acc);
+        finish_row(i, acc);
+      }
+    }
+  } else {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * kThreads) {
+      A acc[NRHS];
+      if constexpr (IsFF<TW, TV>::value)
+        gather_ff<K, NRHS>(op, i, (const float2* const*)p2.v, acc);
+      else
+        gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
+      finish_row(i, acc);
+    }
   }
   double vv[kNV] = {(double)pd[0], (double)pd[1], 0, 0, 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
+    if (sc->stage_err) sc->done = 1;
     for (int q = 0; q < NRHS; ++q) {
       if (!sc->active[q]) continue;
       const double rv = t[q];
@@ -336,7 +489,7 @@ __global__ void __launch_bounds__(kThreads)
   });
 }
 
-// t = A s ; reduce (t, s), (t, t)
+// t = A s ; reduce (t, s), (t, t)  (staged tiles when K > 0)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr,
@@ -346,13 +499,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double sh[kNV * kThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_s : (A)0;
   A pts[2] = {0, 0}, ptt[2] = {0, 0};
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
-       i += (int64_t)gridDim.x * kThreads) {
-    A acc[NRHS];
-    if constexpr (IsFF<TW, TV>::value)
-      gather_ff<K, NRHS>(op, i, (const float2* const*)s2.v, acc);
-    else
-      gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
+  auto finish_row = [&](int64_t i, A* acc) {
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
       A y = acc[q];
@@ -363,9 +510,42 @@ __global__ void __launch_bounds__(kThreads)
       pts[q] += y * si;
       ptt[q] += y * y;
     }
+  };
+  if constexpr (K > 0) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
+    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+      const int64_t row0 = tix * kTileRows;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      const int64_t i = row0 + threadIdx.x;
+      if (i < op.n) {
+        A acc[NRHS];
+        if constexpr (IsFF<TW, TV>::value)
+          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)s2.v, acc);
+        else
+          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)s.v, acc);
+        finish_row(i, acc);
+      }
+    }
+  } else {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * kThreads) {
+      A acc[NRHS];
+      if constexpr (IsFF<TW, TV>::value)
+        gather_ff<K, NRHS>(op, i, (const float2* const*)s2.v, acc);
+      else
+        gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
+      finish_row(i, acc);
+    }
   }
   double vv[kNV] = {(double)pts[0], (double)ptt[0], (double)pts[1], (double)ptt[1], 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+    if (sc->stage_err) sc->done = 1;
     for (int q = 0; q < NRHS; ++q) {
       if (!sc->active[q] || sc->half[q]) continue;
       const double ts = tt[2 * q], t2 = tt[2 * q + 1];
@@ -1095,6 +1275,28 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   double* sigx = P->dscal;
   KScal* h = (KScal*)ctx->host_pinned;
   int total = 0;
+  // staged SpMV launches: one EllStage of dynamic shared memory per block
+  size_t smem = 0;
+  int Gs = G;
+  if constexpr (K > 0) {
+    smem = sizeof(EllStage<K, TW>);
+    const int bps = (int)std::max<size_t>(1, (200u * 1024u) / smem);
+    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
+    Gs = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * std::min(bps, 8));
+    if (Gs < 1) Gs = 1;
+    int rc0 = check_cuda(ctx,
+                         cudaFuncSetAttribute(k_spmv_p<K, NRHS, RANK1, TW, TV>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "smem attribute");
+    if (!rc0)
+      rc0 = check_cuda(ctx,
+                       cudaFuncSetAttribute(k_spmv_s<K, NRHS, RANK1, TW, TV>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem),
+                       "smem attribute");
+    if (rc0) return rc0;
+  }
   for (int q = 0; q < NRHS; ++q) {
     int rc = check_cuda(ctx, cudaMemcpyAsync(work[6][q], x[q], sizeof(TV) * op.n,
                                              cudaMemcpyDeviceToDevice, st),
@@ -1128,12 +1330,12 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (prof) n = std::min(n, StepPlan::kEv / 4);
       for (int it = 0; it < n; ++it) {
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_p<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
+        k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
                                                         S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_s<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, S, T, P->sc, P->gr, S2);
+        k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, S, T, P->sc, P->gr, S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
         k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
@@ -1146,6 +1348,8 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       chunk = std::min(chunk * 2, 64);
     }
     total += h->iters;
+    if (h->stage_err)
+      return set_error(ctx, RBFFD_ERR_CUDA, "SpMV tile copy did not complete (bounded wait)");
     double worst = 0.0;
     bool conv = true;
     for (int q = 0; q < NRHS; ++q) {
