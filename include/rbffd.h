@@ -268,6 +268,16 @@ typedef struct rbffd_stats {
 int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const double* gu,
                const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream);
 
+/*
+ * rbffd_probe_fma - measured FMA throughput of the device (no counterpart in
+ * the paper): 8 independent FMA chains per thread, 8 blocks of 256 threads
+ * per SM, `iters` FMAs per chain, timed with CUDA events on `stream`.
+ * dtype RBFFD_F64 or RBFFD_F32; *gflops (HOST) receives 2 * FMAs / s / 1e9.
+ * Used as the arithmetic roofline of the FP64 weight solves.  Synchronises.
+ */
+int rbffd_probe_fma(rbffd_ctx* ctx, int32_t dtype, int32_t iters, double* gflops,
+                    cudaStream_t stream);
+
 /* Adjoint variables of a state (FP64 device arrays owned by the caller):
  * dJ/du, dJ/dv (N), dJ/dC_{j-1}(u), dJ/dC_{j-1}(v) (N), dJ/dp~ (M). */
 typedef struct rbffd_adjoint {

@@ -107,6 +107,8 @@ PROTOTYPES = {
                                               C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
                                               C.c_uint32, C.c_void_p, C.c_void_p, C.c_int64,
                                               C.POINTER(C.c_int64), C.c_void_p]),
+    "rbffd_probe_fma": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                  C.c_void_p]),
     "rbffd_apply_op": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "rbffd_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC), C.c_void_p,
@@ -385,6 +387,13 @@ def adjoint_step(ctx: Context, flow: Flow, fwd: State, lam: Adjoint, grad_gu, gr
     ctx.check(lib().rbffd_adjoint_step(ctx.handle, C.byref(fc), C.byref(sc), C.byref(ac),
                                        _ptr(grad_gu), _ptr(grad_gv), C.byref(st), _stream()))
     return st.as_dict()
+
+
+def probe_fma(ctx: Context, dtype: int = F64, iters: int = 4096) -> float:
+    """rbffd_probe_fma: measured FMA throughput in GFLOP/s."""
+    g = C.c_double(0.0)
+    ctx.check(lib().rbffd_probe_fma(ctx.handle, dtype, iters, C.byref(g), _stream()))
+    return g.value
 
 
 def version() -> int:
