@@ -115,7 +115,7 @@ __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, co
 // cp.async.bulk copies that complete on an mbarrier.  The threads then gather
 // x for their own row with every address already on chip, so the streaming
 // part of the SpMV never waits on the gathers.
-constexpr int kTileRows = 256;
+constexpr int kTileRows = 128;  // rows per staged tile; blocks run 128 threads
 constexpr long long kSpinLimit = 1ll << 22;  // bounded mbarrier wait (a tile lands in microseconds)
 
 template <int K, typename TW>
@@ -155,40 +155,72 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Stage rows [row0, row0 + 256) of (idx, w); every thread returns once the
-// copies have landed, or false after kSpinLimit polls (then *err is set).
+// Issue the bulk copies of rows [row0, row0 + kTileRows) of (idx, w) into a
+// tile (one thread).  The copy size is rounded to the 32-row padding of ld.
 template <int K, typename TW>
-__device__ __forceinline__ bool stage_tile(EllStage<K, TW>* tile, uint64_t* bar, uint32_t& phase,
+__device__ __forceinline__ void issue_tile(EllStage<K, TW>* tile, uint64_t* bar,
                                            const int32_t* __restrict__ gidx,
-                                           const TW* __restrict__ gw, int64_t ld, int64_t row0,
-                                           int* err) {
-  __syncthreads();  // every thread is done with the previous tile
-  if (threadIdx.x == 0) {
-    const int64_t left = ld - row0;
-    const uint32_t rows = (uint32_t)(left < kTileRows ? left : kTileRows);  // multiple of 32
-    const uint32_t bi = rows * 4u, bw = rows * (uint32_t)sizeof(TW);
-    mbar_expect_tx(bar, (uint32_t)K * (bi + bw));
+                                           const TW* __restrict__ gw, int64_t ld, int64_t row0) {
+  const int64_t left = ld - row0;
+  const uint32_t rows = (uint32_t)(left < kTileRows ? left : kTileRows);  // multiple of 32
+  const uint32_t bi = rows * 4u, bw = rows * (uint32_t)sizeof(TW);
+  mbar_expect_tx(bar, (uint32_t)K * (bi + bw));
 #pragma unroll 4
-    for (int s = 0; s < K; ++s) {
-      bulk_g2s(&tile->idx[s * kTileRows], gidx + s * ld + row0, bi, bar);
-      bulk_g2s(&tile->w[s * kTileRows], gw + s * ld + row0, bw, bar);
-    }
+  for (int s = 0; s < K; ++s) {
+    bulk_g2s(&tile->idx[s * kTileRows], gidx + s * ld + row0, bi, bar);
+    bulk_g2s(&tile->w[s * kTileRows], gw + s * ld + row0, bw, bar);
   }
+}
+
+// Wait (bounded) until a tile's copies have landed; one verdict per block.
+__device__ __forceinline__ bool wait_tile(uint64_t* bar, uint32_t& phase, int* err) {
   long long spins = 0;
   bool ok;
   while (!(ok = mbar_try_wait(bar, phase)) && ++spins < kSpinLimit) {
   }
-  // one verdict for the whole block, so every thread leaves the loop together
   if (!__syncthreads_and(ok ? 1 : 0)) {
     if (threadIdx.x == 0) atomicOr(err, 4);
-    // give the copies in flight one more bounded chance to land before the block leaves
-    spins = 0;
+    spins = 0;  // one more bounded chance for the copies in flight to land
     while (!mbar_try_wait(bar, phase) && ++spins < kSpinLimit) {
     }
     return false;
   }
   phase ^= 1u;
   return true;
+}
+
+// Walk the tiles of this block with two buffers: the copies of the next tile
+// are in flight while the current one is consumed.  body(tile, i_local, i).
+template <int K, typename TW, typename Body>
+__device__ __forceinline__ void staged_rows(const int32_t* __restrict__ gidx,
+                                            const TW* __restrict__ gw, int64_t ld, int64_t n,
+                                            int* err, Body body) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  auto* tiles = reinterpret_cast<EllStage<K, TW>*>(dsm);  // two buffers
+  __shared__ uint64_t bar[2];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  uint32_t phase[2] = {0u, 0u};
+  const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
+  int64_t tix = blockIdx.x;
+  if (tix < ntiles && threadIdx.x == 0) issue_tile<K, TW>(&tiles[0], &bar[0], gidx, gw, ld, tix * kTileRows);
+  for (int cur = 0; tix < ntiles; tix += gridDim.x, cur ^= 1) {
+    const int64_t nxt = tix + gridDim.x;
+    // the other buffer was released by the __syncthreads at the end of the last round
+    if (nxt < ntiles && threadIdx.x == 0)
+      issue_tile<K, TW>(&tiles[cur ^ 1], &bar[cur ^ 1], gidx, gw, ld, nxt * kTileRows);
+    if (!wait_tile(&bar[cur], phase[cur], err)) {
+      // drain the other buffer's copies (bounded) before leaving
+      if (nxt < ntiles) wait_tile(&bar[cur ^ 1], phase[cur ^ 1], err);
+      return;
+    }
+    const int64_t i = tix * kTileRows + threadIdx.x;
+    if (i < n) body(&tiles[cur], (int)threadIdx.x, i);
+    __syncthreads();  // every thread is done with this buffer
+  }
 }
 
 template <typename TV, int NRHS>
@@ -406,29 +438,18 @@ __global__ void __launch_bounds__(kThreads)
     }
   };
   if constexpr (K > 0) {
-    extern __shared__ __align__(128) unsigned char dsm[];
-    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
-    __shared__ uint64_t bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    uint32_t phase = 0;
-    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
-    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
-      const int64_t row0 = tix * kTileRows;
-      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
-      const int64_t i = row0 + threadIdx.x;
-      if (i < op.n) {
-        A acc[NRHS];
-        if constexpr (IsFF<TW, TV>::value)
-          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)p2.v, acc);
-        else
-          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)p.v, acc);
-        finish_row(i, acc);
-      }
-    }
+    staged_rows<K, TW>(op.idx, op.w, op.ld, op.n, &sc->stage_err,
+                       [&](const EllStage<K, TW>* tile, int tid, int64_t i) {
+                         A acc[NRHS];
+                         if constexpr (IsFF<TW, TV>::value)
+                           gather_tile_ff<K, NRHS>(tile, tid, (const float2* const*)p2.v, acc);
+                         else
+                           gather_tile<K, NRHS>(tile, tid, (const TV* const*)p.v, acc);
+                         finish_row(i, acc);
+                       });
   } else {
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
-         i += (int64_t)gridDim.x * kThreads) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
       A acc[NRHS];
       if constexpr (IsFF<TW, TV>::value)
         gather_ff<K, NRHS>(op, i, (const float2* const*)p2.v, acc);
@@ -512,29 +533,18 @@ __global__ void __launch_bounds__(kThreads)
     }
   };
   if constexpr (K > 0) {
-    extern __shared__ __align__(128) unsigned char dsm[];
-    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
-    __shared__ uint64_t bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    uint32_t phase = 0;
-    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
-    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
-      const int64_t row0 = tix * kTileRows;
-      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
-      const int64_t i = row0 + threadIdx.x;
-      if (i < op.n) {
-        A acc[NRHS];
-        if constexpr (IsFF<TW, TV>::value)
-          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)s2.v, acc);
-        else
-          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)s.v, acc);
-        finish_row(i, acc);
-      }
-    }
+    staged_rows<K, TW>(op.idx, op.w, op.ld, op.n, &sc->stage_err,
+                       [&](const EllStage<K, TW>* tile, int tid, int64_t i) {
+                         A acc[NRHS];
+                         if constexpr (IsFF<TW, TV>::value)
+                           gather_tile_ff<K, NRHS>(tile, tid, (const float2* const*)s2.v, acc);
+                         else
+                           gather_tile<K, NRHS>(tile, tid, (const TV* const*)s.v, acc);
+                         finish_row(i, acc);
+                       });
   } else {
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
-         i += (int64_t)gridDim.x * kThreads) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
       A acc[NRHS];
       if constexpr (IsFF<TW, TV>::value)
         gather_ff<K, NRHS>(op, i, (const float2* const*)s2.v, acc);
@@ -1278,8 +1288,10 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   // staged SpMV launches: one EllStage of dynamic shared memory per block
   size_t smem = 0;
   int Gs = G;
+  int Ts = kThreads;
   if constexpr (K > 0) {
-    smem = sizeof(EllStage<K, TW>);
+    smem = 2 * sizeof(EllStage<K, TW>);  // double buffer
+    Ts = kTileRows;
     const int bps = (int)std::max<size_t>(1, (200u * 1024u) / smem);
     const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
     Gs = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * std::min(bps, 8));
@@ -1330,12 +1342,12 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (prof) n = std::min(n, StepPlan::kEv / 4);
       for (int it = 0; it < n; ++it) {
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
+        k_spmv_p<K, NRHS, RANK1><<<Gs, Ts, smem, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
                                                         S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, S, T, P->sc, P->gr, S2);
+        k_spmv_s<K, NRHS, RANK1><<<Gs, Ts, smem, st>>>(op, S, T, P->sc, P->gr, S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
         k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
