@@ -190,11 +190,12 @@ __device__ __forceinline__ bool wait_tile(uint64_t* bar, uint32_t& phase, int* e
 }
 
 // Walk the tiles of this block with two buffers: the copies of the next tile
-// are in flight while the current one is consumed.  body(tile, i_local, i).
-template <int K, typename TW, typename Body>
+// are in flight while the current one is consumed by tile_fn(tile, row0),
+// which every thread of the block calls.
+template <int K, typename TW, typename TileFn>
 __device__ __forceinline__ void staged_rows(const int32_t* __restrict__ gidx,
                                             const TW* __restrict__ gw, int64_t ld, int64_t n,
-                                            int* err, Body body) {
+                                            int* err, TileFn tile_fn) {
   extern __shared__ __align__(128) unsigned char dsm[];
   auto* tiles = reinterpret_cast<EllStage<K, TW>*>(dsm);  // two buffers
   __shared__ uint64_t bar[2];
@@ -206,7 +207,8 @@ __device__ __forceinline__ void staged_rows(const int32_t* __restrict__ gidx,
   uint32_t phase[2] = {0u, 0u};
   const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
   int64_t tix = blockIdx.x;
-  if (tix < ntiles && threadIdx.x == 0) issue_tile<K, TW>(&tiles[0], &bar[0], gidx, gw, ld, tix * kTileRows);
+  if (tix < ntiles && threadIdx.x == 0)
+    issue_tile<K, TW>(&tiles[0], &bar[0], gidx, gw, ld, tix * kTileRows);
   for (int cur = 0; tix < ntiles; tix += gridDim.x, cur ^= 1) {
     const int64_t nxt = tix + gridDim.x;
     // the other buffer was released by the __syncthreads at the end of the last round
@@ -217,11 +219,17 @@ __device__ __forceinline__ void staged_rows(const int32_t* __restrict__ gidx,
       if (nxt < ntiles) wait_tile(&bar[cur ^ 1], phase[cur ^ 1], err);
       return;
     }
-    const int64_t i = tix * kTileRows + threadIdx.x;
-    if (i < n) body(&tiles[cur], (int)threadIdx.x, i);
+    tile_fn(&tiles[cur], tix * kTileRows);
     __syncthreads();  // every thread is done with this buffer
   }
 }
+
+// Staged SpMV thread layout: 512 threads per block, 16 warps.  Warp w handles
+// rows 32*(w/4) .. +31 of the tile and the slots s = w%4, w%4 + 4, ... so the
+// four warps of a row group split the 28 slots and their partial sums meet in
+// shared memory; the warp with w%4 == 0 finishes its 32 rows.
+constexpr int kSplit = 4;
+constexpr int kStagedThreads = kTileRows * kSplit;
 
 template <typename TV, int NRHS>
 struct Vecs {
@@ -325,6 +333,99 @@ __device__ __forceinline__ void gather_tile_ff(const EllStage<K, float>* t, int 
   for (int r = 0; r < NRHS; ++r) acc[r] = (double)sh[r] + (double)sl[r];
 }
 
+template <int K, int NRHS, typename TW, typename TV>
+__device__ __forceinline__ void partial_tile(const EllStage<K, TW>* t, int row, int sg,
+                                             const TV* const* x, typename Acc<TV>::t* acc) {
+  using A = typename Acc<TV>::t;
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = 0;
+#pragma unroll
+  for (int s = sg; s < K; s += kSplit) {
+    const int j = t->idx[s * kTileRows + row];
+    const A w = (A)t->w[s * kTileRows + row];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
+  }
+}
+
+template <int K, int NRHS>
+__device__ __forceinline__ void partial_tile_ff(const EllStage<K, float>* t, int row, int sg,
+                                                const float2* const* x2, float* sh, float* sl) {
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) sh[r] = sl[r] = 0.f;
+#pragma unroll
+  for (int s = sg; s < K; s += kSplit) {
+    const int j = t->idx[s * kTileRows + row];
+    const float w = t->w[s * kTileRows + row];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      const float2 xj = x2[r][j];
+      float p, e, u, ue;
+      two_prod(w, xj.x, p, e);
+      e = fmaf(w, xj.y, e);
+      two_sum(sh[r], p, u, ue);
+      sh[r] = u;
+      sl[r] += ue + e;
+    }
+  }
+}
+
+// Sum of the kSplit partial sums of row `row` (the finishing warp calls it).
+template <int NRHS, typename TW, typename TV>
+struct PartialBuf {
+  // float-float: (hi, lo) per split, right side and row; plain: one value
+  typename Acc<TV>::t v[kSplit][NRHS][kTileRows];
+  float lo[IsFF<TW, TV>::value ? kSplit : 1][NRHS][kTileRows];
+};
+
+// Gather a whole tile with the split layout; finish(i, acc) for each row < n.
+template <int K, int NRHS, typename TW, typename TV, typename Finish>
+__device__ __forceinline__ void spmv_tile(const EllStage<K, TW>* tile, int64_t row0, int64_t n,
+                                          const TV* const* x, const float2* const* x2,
+                                          PartialBuf<NRHS, TW, TV>* pb, Finish finish) {
+  using A = typename Acc<TV>::t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = (warp / kSplit) * 32 + lane, sg = warp % kSplit;
+  if constexpr (IsFF<TW, TV>::value) {
+    float sh[NRHS], sl[NRHS];
+    partial_tile_ff<K, NRHS>(tile, row, sg, x2, sh, sl);
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      pb->v[sg][r][row] = sh[r];
+      pb->lo[sg][r][row] = sl[r];
+    }
+  } else {
+    A acc[NRHS];
+    partial_tile<K, NRHS>(tile, row, sg, x, acc);
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) pb->v[sg][r][row] = acc[r];
+  }
+  __syncthreads();
+  if (sg == 0 && row0 + row < n) {
+    A acc[NRHS];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      if constexpr (IsFF<TW, TV>::value) {
+        float hi = (float)pb->v[0][r][row], lo = pb->lo[0][r][row];
+#pragma unroll
+        for (int g = 1; g < kSplit; ++g) {
+          float u, ue;
+          two_sum(hi, (float)pb->v[g][r][row], u, ue);
+          hi = u;
+          lo += ue + pb->lo[g][r][row];
+        }
+        acc[r] = (A)((double)hi + (double)lo);
+      } else {
+        A a = pb->v[0][r][row];
+#pragma unroll
+        for (int g = 1; g < kSplit; ++g) a += pb->v[g][r][row];
+        acc[r] = a;
+      }
+    }
+    finish(row0 + row, acc);
+  }
+}
+
 // ----------------------------------------------------------- Krylov kernels
 // sum_i x_i, or sum_i c_i x_i when c is given
 template <typename TV>
@@ -419,12 +520,12 @@ __global__ void __launch_bounds__(kThreads)
 // v = A p ; reduce (rh, v).  K > 0: rows come in staged tiles (dynamic shared
 // memory holds one EllStage); K == 0: rows are read directly.
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kStagedThreads)
     k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
              GridReduce gr, Split<NRHS> p2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  __shared__ double sh[kNV * kStagedThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_p : (A)0;
   A pd[2] = {0, 0};
   auto finish_row = [&](int64_t i, A* acc) {
@@ -438,14 +539,11 @@ __global__ void __launch_bounds__(kThreads)
     }
   };
   if constexpr (K > 0) {
+    __shared__ PartialBuf<NRHS, TW, TV> pb;
     staged_rows<K, TW>(op.idx, op.w, op.ld, op.n, &sc->stage_err,
-                       [&](const EllStage<K, TW>* tile, int tid, int64_t i) {
-                         A acc[NRHS];
-                         if constexpr (IsFF<TW, TV>::value)
-                           gather_tile_ff<K, NRHS>(tile, tid, (const float2* const*)p2.v, acc);
-                         else
-                           gather_tile<K, NRHS>(tile, tid, (const TV* const*)p.v, acc);
-                         finish_row(i, acc);
+                       [&](const EllStage<K, TW>* tile, int64_t row0) {
+                         spmv_tile<K, NRHS>(tile, row0, op.n, (const TV* const*)p.v,
+                                            (const float2* const*)p2.v, &pb, finish_row);
                        });
   } else {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.n;
@@ -512,12 +610,12 @@ __global__ void __launch_bounds__(kThreads)
 
 // t = A s ; reduce (t, s), (t, t)  (staged tiles when K > 0)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kStagedThreads)
     k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr,
              Split<NRHS> s2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  __shared__ double sh[kNV * kStagedThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_s : (A)0;
   A pts[2] = {0, 0}, ptt[2] = {0, 0};
   auto finish_row = [&](int64_t i, A* acc) {
@@ -533,14 +631,11 @@ __global__ void __launch_bounds__(kThreads)
     }
   };
   if constexpr (K > 0) {
+    __shared__ PartialBuf<NRHS, TW, TV> pb;
     staged_rows<K, TW>(op.idx, op.w, op.ld, op.n, &sc->stage_err,
-                       [&](const EllStage<K, TW>* tile, int tid, int64_t i) {
-                         A acc[NRHS];
-                         if constexpr (IsFF<TW, TV>::value)
-                           gather_tile_ff<K, NRHS>(tile, tid, (const float2* const*)s2.v, acc);
-                         else
-                           gather_tile<K, NRHS>(tile, tid, (const TV* const*)s.v, acc);
-                         finish_row(i, acc);
+                       [&](const EllStage<K, TW>* tile, int64_t row0) {
+                         spmv_tile<K, NRHS>(tile, row0, op.n, (const TV* const*)s.v,
+                                            (const float2* const*)s2.v, &pb, finish_row);
                        });
   } else {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.n;
@@ -1291,7 +1386,7 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   int Ts = kThreads;
   if constexpr (K > 0) {
     smem = 2 * sizeof(EllStage<K, TW>);  // double buffer
-    Ts = kTileRows;
+    Ts = kStagedThreads;
     const int bps = (int)std::max<size_t>(1, (200u * 1024u) / smem);
     const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
     Gs = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * std::min(bps, 8));
