@@ -115,7 +115,7 @@ __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, co
 // cp.async.bulk copies that complete on an mbarrier.  The threads then gather
 // x for their own row with every address already on chip, so the streaming
 // part of the SpMV never waits on the gathers.
-constexpr int kTileRows = 128;  // rows per staged tile; blocks run 128 threads
+constexpr int kTileRows = 256;
 constexpr long long kSpinLimit = 1ll << 22;  // bounded mbarrier wait (a tile lands in microseconds)
 
 template <int K, typename TW>
@@ -155,32 +155,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Issue the bulk copies of rows [row0, row0 + kTileRows) of (idx, w) into a
-// tile (one thread).  The copy size is rounded to the 32-row padding of ld.
+// Stage rows [row0, row0 + 256) of (idx, w); every thread returns once the
+// copies have landed, or false after kSpinLimit polls (then *err is set).
 template <int K, typename TW>
-__device__ __forceinline__ void issue_tile(EllStage<K, TW>* tile, uint64_t* bar,
+__device__ __forceinline__ bool stage_tile(EllStage<K, TW>* tile, uint64_t* bar, uint32_t& phase,
                                            const int32_t* __restrict__ gidx,
-                                           const TW* __restrict__ gw, int64_t ld, int64_t row0) {
-  const int64_t left = ld - row0;
-  const uint32_t rows = (uint32_t)(left < kTileRows ? left : kTileRows);  // multiple of 32
-  const uint32_t bi = rows * 4u, bw = rows * (uint32_t)sizeof(TW);
-  mbar_expect_tx(bar, (uint32_t)K * (bi + bw));
+                                           const TW* __restrict__ gw, int64_t ld, int64_t row0,
+                                           int* err) {
+  __syncthreads();  // every thread is done with the previous tile
+  if (threadIdx.x == 0) {
+    const int64_t left = ld - row0;
+    const uint32_t rows = (uint32_t)(left < kTileRows ? left : kTileRows);  // multiple of 32
+    const uint32_t bi = rows * 4u, bw = rows * (uint32_t)sizeof(TW);
+    mbar_expect_tx(bar, (uint32_t)K * (bi + bw));
 #pragma unroll 4
-  for (int s = 0; s < K; ++s) {
-    bulk_g2s(&tile->idx[s * kTileRows], gidx + s * ld + row0, bi, bar);
-    bulk_g2s(&tile->w[s * kTileRows], gw + s * ld + row0, bw, bar);
+    for (int s = 0; s < K; ++s) {
+      bulk_g2s(&tile->idx[s * kTileRows], gidx + s * ld + row0, bi, bar);
+      bulk_g2s(&tile->w[s * kTileRows], gw + s * ld + row0, bw, bar);
+    }
   }
-}
-
-// Wait (bounded) until a tile's copies have landed; one verdict per block.
-__device__ __forceinline__ bool wait_tile(uint64_t* bar, uint32_t& phase, int* err) {
   long long spins = 0;
   bool ok;
   while (!(ok = mbar_try_wait(bar, phase)) && ++spins < kSpinLimit) {
   }
+  // one verdict for the whole block, so every thread leaves the loop together
   if (!__syncthreads_and(ok ? 1 : 0)) {
     if (threadIdx.x == 0) atomicOr(err, 4);
-    spins = 0;  // one more bounded chance for the copies in flight to land
+    // give the copies in flight one more bounded chance to land before the block leaves
+    spins = 0;
     while (!mbar_try_wait(bar, phase) && ++spins < kSpinLimit) {
     }
     return false;
@@ -188,48 +190,6 @@ __device__ __forceinline__ bool wait_tile(uint64_t* bar, uint32_t& phase, int* e
   phase ^= 1u;
   return true;
 }
-
-// Walk the tiles of this block with two buffers: the copies of the next tile
-// are in flight while the current one is consumed by tile_fn(tile, row0),
-// which every thread of the block calls.
-template <int K, typename TW, typename TileFn>
-__device__ __forceinline__ void staged_rows(const int32_t* __restrict__ gidx,
-                                            const TW* __restrict__ gw, int64_t ld, int64_t n,
-                                            int* err, TileFn tile_fn) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  auto* tiles = reinterpret_cast<EllStage<K, TW>*>(dsm);  // two buffers
-  __shared__ uint64_t bar[2];
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-  }
-  __syncthreads();
-  uint32_t phase[2] = {0u, 0u};
-  const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
-  int64_t tix = blockIdx.x;
-  if (tix < ntiles && threadIdx.x == 0)
-    issue_tile<K, TW>(&tiles[0], &bar[0], gidx, gw, ld, tix * kTileRows);
-  for (int cur = 0; tix < ntiles; tix += gridDim.x, cur ^= 1) {
-    const int64_t nxt = tix + gridDim.x;
-    // the other buffer was released by the __syncthreads at the end of the last round
-    if (nxt < ntiles && threadIdx.x == 0)
-      issue_tile<K, TW>(&tiles[cur ^ 1], &bar[cur ^ 1], gidx, gw, ld, nxt * kTileRows);
-    if (!wait_tile(&bar[cur], phase[cur], err)) {
-      // drain the other buffer's copies (bounded) before leaving
-      if (nxt < ntiles) wait_tile(&bar[cur ^ 1], phase[cur ^ 1], err);
-      return;
-    }
-    tile_fn(&tiles[cur], tix * kTileRows);
-    __syncthreads();  // every thread is done with this buffer
-  }
-}
-
-// Staged SpMV thread layout: 512 threads per block, 16 warps.  Warp w handles
-// rows 32*(w/4) .. +31 of the tile and the slots s = w%4, w%4 + 4, ... so the
-// four warps of a row group split the 28 slots and their partial sums meet in
-// shared memory; the warp with w%4 == 0 finishes its 32 rows.
-constexpr int kSplit = 4;
-constexpr int kStagedThreads = kTileRows * kSplit;
 
 template <typename TV, int NRHS>
 struct Vecs {
@@ -333,99 +293,6 @@ __device__ __forceinline__ void gather_tile_ff(const EllStage<K, float>* t, int 
   for (int r = 0; r < NRHS; ++r) acc[r] = (double)sh[r] + (double)sl[r];
 }
 
-template <int K, int NRHS, typename TW, typename TV>
-__device__ __forceinline__ void partial_tile(const EllStage<K, TW>* t, int row, int sg,
-                                             const TV* const* x, typename Acc<TV>::t* acc) {
-  using A = typename Acc<TV>::t;
-#pragma unroll
-  for (int r = 0; r < NRHS; ++r) acc[r] = 0;
-#pragma unroll
-  for (int s = sg; s < K; s += kSplit) {
-    const int j = t->idx[s * kTileRows + row];
-    const A w = (A)t->w[s * kTileRows + row];
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
-  }
-}
-
-template <int K, int NRHS>
-__device__ __forceinline__ void partial_tile_ff(const EllStage<K, float>* t, int row, int sg,
-                                                const float2* const* x2, float* sh, float* sl) {
-#pragma unroll
-  for (int r = 0; r < NRHS; ++r) sh[r] = sl[r] = 0.f;
-#pragma unroll
-  for (int s = sg; s < K; s += kSplit) {
-    const int j = t->idx[s * kTileRows + row];
-    const float w = t->w[s * kTileRows + row];
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) {
-      const float2 xj = x2[r][j];
-      float p, e, u, ue;
-      two_prod(w, xj.x, p, e);
-      e = fmaf(w, xj.y, e);
-      two_sum(sh[r], p, u, ue);
-      sh[r] = u;
-      sl[r] += ue + e;
-    }
-  }
-}
-
-// Sum of the kSplit partial sums of row `row` (the finishing warp calls it).
-template <int NRHS, typename TW, typename TV>
-struct PartialBuf {
-  // float-float: (hi, lo) per split, right side and row; plain: one value
-  typename Acc<TV>::t v[kSplit][NRHS][kTileRows];
-  float lo[IsFF<TW, TV>::value ? kSplit : 1][NRHS][kTileRows];
-};
-
-// Gather a whole tile with the split layout; finish(i, acc) for each row < n.
-template <int K, int NRHS, typename TW, typename TV, typename Finish>
-__device__ __forceinline__ void spmv_tile(const EllStage<K, TW>* tile, int64_t row0, int64_t n,
-                                          const TV* const* x, const float2* const* x2,
-                                          PartialBuf<NRHS, TW, TV>* pb, Finish finish) {
-  using A = typename Acc<TV>::t;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = (warp / kSplit) * 32 + lane, sg = warp % kSplit;
-  if constexpr (IsFF<TW, TV>::value) {
-    float sh[NRHS], sl[NRHS];
-    partial_tile_ff<K, NRHS>(tile, row, sg, x2, sh, sl);
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) {
-      pb->v[sg][r][row] = sh[r];
-      pb->lo[sg][r][row] = sl[r];
-    }
-  } else {
-    A acc[NRHS];
-    partial_tile<K, NRHS>(tile, row, sg, x, acc);
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) pb->v[sg][r][row] = acc[r];
-  }
-  __syncthreads();
-  if (sg == 0 && row0 + row < n) {
-    A acc[NRHS];
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) {
-      if constexpr (IsFF<TW, TV>::value) {
-        float hi = (float)pb->v[0][r][row], lo = pb->lo[0][r][row];
-#pragma unroll
-        for (int g = 1; g < kSplit; ++g) {
-          float u, ue;
-          two_sum(hi, (float)pb->v[g][r][row], u, ue);
-          hi = u;
-          lo += ue + pb->lo[g][r][row];
-        }
-        acc[r] = (A)((double)hi + (double)lo);
-      } else {
-        A a = pb->v[0][r][row];
-#pragma unroll
-        for (int g = 1; g < kSplit; ++g) a += pb->v[g][r][row];
-        acc[r] = a;
-      }
-    }
-    finish(row0 + row, acc);
-  }
-}
-
 // ----------------------------------------------------------- Krylov kernels
 // sum_i x_i, or sum_i c_i x_i when c is given
 template <typename TV>
@@ -520,12 +387,12 @@ __global__ void __launch_bounds__(kThreads)
 // v = A p ; reduce (rh, v).  K > 0: rows come in staged tiles (dynamic shared
 // memory holds one EllStage); K == 0: rows are read directly.
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
-__global__ void __launch_bounds__(kStagedThreads)
+__global__ void __launch_bounds__(kThreads)
     k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
              GridReduce gr, Split<NRHS> p2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
-  __shared__ double sh[kNV * kStagedThreads / 32];
+  __shared__ double sh[kNV * kThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_p : (A)0;
   A pd[2] = {0, 0};
   auto finish_row = [&](int64_t i, A* acc) {
@@ -539,15 +406,29 @@ __global__ void __launch_bounds__(kStagedThreads)
     }
   };
   if constexpr (K > 0) {
-    __shared__ PartialBuf<NRHS, TW, TV> pb;
-    staged_rows<K, TW>(op.idx, op.w, op.ld, op.n, &sc->stage_err,
-                       [&](const EllStage<K, TW>* tile, int64_t row0) {
-                         spmv_tile<K, NRHS>(tile, row0, op.n, (const TV* const*)p.v,
-                                            (const float2* const*)p2.v, &pb, finish_row);
-                       });
+    extern __shared__ __align__(128) unsigned char dsm[];
+    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
+    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+      const int64_t row0 = tix * kTileRows;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      const int64_t i = row0 + threadIdx.x;
+      if (i < op.n) {
+        A acc[NRHS];
+        if constexpr (IsFF<TW, TV>::value)
+          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)p2.v, acc);
+        else
+          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)p.v, acc);
+        finish_row(i, acc);
+      }
+    }
   } else {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * kThreads) {
       A acc[NRHS];
       if constexpr (IsFF<TW, TV>::value)
         gather_ff<K, NRHS>(op, i, (const float2* const*)p2.v, acc);
@@ -610,12 +491,12 @@ __global__ void __launch_bounds__(kThreads)
 
 // t = A s ; reduce (t, s), (t, t)  (staged tiles when K > 0)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
-__global__ void __launch_bounds__(kStagedThreads)
+__global__ void __launch_bounds__(kThreads)
     k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr,
              Split<NRHS> s2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
-  __shared__ double sh[kNV * kStagedThreads / 32];
+  __shared__ double sh[kNV * kThreads / 32];
   const A sig = RANK1 ? (A)sc->sum_s : (A)0;
   A pts[2] = {0, 0}, ptt[2] = {0, 0};
   auto finish_row = [&](int64_t i, A* acc) {
@@ -631,15 +512,29 @@ __global__ void __launch_bounds__(kStagedThreads)
     }
   };
   if constexpr (K > 0) {
-    __shared__ PartialBuf<NRHS, TW, TV> pb;
-    staged_rows<K, TW>(op.idx, op.w, op.ld, op.n, &sc->stage_err,
-                       [&](const EllStage<K, TW>* tile, int64_t row0) {
-                         spmv_tile<K, NRHS>(tile, row0, op.n, (const TV* const*)s.v,
-                                            (const float2* const*)s2.v, &pb, finish_row);
-                       });
+    extern __shared__ __align__(128) unsigned char dsm[];
+    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
+    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+      const int64_t row0 = tix * kTileRows;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      const int64_t i = row0 + threadIdx.x;
+      if (i < op.n) {
+        A acc[NRHS];
+        if constexpr (IsFF<TW, TV>::value)
+          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)s2.v, acc);
+        else
+          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)s.v, acc);
+        finish_row(i, acc);
+      }
+    }
   } else {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * kThreads) {
       A acc[NRHS];
       if constexpr (IsFF<TW, TV>::value)
         gather_ff<K, NRHS>(op, i, (const float2* const*)s2.v, acc);
@@ -1383,10 +1278,8 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   // staged SpMV launches: one EllStage of dynamic shared memory per block
   size_t smem = 0;
   int Gs = G;
-  int Ts = kThreads;
   if constexpr (K > 0) {
-    smem = 2 * sizeof(EllStage<K, TW>);  // double buffer
-    Ts = kStagedThreads;
+    smem = sizeof(EllStage<K, TW>);
     const int bps = (int)std::max<size_t>(1, (200u * 1024u) / smem);
     const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
     Gs = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * std::min(bps, 8));
@@ -1437,12 +1330,12 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (prof) n = std::min(n, StepPlan::kEv / 4);
       for (int it = 0; it < n; ++it) {
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_p<K, NRHS, RANK1><<<Gs, Ts, smem, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
+        k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
                                                         S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_s<K, NRHS, RANK1><<<Gs, Ts, smem, st>>>(op, S, T, P->sc, P->gr, S2);
+        k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, S, T, P->sc, P->gr, S2);
         if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
         k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
         k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
