@@ -1,0 +1,125 @@
+"""Parity at the benchmark's full size (1,000,000 P-nodes, 2,996,001 V-nodes,
+the launch configuration bench.py times): sampled rows that the oracle
+computes one by one, and properties of a full step that hold at any size."""
+import numpy as np
+import pytest
+
+from oracle import rbffd_oracle as O
+from paper_2206_06495_gb300 import nodesets as ns
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N_SIDE = 1000
+SAMPLES = 64
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2206_06495_gb300 import build
+    build.build()
+    from paper_2206_06495_gb300 import rbffd
+    return rbffd
+
+
+@pytest.fixture(scope="module")
+def big(R):
+    nd = ns.jittered_cavity(N_SIDE, 2)
+    ctx = R.Context()
+    flow = R.flow_from_nodes(ctx, nd, Re=1.0e4, dt=2e-4, tol=1e-10, inner_tol=1e-2,
+                             max_iter=400000)
+    return nd, ctx, flow
+
+
+def _sample(n, rng):
+    # the first and last rows (ragged tail of the last tile) and random rows
+    return np.unique(np.concatenate([[0, n - 1], rng.choice(n, SAMPLES, replace=False)]))
+
+
+@pytest.mark.parametrize("fam", ["vv", "pv", "pp", "vp", "pn"])
+def test_sampled_stencils_and_weights(R, big, fam):
+    nd, ctx, flow = big
+    t = flow.tensors
+    rng = np.random.default_rng(hash(fam) % 1000)
+    if fam == "pn":
+        bnd = np.nonzero(nd.p_boundary)[0]
+        rows = _sample(bnd.size, rng)
+        ax, ay = nd.px[bnd[rows]], nd.py[bnd[rows]]
+        bx, by = nd.px, nd.py
+        ref_idx = O.knn(ax, ay, bx, by, 28, beta_mask=~nd.p_boundary, alpha_self=bnd[rows])
+        ops = [("dx", "pn_dx"), ("dy", "pn_dy")]
+    else:
+        a, b = {"vv": ("v", "v"), "pv": ("p", "v"), "pp": ("p", "p"), "vp": ("v", "p")}[fam]
+        axs, ays = (nd.vx, nd.vy) if a == "v" else (nd.px, nd.py)
+        bx, by = (nd.vx, nd.vy) if b == "v" else (nd.px, nd.py)
+        rows = _sample(axs.size, rng)
+        ax, ay = axs[rows], ays[rows]
+        ref_idx = O.knn(ax, ay, bx, by, 28)
+        ops = [("dx", f"{fam}_dx"), ("dy", f"{fam}_dy")]
+        if fam in ("vv", "pp"):
+            ops.append(("lap", f"{fam}_lap"))
+    got_idx = t[f"{fam}_idx"][:, torch.as_tensor(rows, device="cuda")].T.cpu().numpy()
+    assert np.array_equal(got_idx.astype(np.int64), ref_idx), fam
+    _, W = O.build_weights(ax, ay, bx, by, 28, 7, 3, tuple(o for o, _ in ops), idx=ref_idx)
+    for op, key in ops:
+        got = t[key][:, torch.as_tensor(rows, device="cuda")].T.cpu().numpy()
+        rel = np.abs(got - W[op]).max(1) / np.abs(W[op]).max(1)
+        assert rel.max() < 1e-10, (fam, op, rel.max())
+
+
+@pytest.mark.parametrize("wdt", ["f64", "f32"])
+def test_sampled_spmv_rows(R, big, wdt):
+    """rbffd_apply_op on the 3M-row V->V D_x, checked row by row in FP64."""
+    nd, ctx, flow = big
+    t = flow.tensors
+    f, *_ = ns.wave_test_function(nd.vx, nd.vy)
+    w = t["vv_dx"] if wdt == "f64" else t["vv_dx"].float()
+    x = torch.as_tensor(f, device="cuda")
+    if wdt == "f32":
+        x = x.float()
+    y = R.apply_op(ctx, t["vv_idx"], w, nd.N, nd.N, x)
+    rows = _sample(nd.N, np.random.default_rng(3))
+    ti = torch.as_tensor(rows, device="cuda")
+    idx = t["vv_idx"][:, ti].T.cpu().numpy()
+    ww = w[:, ti].T.double().cpu().numpy()
+    xv = x.double().cpu().numpy()
+    ref = (ww * xv[idx]).sum(1)
+    scale = (np.abs(ww) * np.abs(xv[idx])).sum(1)
+    got = y[ti].double().cpu().numpy()
+    tol = 1e-13 if wdt == "f64" else 2e-6
+    assert (np.abs(got - ref) / scale).max() < tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_step_properties(R, big, precision):
+    """One fractional step of the bench workload: wall data exact, pressure
+    correction mean-free, the correction lowers the interior divergence of the
+    intermediate field, and both implicit solves reached the tolerance."""
+    nd, ctx, flow = big
+    flow.precision = precision
+    st = R.State.zeros(flow)
+    gu = np.zeros(nd.N)
+    gu[nd.v_wall == ns.WALL_TOP] = 1.0
+    gut = torch.as_tensor(gu, device="cuda")
+    gvt = torch.zeros_like(gut)
+    stats = R.step(ctx, flow, st, gut, gvt, 1)
+    assert stats["poisson_relres"] <= 1e-10 and stats["helm_relres"] <= 1e-10
+    u, v = st.u.cpu().numpy(), st.v.cpu().numpy()
+    wall = nd.v_boundary
+    assert np.array_equal(u[wall], gu[wall]) and np.array_equal(v[wall], 0.0 * gu[wall])
+    pt = st.pt.cpu().numpy()
+    assert abs(pt.mean()) <= 1e-12 * max(np.abs(pt).max(), 1e-300)
+    assert np.isfinite(u).all() and np.isfinite(st.p.cpu().numpy()).all()
+    # the correction removes most of the interior divergence that the wall
+    # data alone (u = g on the lid, 0 elsewhere) would carry
+    t = flow.tensors
+
+    def div(uu, vv):
+        d = R.apply_op(ctx, t["pv_idx"], t["pv_dx"], nd.M, nd.N, uu)
+        d = R.apply_op(ctx, t["pv_idx"], t["pv_dy"], nd.M, nd.N, vv, d, 1.0, 1.0)
+        return d.cpu().numpy()[~nd.p_boundary]
+
+    d1 = np.linalg.norm(div(st.u, st.v))
+    d0 = np.linalg.norm(div(gut, gvt))
+    assert d1 < 0.5 * d0, (d1, d0)
