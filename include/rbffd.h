@@ -200,6 +200,15 @@ int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, d
  * overwrite_bc    1 = set wall V-nodes to the wall data after the correction
  * profile         1 = time every SpMV launch of the pressure solves with CUDA
  *                 events on `stream` (reported in rbffd_stats); 0 = off
+ * precond         pressure-solve preconditioner (not in the paper, which does
+ *                 not say how it solves): 0 = none, 1 = one multigrid V-cycle
+ *                 on the weighted graph Laplacian of the P-node edges (right
+ *                 preconditioning; the converged solution is unchanged).  The
+ *                 hierarchy is built on the host once per flow description.
+ * p_edges         int32[n_edges][2]: the two P-nodes of each edge of the
+ *                 staggered node set (each V-node sits at an edge midpoint)
+ * p_x, p_y        P-node coordinates, device double[M] (edge weights
+ *                 1/|x_a - x_b|^2); all three are read only when precond = 1
  */
 typedef struct rbffd_flow {
   int64_t N, M, ld_v, ld_p;
@@ -221,11 +230,15 @@ typedef struct rbffd_flow {
   const double *pn_dx, *pn_dy;
   double Re, dt;
   int32_t precision;
+  int32_t precond;
   double tol, inner_tol;
   int32_t max_iter;
   int32_t km_mode;
   int32_t overwrite_bc;
   int32_t profile;
+  const int32_t* p_edges;
+  int64_t n_edges;
+  const double *p_x, *p_y;
 } rbffd_flow;
 
 /* Solver state at step j (all FP64 device arrays owned by the caller). */

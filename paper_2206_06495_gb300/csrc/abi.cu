@@ -194,6 +194,10 @@ static int check_flow(rbffd_ctx* ctx, const rbffd_flow* flow) {
       (f.precision != RBFFD_PREC_FP64 && f.precision != RBFFD_PREC_MIXED) || f.km_mode < 0 ||
       f.km_mode > 2 || (f.precision == RBFFD_PREC_MIXED && !(f.inner_tol > 0 && f.inner_tol < 1)))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad Re, dt, tolerances or modes");
+  if (f.precond != 0 && f.precond != 1)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "precond must be 0 or 1");
+  if (f.precond && (!f.p_edges || f.n_edges < 1 || f.n_edges > INT32_MAX || !f.p_x || !f.p_y))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "precond = 1 needs p_edges, n_edges, p_x, p_y");
   return RBFFD_OK;
 }
 

@@ -1,0 +1,367 @@
+// Host-side set-up of the pressure preconditioner's multigrid hierarchy (the
+// V-cycle kernels are in step.cu).  Everything here runs once per flow
+// description; the order of every loop is fixed, so the hierarchy, and with
+// it every iterate of the solver, is the same from run to run.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "amg.cuh"
+
+namespace rbffd {
+
+namespace {
+
+// Off-diagonal part in CSR (columns sorted) plus the diagonal.
+struct HostCsr {
+  int64_t n = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  std::vector<double> diag;
+};
+
+// Weighted graph Laplacian of the kept P-node edges.  Returns an error text or
+// an empty string.
+std::string edge_graph(int64_t M, int64_t ne, const std::vector<int32_t>& e,
+                       const std::vector<double>& x, const std::vector<double>& y,
+                       const std::vector<uint8_t>& bc, HostCsr* G) {
+  std::vector<uint8_t> inner(ne), has_in(M, 0);
+  for (int64_t k = 0; k < ne; ++k) {
+    const int32_t a = e[2 * k], b = e[2 * k + 1];
+    if (a < 0 || a >= M || b < 0 || b >= M) return "an edge end is not a P-node";
+    if (a == b) return "an edge joins a P-node to itself";
+    inner[k] = !(bc[a] && bc[b]);
+    if (inner[k]) has_in[a] = has_in[b] = 1;
+  }
+  std::vector<int64_t> cnt(M + 1, 0);
+  auto kept = [&](int64_t k) {
+    return inner[k] || !has_in[e[2 * k]] || !has_in[e[2 * k + 1]];
+  };
+  for (int64_t k = 0; k < ne; ++k)
+    if (kept(k)) {
+      ++cnt[e[2 * k] + 1];
+      ++cnt[e[2 * k + 1] + 1];
+    }
+  for (int64_t i = 0; i < M; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int32_t> col(cnt[M]);
+  std::vector<double> w(cnt[M]);
+  std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
+  for (int64_t k = 0; k < ne; ++k) {
+    if (!kept(k)) continue;
+    const int32_t a = e[2 * k], b = e[2 * k + 1];
+    const double dx = x[a] - x[b], dy = y[a] - y[b], d2 = dx * dx + dy * dy;
+    if (!(d2 > 0.0)) return "an edge has coincident endpoints";
+    col[cur[a]] = b;
+    w[cur[a]++] = 1.0 / d2;
+    col[cur[b]] = a;
+    w[cur[b]++] = 1.0 / d2;
+  }
+  // sort each row by column and merge repeated edges
+  G->n = M;
+  G->ptr.assign(M + 1, 0);
+  G->col.clear();
+  G->val.clear();
+  G->diag.assign(M, 0.0);
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < M; ++i) {
+    row.clear();
+    for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) row.emplace_back(col[p], w[p]);
+    std::sort(row.begin(), row.end(),
+              [](const auto& u, const auto& v) { return u.first < v.first; });
+    if (row.empty()) return "a P-node has no edge";
+    double s = 0.0;
+    for (size_t q = 0; q < row.size(); ++q) {
+      if (q > 0 && row[q].first == row[q - 1].first) {
+        G->val.back() -= row[q].second;
+      } else {
+        G->col.push_back(row[q].first);
+        G->val.push_back(-row[q].second);
+      }
+      s += row[q].second;
+    }
+    G->diag[i] = s;
+    G->ptr[i + 1] = (int64_t)G->col.size();
+  }
+  return std::string();
+}
+
+// Greedy pairwise matching: in row order, an unmatched row takes its
+// unmatched neighbour of strongest normalised coupling -a_ij / sqrt(a_ii a_jj),
+// the lowest column on ties; a row without one stays alone.  (The raw coupling
+// -a_ij would pair large aggregates with each other and strand the small ones
+// as singletons, and coarsening would stall after a few levels.)
+int32_t pairwise(const HostCsr& A, std::vector<int32_t>* agg) {
+  agg->assign(A.n, -1);
+  int32_t nc = 0;
+  for (int64_t i = 0; i < A.n; ++i) {
+    if ((*agg)[i] >= 0) continue;
+    int32_t best = -1;
+    double bw = 0.0;
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+      const int32_t j = A.col[p];
+      if ((*agg)[j] >= 0) continue;
+      const double dd = A.diag[i] * A.diag[j];
+      const double sij = dd > 0.0 ? -A.val[p] / std::sqrt(dd) : 0.0;
+      if (sij > bw) {
+        bw = sij;
+        best = j;
+      }
+    }
+    (*agg)[i] = nc;
+    if (best >= 0) (*agg)[best] = nc;
+    ++nc;
+  }
+  return nc;
+}
+
+// Children of each aggregate in row order (counting sort).
+void children(const std::vector<int32_t>& agg, int32_t nc, std::vector<int64_t>* cptr,
+              std::vector<int32_t>* cidx) {
+  cptr->assign(nc + 1, 0);
+  for (int32_t a : agg) ++(*cptr)[a + 1];
+  for (int32_t I = 0; I < nc; ++I) (*cptr)[I + 1] += (*cptr)[I];
+  cidx->resize(agg.size());
+  std::vector<int64_t> cur(cptr->begin(), cptr->end() - 1);
+  for (size_t i = 0; i < agg.size(); ++i) (*cidx)[cur[agg[i]]++] = (int32_t)i;
+}
+
+// C = P^T A P for the piecewise-constant P of `agg`.
+void galerkin(const HostCsr& A, const std::vector<int32_t>& agg, int32_t nc, HostCsr* C) {
+  std::vector<int64_t> cptr;
+  std::vector<int32_t> cidx;
+  children(agg, nc, &cptr, &cidx);
+  C->n = nc;
+  C->ptr.assign(nc + 1, 0);
+  C->col.clear();
+  C->val.clear();
+  C->diag.assign(nc, 0.0);
+  std::vector<int64_t> pos(nc, -1);
+  std::vector<std::pair<int32_t, double>> row;
+  for (int32_t I = 0; I < nc; ++I) {
+    row.clear();
+    double d = 0.0;
+    for (int64_t c = cptr[I]; c < cptr[I + 1]; ++c) {
+      const int32_t i = cidx[c];
+      d += A.diag[i];
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        const int32_t J = agg[A.col[p]];
+        if (J == I) {
+          d += A.val[p];
+        } else if (pos[J] < 0) {
+          pos[J] = (int64_t)row.size();
+          row.emplace_back(J, A.val[p]);
+        } else {
+          row[pos[J]].second += A.val[p];
+        }
+      }
+    }
+    for (auto& rv : row) pos[rv.first] = -1;
+    std::sort(row.begin(), row.end(),
+              [](const auto& u, const auto& v) { return u.first < v.first; });
+    for (auto& rv : row) {
+      C->col.push_back(rv.first);
+      C->val.push_back(rv.second);
+    }
+    C->diag[I] = d;
+    C->ptr[I + 1] = (int64_t)C->col.size();
+  }
+}
+
+// Dense inverse of (A + sigma 1 1^T + eps diag(A)) by Cholesky, row-major.
+// sigma lifts the constant null vector of the Laplacian to the mean diagonal;
+// eps = 1e-10 keeps the factorisation defined if the graph falls apart.
+bool coarse_inverse(const HostCsr& A, std::vector<double>* X) {
+  const int64_t n = A.n;
+  std::vector<double> B(n * n, 0.0);
+  double dm = 0.0;
+  for (int64_t i = 0; i < n; ++i) dm += A.diag[i];
+  dm /= (double)n;
+  const double sigma = dm / (double)n;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j) B[i * n + j] = sigma;
+    B[i * n + i] += A.diag[i] * (1.0 + 1e-10);
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) B[i * n + A.col[p]] += A.val[p];
+  }
+  // lower Cholesky factor in place
+  for (int64_t j = 0; j < n; ++j) {
+    double d = B[j * n + j];
+    for (int64_t k = 0; k < j; ++k) d -= B[j * n + k] * B[j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    B[j * n + j] = ljj;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double s = B[i * n + j];
+      for (int64_t k = 0; k < j; ++k) s -= B[i * n + k] * B[j * n + k];
+      B[i * n + j] = s / ljj;
+    }
+  }
+  // W = L^-1 (stored transposed: WT[c][i] = W[i][c]), then X = W^T W
+  std::vector<double> WT(n * n, 0.0), t(n);
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t i = 0; i < c; ++i) t[i] = 0.0;
+    for (int64_t i = c; i < n; ++i) {
+      double s = i == c ? 1.0 : 0.0;
+      for (int64_t k = c; k < i; ++k) s -= B[i * n + k] * t[k];
+      t[i] = s / B[i * n + i];
+    }
+    for (int64_t i = 0; i < n; ++i) WT[c * n + i] = t[i];
+  }
+  X->assign(n * n, 0.0);
+  for (int64_t a = 0; a < n; ++a)
+    for (int64_t b = a; b < n; ++b) {
+      double s = 0.0;
+      for (int64_t k = std::max(a, b); k < n; ++k) s += WT[a * n + k] * WT[b * n + k];
+      (*X)[a * n + b] = (*X)[b * n + a] = s;
+    }
+  return true;
+}
+
+template <typename T>
+int aalloc(rbffd_ctx* ctx, Amg* a, T** out, size_t count) {
+  void* p = nullptr;
+  int rc = check_cuda(ctx, cudaMalloc(&p, sizeof(T) * (count ? count : 1)), "multigrid alloc");
+  if (rc) return rc;
+  a->allocs.push_back(p);
+  *out = (T*)p;
+  return RBFFD_OK;
+}
+
+template <typename T>
+int upload(rbffd_ctx* ctx, Amg* a, const std::vector<T>& h, T** out, cudaStream_t st) {
+  int rc = aalloc(ctx, a, out, h.size());
+  if (rc) return rc;
+  return check_cuda(ctx, cudaMemcpyAsync(*out, h.data(), sizeof(T) * h.size(),
+                                         cudaMemcpyHostToDevice, st),
+                    "multigrid upload");
+}
+
+template <typename T>
+int download(rbffd_ctx* ctx, const T* d, size_t count, std::vector<T>* h, cudaStream_t st) {
+  h->resize(count);
+  return check_cuda(ctx, cudaMemcpyAsync(h->data(), d, sizeof(T) * count, cudaMemcpyDeviceToHost,
+                                         st),
+                    "multigrid download");
+}
+
+}  // namespace
+
+void amg_free(Amg* a) {
+  if (!a) return;
+  for (void* p : a->allocs) cudaFree(p);
+  delete a;
+}
+
+int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const double* es,
+              Amg** out, cudaStream_t st) {
+  *out = nullptr;
+  if (!f.p_edges || f.n_edges <= 0 || !f.p_x || !f.p_y)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                     "precond = 1 needs the P-node edges (p_edges, n_edges) and p_x, p_y");
+  const int64_t M = f.M;
+  std::vector<int32_t> e;
+  std::vector<double> x, y;
+  std::vector<uint8_t> bc;
+  int rc = download(ctx, f.p_edges, (size_t)(2 * f.n_edges), &e, st);
+  if (!rc) rc = download(ctx, f.p_x, (size_t)M, &x, st);
+  if (!rc) rc = download(ctx, f.p_y, (size_t)M, &y, st);
+  if (!rc) rc = download(ctx, f.p_bc, (size_t)M, &bc, st);
+  if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(st), "multigrid download");
+  if (rc) return rc;
+  std::vector<HostCsr> L(1);
+  std::string why = edge_graph(M, f.n_edges, e, x, y, bc, &L[0]);
+  if (!why.empty()) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "pressure graph: %s", why.c_str());
+  std::vector<std::vector<int32_t>> aggs;
+  while (L.back().n > kAmgCoarse && (int)L.size() < kAmgMaxLevels) {
+    const HostCsr& A = L.back();
+    std::vector<int32_t> a1, a2;
+    HostCsr A1, A2;
+    const int32_t n1 = pairwise(A, &a1);
+    galerkin(A, a1, n1, &A1);
+    const int32_t n2 = pairwise(A1, &a2);
+    galerkin(A1, a2, n2, &A2);
+    if ((double)n2 > 0.85 * (double)A.n) break;  // no longer coarsening
+    for (auto& v : a1) v = a2[v];
+    aggs.push_back(std::move(a1));
+    L.push_back(std::move(A2));
+  }
+  if (L.back().n > 8 * kAmgCoarse)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                     "pressure graph does not coarsen below %lld nodes (disconnected?)",
+                     (long long)L.back().n);
+  std::vector<double> Xd;
+  if (!coarse_inverse(L.back(), &Xd))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "coarsest pressure graph matrix is not positive");
+
+  Amg* a = new Amg();
+  auto fail = [&](int code) {
+    amg_free(a);
+    return code;
+  };
+  a->nlev = (int)L.size();
+  for (int l = 0; l < a->nlev; ++l) {
+    const HostCsr& A = L[l];
+    AmgLevel& g = a->lev[l];
+    g.n = A.n;
+    g.ld = round_up(A.n, 32);
+    a->sizes.push_back((int)A.n);
+    if ((rc = aalloc(ctx, a, &g.r, g.ld)) || (rc = aalloc(ctx, a, &g.z, g.ld))) return fail(rc);
+    if (l == a->nlev - 1) break;
+    if ((rc = aalloc(ctx, a, &g.x, g.ld))) return fail(rc);
+    int width = 1;
+    for (int64_t i = 0; i < A.n; ++i) width = std::max<int>(width, (int)(A.ptr[i + 1] - A.ptr[i]));
+    g.width = width;
+    std::vector<int32_t> hidx((size_t)width * g.ld);
+    std::vector<float> hval((size_t)width * g.ld, 0.f), hd(g.ld, 1.f), hwd(g.ld, 0.f);
+    for (int64_t i = 0; i < g.ld; ++i)
+      for (int s = 0; s < width; ++s) hidx[s * g.ld + i] = (int32_t)std::min<int64_t>(i, A.n - 1);
+    for (int64_t i = 0; i < A.n; ++i) {
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        const int s = (int)(p - A.ptr[i]);
+        hidx[s * g.ld + i] = A.col[p];
+        hval[s * g.ld + i] = (float)A.val[p];
+      }
+      hd[i] = (float)A.diag[i];
+      hwd[i] = A.diag[i] > 0.0 ? (float)(kAmgOmega / A.diag[i]) : 0.f;
+    }
+    std::vector<int64_t> cptr;
+    std::vector<int32_t> cidx;
+    const int32_t nc = (int32_t)L[l + 1].n;
+    children(aggs[l], nc, &cptr, &cidx);
+    int cw = 1;
+    for (int32_t I = 0; I < nc; ++I) cw = std::max<int>(cw, (int)(cptr[I + 1] - cptr[I]));
+    if (cw > 4)  // two pairwise passes make aggregates of at most four rows
+      return fail(set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid aggregate of %d rows", cw));
+    g.cw = cw;
+    g.ld_c = round_up(nc, 32);
+    std::vector<int32_t> hch((size_t)cw * g.ld_c, -1);
+    for (int32_t I = 0; I < nc; ++I)
+      for (int64_t c = cptr[I]; c < cptr[I + 1]; ++c) hch[(c - cptr[I]) * g.ld_c + I] = cidx[c];
+    if ((rc = upload(ctx, a, hidx, &g.idx, st)) || (rc = upload(ctx, a, hval, &g.val, st)) ||
+        (rc = upload(ctx, a, hd, &g.diag, st)) || (rc = upload(ctx, a, hwd, &g.wd, st)) ||
+        (rc = upload(ctx, a, aggs[l], &g.agg, st)) || (rc = upload(ctx, a, hch, &g.ch, st)))
+      return fail(rc);
+  }
+  a->nc = L.back().n;
+  std::vector<float> hX(Xd.begin(), Xd.end());
+  if ((rc = upload(ctx, a, hX, &a->Xc, st))) return fail(rc);
+  // level-0 scaling: the scaled pressure rows approximate rows of G divided by diag(G)
+  std::vector<float> hc(M), hce(M);
+  double ces = 0.0;
+  for (int64_t i = 0; i < M; ++i) {
+    const double ci = diag_a[i] != 0.0 ? L[0].diag[i] / diag_a[i] : L[0].diag[i];
+    hc[i] = (float)ci;
+    hce[i] = (float)(ci * es[i]);
+    ces += ci * es[i];
+  }
+  if (!(ces != 0.0) || !std::isfinite(ces)) return fail(set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                                                                  "pressure rank-one column is zero"));
+  a->inv_ces = 1.0 / ces;
+  a->inv_R = 1.0 / (double)M;
+  if ((rc = upload(ctx, a, hc, &a->c, st)) || (rc = upload(ctx, a, hce, &a->ce, st))) return fail(rc);
+  if ((rc = check_cuda(ctx, cudaStreamSynchronize(st), "multigrid upload"))) return fail(rc);
+  *out = a;
+  return RBFFD_OK;
+}
+
+}  // namespace rbffd

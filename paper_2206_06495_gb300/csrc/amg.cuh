@@ -1,0 +1,82 @@
+// Multigrid preconditioner of the pressure solve.
+//
+// The paper solves its pressure Poisson system without saying how; an
+// unpreconditioned Krylov method needs O(1/h) iterations on it.  Both the
+// scaled RBF-FD Laplacian and the weighted graph Laplacian of the P-node
+// edges (the edges whose midpoints are the V-nodes of the staggered node set,
+// Section 3) approximate the same continuous operator, so the graph Laplacian
+// G is spectrally close to it with bounds that do not depend on h.  G is a
+// symmetric M-matrix with zero row sums: plain aggregation multigrid on it is
+// robust, while a multigrid on the RBF-FD matrix itself is not (its Jacobi
+// iteration grows transiently near the walls).  One V-cycle on G is the right
+// preconditioner of BiCGSTAB; it changes the iteration count, not the
+// solution, which is still the converged solve of the RBF-FD system.
+//
+// G: edge weight 1/|x_a - x_b|^2; an edge between two boundary P-nodes is left
+// out (boundary rows of the pressure system are one-sided Neumann rows on
+// interior nodes) unless one of its ends has no other edge to an interior node.
+// Hierarchy: two passes of pairwise matching by strongest coupling per level
+// (aggregates of up to 4 nodes), Galerkin coarse matrices P^T G P with
+// piecewise-constant P, down to at most kAmgCoarse nodes, where the dense
+// inverse of (G_c + sigma 1 1^T) is applied.  Smoother: one damped Jacobi
+// sweep before and after the coarse correction, which is scaled by
+// kAmgCoarseScale (the usual over-correction of plain aggregation).
+// The hierarchy is built once per flow description on the host (like a
+// symbolic factorisation); every V-cycle operation runs in CUDA kernels, in
+// FP32 (a preconditioner only has to be a fixed linear map).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace rbffd {
+
+constexpr int kAmgMaxLevels = 16;
+constexpr int kAmgCoarse = 512;
+constexpr float kAmgOmega = 0.8f;
+constexpr float kAmgCoarseScale = 1.6f;
+
+// One level of the hierarchy (device arrays).  Rows of level l + 1 are the
+// aggregates of level l.  The coarsest level holds only r, z and the dense
+// inverse.
+struct AmgLevel {
+  int64_t n = 0, ld = 0;   // rows; leading dimension of the slot-major arrays
+  int width = 0;           // off-diagonal slots per row (padding: own index, weight 0)
+  int32_t* idx = nullptr;  // [width][ld] off-diagonal columns
+  float* val = nullptr;    // [width][ld] off-diagonal entries (<= 0)
+  float* diag = nullptr;   // [n]
+  float* wd = nullptr;     // [n] omega / diag
+  int32_t* agg = nullptr;  // [n] row of level l + 1 that row i belongs to
+  int cw = 0;              // most rows in one aggregate
+  int64_t ld_c = 0;        // leading dimension of ch
+  int32_t* ch = nullptr;   // [cw][ld_c] rows of aggregate I (level l + 1 row), -1 padding
+  float* r = nullptr;      // right side at this level
+  float* x = nullptr;      // pre-smoothed iterate
+  float* z = nullptr;      // level result (after the post-smoothing sweep)
+};
+
+struct Amg {
+  int nlev = 0;
+  AmgLevel lev[kAmgMaxLevels];
+  float* Xc = nullptr;  // [nc][nc] dense inverse on the coarsest level
+  int64_t nc = 0;
+  // level-0 map of a residual v of the scaled pressure system: r0 = c v - mu ce,
+  // mu = (c . v) / (c . es); the result is z + mu / M (see step.cu)
+  float* c = nullptr;   // [M] diag(G) / diag(A)
+  float* ce = nullptr;  // [M] c * es
+  double inv_ces = 0.0;
+  double inv_R = 0.0;
+  std::vector<int> sizes;  // rows per level (host copy, for reports)
+  std::vector<void*> allocs;
+};
+
+// Build the hierarchy of the flow's P-node edge graph.  diag_a and es are
+// HOST copies (M values) of the diagonal and the rank-one column of the scaled
+// pressure operator.  Errors: INVALID_ARG (edges out of range, coincident
+// endpoints, a P-node without edges, a graph that does not coarsen), CUDA, OOM.
+int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const double* es,
+              Amg** out, cudaStream_t st);
+void amg_free(Amg* a);
+
+}  // namespace rbffd

@@ -27,8 +27,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <vector>
 
+#include "amg.cuh"
 #include "common.cuh"
 
 namespace rbffd {
@@ -52,6 +54,8 @@ struct KScal {
   double rho[2], alpha[2], omega[2], beta[2];
   double rr[2], bb[2];
   double sum_p, sum_s, sum_x;
+  double cp, cs;  // preconditioned solves: (c . p), (c . s) of the multigrid's level-0 map
+  double ysum;    // preconditioned solves: sum of the V-cycle result before its shift
   double tol2;
   int active[2];
   int half[2];
@@ -328,7 +332,7 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_init(KOp<TW, TV> op, Vecs<TV, NRHS> x, Vecs<TV, NRHS> b, Vecs<TV, NRHS> r,
            Vecs<TV, NRHS> rh, Vecs<TV, NRHS> p, const double* sigma_x, KScal* sc, GridReduce gr,
-           double tol2, int maxit, uint32_t seed, Split<NRHS> p2) {
+           double tol2, int maxit, uint32_t seed, Split<NRHS> p2, const float* __restrict__ pcc) {
   using A = typename Acc<TV>::t;
   __shared__ double sh[kNV * kThreads / 32];
   A prr[2] = {0, 0}, pbb[2] = {0, 0}, prh[2] = {0, 0}, psum = 0;
@@ -348,11 +352,11 @@ __global__ void __launch_bounds__(kThreads)
       r.v[q][i] = (TV)ri;
       rh.v[q][i] = (TV)(sgn * ri);
       p.v[q][i] = (TV)ri;
-      if (IsFF<TW, TV>::value) p2.v[q][i] = split2((double)ri);
+      if (IsFF<TW, TV>::value && p2.v[q]) p2.v[q][i] = split2((double)ri);
       prr[q] += ri * ri;
       pbb[q] += bi * bi;
       prh[q] += sgn * ri * ri;
-      if (RANK1) psum += op.rdot ? (A)op.rdot[i] * ri : ri;
+      if (RANK1) psum += pcc ? (A)pcc[i] * ri : (op.rdot ? (A)op.rdot[i] * ri : ri);
     }
   }
   double v[kNV] = {(double)prr[0], (double)pbb[0], (double)prr[1],
@@ -379,7 +383,12 @@ __global__ void __launch_bounds__(kThreads)
       any |= sc->active[q];
     }
     for (int q = NRHS; q < 2; ++q) sc->active[q] = 0;
-    if (RANK1) sc->sum_p = t[5];
+    if (RANK1) {
+      if (pcc)
+        sc->cp = t[5];
+      else
+        sc->sum_p = t[5];
+    }
     sc->done = (any && maxit > 0) ? 0 : 1;
   });
 }
@@ -457,7 +466,8 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_s(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> v, Vecs<TV, NRHS> s, KScal* sc,
-               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> s2) {
+               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> s2,
+               const float* __restrict__ pcc) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -478,22 +488,28 @@ __global__ void __launch_bounds__(kThreads)
       s.v[q][i] = si;
       if (s2.v[0]) s2.v[q][i] = split2((double)si);
       pss[q] += si * si;
-      if (RANK1) psum += rdot ? rdot[i] * si : si;
+      if (RANK1) psum += pcc ? (A)pcc[i] * si : (rdot ? rdot[i] * si : si);
     }
   }
   double vv[kNV] = {(double)pss[0], (double)pss[1], (double)psum, 0, 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
     for (int q = 0; q < NRHS; ++q)
       if (sc->active[q] && t[q] <= sc->tol2 * sc->bb[q]) sc->half[q] = 1;
-    if (RANK1) sc->sum_s = t[2];
+    if (RANK1) {
+      if (pcc)
+        sc->cs = t[2];
+      else
+        sc->sum_s = t[2];
+    }
   });
 }
 
-// t = A s ; reduce (t, s), (t, t)  (staged tiles when K > 0)
+// t = A s^ ; reduce (t, s), (t, t)  (staged tiles when K > 0).  s^ = s, or the
+// preconditioned B s in a preconditioned solve; sres = s.
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
-    k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr,
-             Split<NRHS> s2) {
+    k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> sres, Vecs<TV, NRHS> t, KScal* sc,
+             GridReduce gr, Split<NRHS> s2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -503,11 +519,10 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
       A y = acc[q];
-      const A si = (A)s.v[q][i];
-      if (op.diag1) y += si;
+      if (op.diag1) y += (A)s.v[q][i];
       if (RANK1) y += (A)op.es[i] * sig;
       t.v[q][i] = (TV)y;
-      pts[q] += y * si;
+      pts[q] += y * (A)sres.v[q][i];
       ptt[q] += y * y;
     }
   };
@@ -560,11 +575,13 @@ __global__ void __launch_bounds__(kThreads)
   });
 }
 
-// x += alpha p + omega s ; r = s - omega t ; reduce (rh, r), (r, r)
+// x += alpha p^ + omega s^ ; r = s - omega t ; reduce (rh, r), (r, r).
+// p^, s^ = p, s, or their preconditioned images in a preconditioned solve.
 template <int NRHS, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_xr(int64_t n, Vecs<TV, NRHS> x, Vecs<TV, NRHS> r, Vecs<TV, NRHS> rh,
-                Vecs<TV, NRHS> p, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t, KScal* sc, GridReduce gr) {
+                Vecs<TV, NRHS> p, Vecs<TV, NRHS> shat, Vecs<TV, NRHS> s, Vecs<TV, NRHS> t,
+                KScal* sc, GridReduce gr) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -589,7 +606,7 @@ __global__ void __launch_bounds__(kThreads)
         x.v[q][i] += al[q] * p.v[q][i];
         ri = si;
       } else {
-        x.v[q][i] += al[q] * p.v[q][i] + om[q] * si;
+        x.v[q][i] += al[q] * p.v[q][i] + om[q] * shat.v[q][i];
         ri = si - om[q] * t.v[q][i];
       }
       r.v[q][i] = ri;
@@ -636,7 +653,8 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_p(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, KScal* sc,
-               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> p2) {
+               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> p2,
+               const float* __restrict__ pcc) {
   using A = TV;
   if (sc->done) return;
   __shared__ double sh[kNV * kThreads / 32];
@@ -657,12 +675,161 @@ __global__ void __launch_bounds__(kThreads)
       const A pi = r.v[q][i] + be[q] * (p.v[q][i] - om[q] * v.v[q][i]);
       p.v[q][i] = pi;
       if (p2.v[0]) p2.v[q][i] = split2((double)pi);
-      if (RANK1) psum += rdot ? rdot[i] * pi : pi;
+      if (RANK1) psum += pcc ? (A)pcc[i] * pi : (rdot ? rdot[i] * pi : pi);
     }
   }
   double vv[kNV] = {(double)psum, 0, 0, 0, 0, 0};
   grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
-    if (RANK1) sc->sum_p = tt[0];
+    if (RANK1) {
+      if (pcc)
+        sc->cp = tt[0];
+      else
+        sc->sum_p = tt[0];
+    }
+  });
+}
+
+// ------------------------------------------- multigrid preconditioner (amg.cuh)
+// z = B v for a residual v of the scaled pressure system A_f = A + es 1^T:
+//   mu = (c . v) / (c . es);  r0 = c v - mu ce;  y = one V-cycle on G for r0;
+//   z = y - mean(y) + mu / M.
+// Since A is close to diag(1/c) G and A 1 = 0, this inverts the constant mode
+// exactly (B es = 1 / M, and A_f 1 / M = es) and G on the rest.  (c . v) and
+// (c . s) come from the reductions of the kernels that produce p and s.
+
+// r0 = c v - mu ce (which = 0: v = p, mu from sc->cp; 1: v = s, from sc->cs)
+template <typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_pc_in(int64_t n, const TV* __restrict__ v, const float* __restrict__ c,
+            const float* __restrict__ ce, int which, double inv_ces, const KScal* sc,
+            float* __restrict__ r0) {
+  if (sc->done) return;
+  const float mu = (float)((which ? sc->cs : sc->cp) * inv_ces);
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads)
+    r0[i] = c[i] * (float)v[i] - mu * ce[i];
+}
+
+// Pre-smoothing from zero (x = omega D^-1 r) and restriction of its residual:
+// rc[I] = sum over the rows i of aggregate I of (r - G x)_i.  Four lanes per
+// aggregate, one per row (aggregates hold at most four rows), summed by a
+// fixed shuffle tree; neighbours' x values are formed from their r on the fly.
+__global__ void __launch_bounds__(kThreads)
+    k_pc_restrict(AmgLevel F, int64_t nc, float* __restrict__ rc, const KScal* sc) {
+  if (sc->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = nc * 4;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  // the loop condition is uniform across a warp (stride is a multiple of 32)
+  for (int64_t t = blockIdx.x * (int64_t)kThreads + threadIdx.x; t - lane < total; t += stride) {
+    const int64_t I = t >> 2;
+    const int q = (int)(t & 3);
+    float res = 0.f;
+    const int32_t i = (t < total && q < F.cw) ? F.ch[q * F.ld_c + I] : -1;
+    if (i >= 0) {
+      const float ri = F.r[i];
+      const float xi = F.wd[i] * ri;
+      F.x[i] = xi;
+      float ax = F.diag[i] * xi;
+#pragma unroll 4
+      for (int s = 0; s < F.width; ++s) {
+        const int32_t j = F.idx[s * F.ld + i];
+        ax += F.val[s * F.ld + i] * (F.wd[j] * F.r[j]);
+      }
+      res = ri - ax;
+    }
+    res += __shfl_xor_sync(0xffffffffu, res, 1);
+    res += __shfl_xor_sync(0xffffffffu, res, 2);
+    if (q == 0 && t < total) rc[I] = res;
+  }
+}
+
+// x_fine[i] += s * z for the rows i of aggregate `row` (the coarse-grid
+// correction of the finer level, written by the coarse level's thread)
+__device__ __forceinline__ void prolong_to(const AmgLevel& Fine, int64_t row, float z) {
+  const float v = kAmgCoarseScale * z;
+  for (int q = 0; q < Fine.cw; ++q) {
+    const int32_t c = Fine.ch[q * Fine.ld_c + row];
+    if (c < 0) break;
+    Fine.x[c] += v;
+  }
+}
+
+// Coarsest level: z = X r with the dense inverse X (one warp per row), then
+// the correction of the next finer level.
+__global__ void __launch_bounds__(kThreads)
+    k_pc_coarse(int64_t nc, const float* __restrict__ X, const float* __restrict__ r,
+                float* __restrict__ z, AmgLevel Fine, int has_fine, const KScal* sc) {
+  if (sc->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t row = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; row < nc; row += nw) {
+    float acc = 0.f;
+    for (int64_t j = lane; j < nc; j += 32) acc += X[row * nc + j] * r[j];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      z[row] = acc;
+      if (has_fine) prolong_to(Fine, row, acc);
+    }
+  }
+}
+
+// One post-smoothing sweep on a level whose x already holds the coarse-grid
+// correction: z = x + omega D^-1 (r - G x).  Levels above 0 then add their
+// correction to the next finer level (PROLONG); level 0 reduces sum(z) into
+// sc->ysum (REDUCE).
+template <bool PROLONG, bool REDUCE>
+__global__ void __launch_bounds__(kThreads)
+    k_pc_up(AmgLevel F, AmgLevel Fine, float* __restrict__ z, KScal* sc, GridReduce gr) {
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  double part = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < F.n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const float xi = F.x[i];
+    float ax = F.diag[i] * xi;
+#pragma unroll 4
+    for (int q = 0; q < F.width; ++q) {
+      const int32_t j = F.idx[q * F.ld + i];
+      ax += F.val[q * F.ld + i] * F.x[j];
+    }
+    const float zi = xi + F.wd[i] * (F.r[i] - ax);
+    z[i] = zi;
+    if (PROLONG) prolong_to(Fine, i, zi);
+    if (REDUCE) part += (double)zi;
+  }
+  if (REDUCE) {
+    double v[kNV] = {part, 0, 0, 0, 0, 0};
+    grid_reduce<kNV>(v, gr, sh, [&](double* t) { sc->ysum = t[0]; });
+  }
+}
+
+// out = y - mean(y) + mu / M (and its split copy); reduce sum(out) into the
+// rank-one sum that the following SpMV uses.  have_sum = 0: y is already
+// mean-free (a one-level hierarchy solves the lifted coarse system directly).
+template <typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_pc_out(int64_t n, const float* __restrict__ y, int have_sum, double inv_ces, double inv_R,
+             int which, TV* __restrict__ out, float2* __restrict__ out2, KScal* sc,
+             GridReduce gr) {
+  if (sc->done) return;
+  __shared__ double sh[kNV * kThreads / 32];
+  const double mu = (which ? sc->cs : sc->cp) * inv_ces;
+  const double shift = (mu - (have_sum ? sc->ysum : 0.0)) * inv_R;
+  double part = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const double zi = (double)y[i] + shift;
+    out[i] = (TV)zi;
+    if (out2) out2[i] = split2(zi);
+    part += zi;
+  }
+  double v[kNV] = {part, 0, 0, 0, 0, 0};
+  grid_reduce<kNV>(v, gr, sh, [&](double* t) {
+    if (which)
+      sc->sum_s = t[0];
+    else
+      sc->sum_p = t[0];
   });
 }
 
@@ -1046,6 +1213,18 @@ __global__ void k_scale_by_inv_abs(int64_t n, double* __restrict__ x, const doub
     x[i] *= s;
 }
 
+// diagonal of the scaled pressure operator (the sum of the slots on the row's own node)
+__global__ void k_diag(int64_t M, int64_t ld, int k, const int32_t* __restrict__ idx,
+                       const double* __restrict__ w, double* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < k; ++q)
+      if (idx[q * ld + i] == (int32_t)i) s += w[q * ld + i];
+    d[i] = s;
+  }
+}
+
 __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -1086,6 +1265,18 @@ struct StepPlan {
   KScal* sc = nullptr;
   double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
   struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
+  Amg* amg = nullptr;                 // pressure preconditioner (precond = 1)
+  double *ph = nullptr, *sh = nullptr;  // preconditioned search directions B p, B s
+  // CUDA graphs of Krylov iteration chunks: one per solve (its operator,
+  // vectors and preconditioner) and chunk length, captured on first use on a
+  // private stream and replayed on the caller's stream
+  struct Graph {
+    const void* key[10];
+    int n;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;
   int64_t launches = 0;     // kernels launched by rbffd_step on this plan
   // optional per-launch timing of the pressure-solve SpMV kernels
   static constexpr int kEv = 512;
@@ -1101,6 +1292,9 @@ void adjoint_plan_free(struct AdjointPlan* a);
 void step_plan_free(StepPlan* p) {
   if (!p) return;
   adjoint_plan_free(p->adj);
+  amg_free(p->amg);
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
   for (int i = 0; i < StepPlan::kEv; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   for (void* a : p->allocs) cudaFree(a);
@@ -1127,9 +1321,18 @@ int to32(rbffd_ctx* ctx, StepPlan* p, const double* src, int64_t n, float** dst,
   return check_cuda(ctx, cudaGetLastError(), "to_f32");
 }
 
+// The fields a plan is built from: solver controls (tolerances, iteration
+// cap, boundary modes, profiling) are read per call and do not key the plan.
+rbffd_flow plan_key(const rbffd_flow& f) {
+  rbffd_flow k = f;
+  k.tol = k.inner_tol = 0.0;
+  k.max_iter = k.km_mode = k.overwrite_bc = k.profile = 0;
+  return k;
+}
+
 int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t st) {
   StepPlan* p = new StepPlan();
-  p->key = f;
+  p->key = plan_key(f);
   p->k = ctx->prm.n;
   p->N = f.N;
   p->M = f.M;
@@ -1193,6 +1396,22 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
                        herr);
     }
   }
+  if (f.precond) {
+    // multigrid hierarchy of the P-node edge graph, scaled to the pressure rows
+    std::vector<double> hd(f.M), hes(f.M);
+    k_diag<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, p->Lidx, p->Lw, p->kw64[0][0]);
+    TRY(check_cuda(ctx, cudaGetLastError(), "diagonal"));
+    TRY(check_cuda(ctx, cudaMemcpyAsync(hd.data(), p->kw64[0][0], sizeof(double) * f.M,
+                                        cudaMemcpyDeviceToHost, st),
+                   "diagonal copy"));
+    TRY(check_cuda(ctx, cudaMemcpyAsync(hes.data(), p->es, sizeof(double) * f.M,
+                                        cudaMemcpyDeviceToHost, st),
+                   "rank-one column copy"));
+    TRY(check_cuda(ctx, cudaStreamSynchronize(st), "diagonal sync"));
+    TRY(amg_build(ctx, f, hd.data(), hes.data(), &p->amg, st));
+    TRY(palloc(ctx, p, &p->ph, f.M));
+    TRY(palloc(ctx, p, &p->sh, f.M));
+  }
   if (p->mix) {
     TRY(to32(ctx, p, p->Lw, np, &p->Lw32, st));
     TRY(to32(ctx, p, p->es, f.M, &p->es32, st));
@@ -1250,13 +1469,81 @@ void collect_events(StepPlan* P) {
   P->ev_used = 0;
 }
 
+// out = B v (one application of the multigrid preconditioner, 2 nlev + 1 launches)
+template <typename TV>
+void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* out, float2* out2,
+            cudaStream_t st) {
+  const int G = P->grid;
+  auto grid_for = [&](int64_t rows) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(G, (rows + kThreads - 1) / kThreads));
+  };
+  const int64_t n = a->lev[0].n;
+  k_pc_in<TV><<<G, kThreads, 0, st>>>(n, v, a->c, a->ce, which, a->inv_ces, P->sc, a->lev[0].r);
+  for (int l = 0; l + 1 < a->nlev; ++l)
+    k_pc_restrict<<<grid_for(a->lev[l + 1].n * 4), kThreads, 0, st>>>(
+        a->lev[l], a->lev[l + 1].n, a->lev[l + 1].r, P->sc);
+  const AmgLevel& C = a->lev[a->nlev - 1];
+  const AmgLevel& Cf = a->lev[a->nlev >= 2 ? a->nlev - 2 : 0];
+  k_pc_coarse<<<grid_for(a->nc * 32), kThreads, 0, st>>>(a->nc, a->Xc, C.r, C.z, Cf,
+                                                         a->nlev >= 2 ? 1 : 0, P->sc);
+  for (int l = a->nlev - 2; l >= 1; --l)
+    k_pc_up<true, false><<<grid_for(a->lev[l].n), kThreads, 0, st>>>(a->lev[l], a->lev[l - 1],
+                                                                     a->lev[l].z, P->sc, P->gr);
+  if (a->nlev >= 2)
+    k_pc_up<false, true><<<G, kThreads, 0, st>>>(a->lev[0], a->lev[0], a->lev[0].z, P->sc,
+                                                 P->gr);
+  k_pc_out<TV><<<G, kThreads, 0, st>>>(n, a->lev[0].z, a->nlev >= 2 ? 1 : 0, a->inv_ces,
+                                       a->inv_R, which, out, out2, P->sc, P->gr);
+}
+
+// The graph of `n` iterations of one solve, captured on first use.
+int chunk_graph(rbffd_ctx* ctx, StepPlan* P, const void* const (&key)[10], int n,
+                const std::function<void(cudaStream_t, int)>& issue, cudaGraphExec_t* out) {
+  for (const auto& g : P->graphs)
+    if (g.n == n && memcmp(g.key, key, sizeof(g.key)) == 0) {
+      *out = g.exec;
+      return RBFFD_OK;
+    }
+  int rc = 0;
+  if (!P->cap &&
+      (rc = check_cuda(ctx, cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking),
+                       "capture stream")))
+    return rc;
+  if ((rc = check_cuda(ctx, cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal),
+                       "begin capture")))
+    return rc;
+  issue(P->cap, n);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(P->cap, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return check_cuda(ctx, e, "end capture");
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if ((rc = check_cuda(ctx, e2, "graph instantiate"))) return rc;
+  StepPlan::Graph entry;
+  memcpy(entry.key, key, sizeof(entry.key));
+  entry.n = n;
+  entry.exec = ex;
+  P->graphs.push_back(entry);
+  *out = ex;
+  return RBFFD_OK;
+}
+
+// BiCGSTAB on op x = b; with pc (pressure solves only, one right side, no
+// rdot), right-preconditioned: p^ = B p, s^ = B s, the SpMVs act on p^ and s^,
+// and x gathers alpha p^ + omega s^, so r stays the true residual recurrence.
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
              cudaStream_t st, bool prof = false, uint32_t seed_base = 0,
-             float2* const* p2s = nullptr, float2* const* s2s = nullptr) {
-  Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
-  Split<NRHS> P2, S2;
+             float2* const* p2s = nullptr, float2* const* s2s = nullptr,
+             const Amg* pc = nullptr) {
+  static_assert(sizeof(TV) == 8, "the preconditioned directions are FP64 vectors");
+  Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T, PH, SH;
+  Split<NRHS> P2, S2, none{};
   for (int q = 0; q < NRHS; ++q) {
     P2.v[q] = p2s ? p2s[q] : nullptr;
     S2.v[q] = s2s ? s2s[q] : nullptr;
@@ -1270,7 +1557,17 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     V.v[q] = work[3][q];
     S.v[q] = work[4][q];
     T.v[q] = work[5][q];
+    PH.v[q] = PP.v[q];
+    SH.v[q] = S.v[q];
   }
+  if (pc) {
+    if (NRHS != 1 || !RANK1 || op.rdot)
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid preconditioner: pressure solves only");
+    PH.v[0] = (TV*)P->ph;
+    SH.v[0] = (TV*)P->sh;
+  }
+  const float* pcc = pc ? pc->c : nullptr;
+  const int vc_launches = pc ? 2 * pc->nlev + 1 : 0;
   const int G = P->grid;
   double* sigx = P->dscal;
   KScal* h = (KScal*)ctx->host_pinned;
@@ -1312,8 +1609,9 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
                                                     (restart || seed_base)
                                                         ? 0x51ED27u + 977u * seed_base + restart
                                                         : 0u,
-                                                    P2);
-    P->launches += RANK1 ? 2 : 1;
+                                                    pc ? none : P2, pcc);
+    P->launches += (RANK1 ? 2 : 1) + (pc ? vc_launches : 0);
+    if (pc) vcycle<TV>(P, pc, PP.v[0], 0, PH.v[0], P2.v[0], st);
     int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
     if (rc) return rc;
     int issued = 0, chunk = 4;
@@ -1328,20 +1626,38 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (h->done || issued >= budget) break;
       int n = std::min(chunk, budget - issued);
       if (prof) n = std::min(n, StepPlan::kEv / 4);
-      for (int it = 0; it < n; ++it) {
-        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, PP, V, RH, P->sc, P->gr, P2);
-        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_update_s<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
-                                                        S2);
-        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, S, T, P->sc, P->gr, S2);
-        if (prof) cudaEventRecord(P->ev[P->ev_used++], st);
-        k_update_xr<NRHS><<<G, kThreads, 0, st>>>(op.n, X, R, RH, PP, S, T, P->sc, P->gr);
-        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
-                                                        P2);
+      // one chunk of iterations; every kernel returns at once after the solve
+      // has finished (sc->done), so a chunk may overshoot harmlessly
+      auto issue = [&](cudaStream_t s, int cnt) {
+        for (int it = 0; it < cnt; ++it) {
+          if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PH, V, RH, P->sc, P->gr, P2);
+          if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+          k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
+                                                         pc ? none : S2, pcc);
+          if (pc) vcycle<TV>(P, pc, S.v[0], 1, SH.v[0], S2.v[0], s);
+          if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+          k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, SH, S, T, P->sc, P->gr, S2);
+          if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+          k_update_xr<NRHS><<<G, kThreads, 0, s>>>(op.n, X, R, RH, PH, SH, S, T, P->sc, P->gr);
+          k_update_p<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
+                                                         pc ? none : P2, pcc);
+          if (pc) vcycle<TV>(P, pc, PP.v[0], 0, PH.v[0], P2.v[0], s);
+        }
+      };
+      if (prof) {
+        issue(st, n);  // per-launch events need eager launches
+      } else {
+        const void* const key[10] = {(const void*)&bicgstab<K, NRHS, RANK1, TW, TV>,
+                                     op.idx, op.w, op.es, X.v[0], X.v[NRHS - 1], pc,
+                                     P2.v[0], S2.v[0], work[0][0]};
+        cudaGraphExec_t g = nullptr;
+        rc = chunk_graph(ctx, P, key, n, issue, &g);
+        if (rc) return rc;
+        rc = check_cuda(ctx, cudaGraphLaunch(g, st), "graph launch");
+        if (rc) return rc;
       }
-      P->launches += 5 * n;
+      P->launches += (int64_t)(5 + 2 * vc_launches) * n;
       rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
       if (rc) return rc;
       issued += n;
@@ -1483,7 +1799,7 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     SolveResult inner;
     rc = bicgstab<K, NRHS, RANK1, float, double>(ctx, P, op32, E64.v, B64.v, P->kw64, inner_tol,
                                                  maxit - used, &inner, st, prof, retries, P->p2,
-                                                 P->s2);
+                                                 P->s2, RANK1 ? P->amg : nullptr);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
@@ -1585,7 +1901,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                               &sweeps, st, prof);
     else
       rc = bicgstab<K, 1, true, double, double>(ctx, P, L64, px, pbv, P->kw64, f.tol, f.max_iter,
-                                                &pr, st, prof);
+                                                &pr, st, prof, 0, nullptr, nullptr, P->amg);
     if (rc) return rc;
     if (stats) {
       stats->poisson_iters += pr.iters;
@@ -1624,7 +1940,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
 
 int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st) {
-  if (ctx->plan && memcmp(&ctx->plan->key, f, sizeof(rbffd_flow)) != 0) {
+  const rbffd_flow key = plan_key(*f);
+  if (ctx->plan && memcmp(&ctx->plan->key, &key, sizeof(rbffd_flow)) != 0) {
     cudaStreamSynchronize(st);
     step_plan_free(ctx->plan);
     ctx->plan = nullptr;
@@ -2055,7 +2372,8 @@ int build_adjoint_plan(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, cudaStr
 int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* fp, const rbffd_state* s, rbffd_adjoint* lam,
                 double* grad_gu, double* grad_gv, rbffd_stats* stats, cudaStream_t st) {
   const rbffd_flow& f = *fp;
-  if (ctx->plan && memcmp(&ctx->plan->key, fp, sizeof(rbffd_flow)) != 0) {
+  const rbffd_flow key = plan_key(f);
+  if (ctx->plan && memcmp(&ctx->plan->key, &key, sizeof(rbffd_flow)) != 0) {
     cudaStreamSynchronize(st);
     step_plan_free(ctx->plan);
     ctx->plan = nullptr;

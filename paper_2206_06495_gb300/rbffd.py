@@ -62,8 +62,11 @@ class FlowC(C.Structure):
                 ("nb_p", C.c_int64), ("ld_b", C.c_int64), ("pn_rows", C.c_void_p),
                 ("pn_idx", C.c_void_p), ("pn_dx", C.c_void_p), ("pn_dy", C.c_void_p),
                 ("Re", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
+                ("precond", C.c_int32),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("max_iter", C.c_int32),
-                ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32), ("profile", C.c_int32)]
+                ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32), ("profile", C.c_int32),
+                ("p_edges", C.c_void_p), ("n_edges", C.c_int64), ("p_x", C.c_void_p),
+                ("p_y", C.c_void_p)]
 
 
 class StateC(C.Structure):
@@ -261,6 +264,7 @@ class Flow:
     km_mode: int = 1
     overwrite_bc: int = 1
     profile: int = 0
+    precond: int = 1
     _c: FlowC = field(default=None, repr=False)
 
     def cstruct(self) -> FlowC:
@@ -277,7 +281,11 @@ class Flow:
                      pn_rows=p("pn_rows"), pn_idx=p("pn_idx"), pn_dx=p("pn_dx"), pn_dy=p("pn_dy"),
                      Re=self.Re, dt=self.dt, precision=self.precision, tol=self.tol,
                      inner_tol=self.inner_tol, max_iter=self.max_iter, km_mode=self.km_mode,
-                     overwrite_bc=self.overwrite_bc, profile=self.profile)
+                     overwrite_bc=self.overwrite_bc, profile=self.profile,
+                     precond=self.precond,
+                     p_edges=p("p_edges") if "p_edges" in t else None,
+                     n_edges=t["p_edges"].shape[0] if "p_edges" in t else 0,
+                     p_x=p("px") if "px" in t else None, p_y=p("py") if "py" in t else None)
 
 
 def flow_from_nodes(ctx: Context, nodes, Re: float, dt: float, device="cuda", **kw) -> Flow:
@@ -320,6 +328,7 @@ def flow_from_nodes(ctx: Context, nodes, Re: float, dt: float, device="cuda", **
     t["p_bc"] = d(nodes.p_boundary.astype(np.uint8))
     t["p_nx"], t["p_ny"] = d(nodes.p_nx), d(nodes.p_ny)
     t["px"], t["py"], t["vx"], t["vy"] = px, py, vx, vy
+    t["p_edges"] = d(np.asarray(nodes.edges, dtype=np.int32))
     return Flow(N=N, M=M, tensors=t, Re=Re, dt=dt, **kw)
 
 
