@@ -28,25 +28,24 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Block-wide sum of NV values per thread, fixed reduction tree (deterministic
-// for a fixed block size).  Result valid in thread 0.  `sh` holds at least
-// NV * (blockDim.x / 32) doubles.
+// Block-wide sum of NV values per thread in a fixed order (deterministic for
+// a fixed block size).  Result valid in thread 0.  `sh` holds at least
+// NV * blockDim.x doubles.  The threads only store their values; warp 0 adds
+// them (each lane a strided column, then one butterfly), so a block issues
+// about (blockDim.x / 32 + 4) FP64 adds per value instead of five per value
+// in every warp: FP64 instructions are scarce on this GPU.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
 #pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  for (int j = 0; j < NV; ++j) sh[j * nt + tid] = v[j];
   __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) sh[j * nw + wid] = v[j];
-  }
-  __syncthreads();
-  if (wid == 0) {
+  if (tid < 32) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      double t = lane < nw ? sh[j * nw + lane] : 0.0;
-      v[j] = warp_sum(t);
+      double a = sh[j * nt + tid];
+      for (int k = tid + 32; k < nt; k += 32) a += sh[j * nt + k];
+      v[j] = warp_sum(a);
     }
   }
   __syncthreads();

@@ -56,6 +56,7 @@ struct KScal {
   double sum_p, sum_s, sum_x;
   double cp, cs;  // preconditioned solves: (c . p), (c . s) of the multigrid's level-0 map
   double ysum;    // preconditioned solves: sum of the V-cycle result before its shift
+  double kap[2];  // preconditioned solves: B p = zp + kap[0], B s = zs + kap[1]
   double tol2;
   int active[2];
   int half[2];
@@ -82,6 +83,7 @@ struct KOp {
   int diag1;       // add x_i (identity part of H)
   const TV* es;    // rank-one column, or null
   const TV* rdot;  // rank-one row (y += es * (rdot . x)); null = all ones
+  const TV* a1 = nullptr;  // A 1 (row sums): the product with a constant shift
 };
 
 template <typename T>
@@ -303,7 +305,8 @@ template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_sum(const TV* __restrict__ x, int64_t n,
                                                   GridReduce gr, double* out,
                                                   const TV* __restrict__ c = nullptr) {
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 1;
+  __shared__ double sh[NU_ * kThreads];
   float part = 0.f;
   double partd = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
@@ -314,8 +317,8 @@ __global__ void __launch_bounds__(kThreads) k_sum(const TV* __restrict__ x, int6
     else
       part += (float)xi;
   }
-  double v[kNV] = {partd + (double)part, 0, 0, 0, 0, 0};
-  grid_reduce<kNV>(v, gr, sh, [&](double* t) { *out = t[0]; });
+  double v[NU_] = {partd + (double)part};
+  grid_reduce<NU_>(v, gr, sh, [&](double* t) { *out = t[0]; });
 }
 
 // sign pattern of a restarted shadow residual (a 32-bit integer hash of i and the seed)
@@ -332,15 +335,22 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_init(KOp<TW, TV> op, Vecs<TV, NRHS> x, Vecs<TV, NRHS> b, Vecs<TV, NRHS> r,
            Vecs<TV, NRHS> rh, Vecs<TV, NRHS> p, const double* sigma_x, KScal* sc, GridReduce gr,
-           double tol2, int maxit, uint32_t seed, Split<NRHS> p2, const float* __restrict__ pcc) {
+           double tol2, int maxit, uint32_t seed, Split<NRHS> p2, const float* __restrict__ pcc,
+           int x_zero) {
   using A = typename Acc<TV>::t;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = kNV;
+  __shared__ double sh[NU_ * kThreads];
   A prr[2] = {0, 0}, pbb[2] = {0, 0}, prh[2] = {0, 0}, psum = 0;
-  const A sig = RANK1 ? (A)*sigma_x : (A)0;
+  const A sig = (RANK1 && !x_zero) ? (A)*sigma_x : (A)0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
        i += (int64_t)gridDim.x * kThreads) {
     A acc[NRHS];
-    gather_rows<K, NRHS>(op, i, (const TV* const*)x.v, acc);
+    if (x_zero) {  // x = 0: r = b without the product
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) acc[q] = 0;
+    } else {
+      gather_rows<K, NRHS>(op, i, (const TV* const*)x.v, acc);
+    }
     const A sgn = seed ? (A)shadow_sign(i, seed) : (A)1;
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
@@ -362,7 +372,7 @@ __global__ void __launch_bounds__(kThreads)
   double v[kNV] = {(double)prr[0], (double)pbb[0], (double)prr[1],
                    (double)pbb[1], (double)prh[0], (double)prh[1]};
   if (RANK1) v[5] = (double)psum;  // NRHS == 1 here: slot 5 carries sum(r)
-  grid_reduce<kNV>(v, gr, sh, [&](double* t) {
+  grid_reduce<NU_>(v, gr, sh, [&](double* t) {
     sc->tol2 = tol2;
     sc->maxit = maxit;
     sc->iters = 0;
@@ -401,7 +411,8 @@ __global__ void __launch_bounds__(kThreads)
              GridReduce gr, Split<NRHS> p2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = NRHS;
+  __shared__ double sh[NU_ * kThreads];
   const A sig = RANK1 ? (A)sc->sum_p : (A)0;
   A pd[2] = {0, 0};
   auto finish_row = [&](int64_t i, A* acc) {
@@ -446,8 +457,10 @@ __global__ void __launch_bounds__(kThreads)
       finish_row(i, acc);
     }
   }
-  double vv[kNV] = {(double)pd[0], (double)pd[1], 0, 0, 0, 0};
-  grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
+  double vv[NU_];
+#pragma unroll
+  for (int q = 0; q < NU_; ++q) vv[q] = (double)pd[q];
+  grid_reduce<NU_>(vv, gr, sh, [&](double* t) {
     if (sc->stage_err) sc->done = 1;
     for (int q = 0; q < NRHS; ++q) {
       if (!sc->active[q]) continue;
@@ -470,7 +483,8 @@ __global__ void __launch_bounds__(kThreads)
                const float* __restrict__ pcc) {
   using A = TV;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 3;
+  __shared__ double sh[NU_ * kThreads];
   A al[2];
   int act[2];
 #pragma unroll
@@ -491,8 +505,8 @@ __global__ void __launch_bounds__(kThreads)
       if (RANK1) psum += pcc ? (A)pcc[i] * si : (rdot ? rdot[i] * si : si);
     }
   }
-  double vv[kNV] = {(double)pss[0], (double)pss[1], (double)psum, 0, 0, 0};
-  grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
+  double vv[NU_] = {(double)pss[0], (double)pss[1], (double)psum};
+  grid_reduce<NU_>(vv, gr, sh, [&](double* t) {
     for (int q = 0; q < NRHS; ++q)
       if (sc->active[q] && t[q] <= sc->tol2 * sc->bb[q]) sc->half[q] = 1;
     if (RANK1) {
@@ -512,7 +526,8 @@ __global__ void __launch_bounds__(kThreads)
              GridReduce gr, Split<NRHS> s2) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 2 * NRHS;
+  __shared__ double sh[NU_ * kThreads];
   const A sig = RANK1 ? (A)sc->sum_s : (A)0;
   A pts[2] = {0, 0}, ptt[2] = {0, 0};
   auto finish_row = [&](int64_t i, A* acc) {
@@ -558,8 +573,13 @@ __global__ void __launch_bounds__(kThreads)
       finish_row(i, acc);
     }
   }
-  double vv[kNV] = {(double)pts[0], (double)ptt[0], (double)pts[1], (double)ptt[1], 0, 0};
-  grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+  double vv[NU_];
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) {
+    vv[2 * q] = (double)pts[q];
+    vv[2 * q + 1] = (double)ptt[q];
+  }
+  grid_reduce<NU_>(vv, gr, sh, [&](double* tt) {
     if (sc->stage_err) sc->done = 1;
     for (int q = 0; q < NRHS; ++q) {
       if (!sc->active[q] || sc->half[q]) continue;
@@ -584,7 +604,8 @@ __global__ void __launch_bounds__(kThreads)
                 KScal* sc, GridReduce gr) {
   using A = TV;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 2 * NRHS;
+  __shared__ double sh[NU_ * kThreads];
   A al[2], om[2];
   int act[2], hf[2];
 #pragma unroll
@@ -614,8 +635,13 @@ __global__ void __launch_bounds__(kThreads)
       prr[q] += ri * ri;
     }
   }
-  double vv[kNV] = {(double)prh[0], (double)prr[0], (double)prh[1], (double)prr[1], 0, 0};
-  grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+  double vv[NU_];
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) {
+    vv[2 * q] = (double)prh[q];
+    vv[2 * q + 1] = (double)prr[q];
+  }
+  grid_reduce<NU_>(vv, gr, sh, [&](double* tt) {
     sc->iters += 1;
     int any = 0;
     for (int q = 0; q < NRHS; ++q) {
@@ -657,7 +683,8 @@ __global__ void __launch_bounds__(kThreads)
                const float* __restrict__ pcc) {
   using A = TV;
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 1;
+  __shared__ double sh[NU_ * kThreads];
   A be[2], om[2];
   int act[2];
 #pragma unroll
@@ -678,8 +705,8 @@ __global__ void __launch_bounds__(kThreads)
       if (RANK1) psum += pcc ? (A)pcc[i] * pi : (rdot ? rdot[i] * pi : pi);
     }
   }
-  double vv[kNV] = {(double)psum, 0, 0, 0, 0, 0};
-  grid_reduce<kNV>(vv, gr, sh, [&](double* tt) {
+  double vv[NU_] = {(double)psum};
+  grid_reduce<NU_>(vv, gr, sh, [&](double* tt) {
     if (RANK1) {
       if (pcc)
         sc->cp = tt[0];
@@ -696,6 +723,18 @@ __global__ void __launch_bounds__(kThreads)
 // Since A is close to diag(1/c) G and A 1 = 0, this inverts the constant mode
 // exactly (B es = 1 / M, and A_f 1 / M = es) and G on the rest.  (c . v) and
 // (c . s) come from the reductions of the kernels that produce p and s.
+
+// B v = z + kap with kap = (mu - sum(z)) / M, so that B v = z - mean(z) + mu / M;
+// the rank-one sum of B v is then mu.
+__device__ __forceinline__ void pc_finish(KScal* sc, int which, double zsum, double inv_ces,
+                                          double inv_R) {
+  const double mu = (which ? sc->cs : sc->cp) * inv_ces;
+  sc->kap[which] = (mu - zsum) * inv_R;
+  if (which)
+    sc->sum_s = mu;
+  else
+    sc->sum_p = mu;
+}
 
 // r0 = c v - mu ce (which = 0: v = p, mu from sc->cp; 1: v = s, from sc->cs)
 template <typename TV>
@@ -780,9 +819,11 @@ __global__ void __launch_bounds__(kThreads)
 // sc->ysum (REDUCE).
 template <bool PROLONG, bool REDUCE>
 __global__ void __launch_bounds__(kThreads)
-    k_pc_up(AmgLevel F, AmgLevel Fine, float* __restrict__ z, KScal* sc, GridReduce gr) {
+    k_pc_up(AmgLevel F, AmgLevel Fine, float* __restrict__ z, KScal* sc, GridReduce gr,
+            int which, double inv_ces, double inv_R) {
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 1;
+  __shared__ double sh[NU_ * kThreads];
   double part = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < F.n;
        i += (int64_t)gridDim.x * kThreads) {
@@ -799,38 +840,193 @@ __global__ void __launch_bounds__(kThreads)
     if (REDUCE) part += (double)zi;
   }
   if (REDUCE) {
-    double v[kNV] = {part, 0, 0, 0, 0, 0};
-    grid_reduce<kNV>(v, gr, sh, [&](double* t) { sc->ysum = t[0]; });
+    double v[NU_] = {part};
+    grid_reduce<NU_>(v, gr, sh, [&](double* t) { pc_finish(sc, which, t[0], inv_ces, inv_R); });
   }
 }
 
-// out = y - mean(y) + mu / M (and its split copy); reduce sum(out) into the
-// rank-one sum that the following SpMV uses.  have_sum = 0: y is already
-// mean-free (a one-level hierarchy solves the lifted coarse system directly).
+// one-level hierarchy: the lifted coarse solve is already mean-free
+__global__ void k_pc_fin1(KScal* sc, int which, double inv_ces, double inv_R) {
+  if (sc->done) return;
+  pc_finish(sc, which, 0.0, inv_ces, inv_R);
+}
+
+// sum_s w[s][i] z[idx[s][i]] for a float vector z: FP64 sums for FP64
+// weights; float-float sums of exact products for FP32 weights in an FP64
+// solve; FP32 sums in an FP32 solve.
+template <typename TW, typename TV>
+struct ZAcc;
+template <>
+struct ZAcc<double, double> {
+  double a = 0.0;
+  __device__ __forceinline__ void add(double w, float z) { a += w * (double)z; }
+  __device__ __forceinline__ double get() const { return a; }
+};
+template <>
+struct ZAcc<float, float> {  // FP32 inner solves: plain FP32 sums
+  float a = 0.f;
+  __device__ __forceinline__ void add(float w, float z) { a = fmaf(w, z, a); }
+  __device__ __forceinline__ float get() const { return a; }
+};
+template <>
+struct ZAcc<float, double> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float w, float z) {
+    float p, e, u, ue;
+    two_prod(w, z, p, e);
+    two_sum(h, p, u, ue);
+    h = u;
+    l += ue + e;
+  }
+  __device__ __forceinline__ double get() const { return (double)h + (double)l; }
+};
+
+// Preconditioned-solve SpMVs with the operand B v = z + kap (pressure, one
+// right side, staged tiles when K > 0):
+//   y = A z + kap (A 1) + es mu,   mu = rank-one sum of B v (sc->sum_p / sum_s)
+// WHICH = 0: v = A p^, reduce (rh, v) -> alpha;  WHICH = 1: t = A s^, reduce
+// (t, s), (t, t) -> omega.
+template <int K, typename TW, typename TV, int WHICH>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_pc(KOp<TW, TV> op, const float* __restrict__ z, TV* __restrict__ y,
+              const TV* __restrict__ dotv, KScal* sc, GridReduce gr) {
+  if (sc->done) return;
+  constexpr int NU_ = 2;
+  __shared__ double sh[NU_ * kThreads];
+  const TV kap = (TV)sc->kap[WHICH];
+  const TV sig = (TV)(WHICH ? sc->sum_s : sc->sum_p);
+  TV d0 = 0, d1 = 0;
+  auto finish_row = [&](int64_t i, TV acc) {
+    const TV yi = acc + kap * op.a1[i] + op.es[i] * sig;
+    y[i] = yi;
+    const TV di = dotv[i];  // rh for WHICH 0, s for WHICH 1
+    d0 += di * yi;
+    if (WHICH) d1 += yi * yi;
+  };
+  if constexpr (K > 0) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
+    for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+      const int64_t row0 = tix * kTileRows;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      const int64_t i = row0 + threadIdx.x;
+      if (i < op.n) {
+        ZAcc<TW, TV> acc;
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          acc.add(tile->w[q * kTileRows + threadIdx.x], z[tile->idx[q * kTileRows + threadIdx.x]]);
+        finish_row(i, (TV)acc.get());
+      }
+    }
+  } else {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * kThreads) {
+      ZAcc<TW, TV> acc;
+      for (int q = 0; q < op.k; ++q) acc.add(op.w[q * op.ld + i], z[op.idx[q * op.ld + i]]);
+      finish_row(i, (TV)acc.get());
+    }
+  }
+  double vv[NU_] = {(double)d0, (double)d1};
+  grid_reduce<NU_>(vv, gr, sh, [&](double* t) {
+    if (sc->stage_err) sc->done = 1;
+    if (!sc->active[0]) return;
+    if (WHICH == 0) {
+      const double rv = t[0];
+      if (rv == 0.0 || !isfinite(rv)) {
+        sc->active[0] = 0;
+        sc->status = isfinite(rv) ? 1 : 2;
+        return;
+      }
+      sc->alpha[0] = sc->rho[0] / rv;
+    } else {
+      if (sc->half[0]) return;
+      const double ts = t[0], t2 = t[1];
+      if (!(t2 > 0.0) || !isfinite(ts)) {
+        sc->omega[0] = 0.0;
+        sc->active[0] = 0;
+        sc->status = isfinite(t2) ? 3 : 2;
+        return;
+      }
+      sc->omega[0] = ts / t2;
+    }
+  });
+}
+
+// x += alpha (zp + kap_p) + omega (zs + kap_s) ; r = s - omega t ; reduce (rh, r), (r, r)
 template <typename TV>
 __global__ void __launch_bounds__(kThreads)
-    k_pc_out(int64_t n, const float* __restrict__ y, int have_sum, double inv_ces, double inv_R,
-             int which, TV* __restrict__ out, float2* __restrict__ out2, KScal* sc,
-             GridReduce gr) {
+    k_update_xr_pc(int64_t n, TV* __restrict__ x, TV* __restrict__ r, const TV* __restrict__ rh,
+                   const float* __restrict__ zp, const float* __restrict__ zs,
+                   const TV* __restrict__ s, const TV* __restrict__ t, KScal* sc, GridReduce gr) {
   if (sc->done) return;
-  __shared__ double sh[kNV * kThreads / 32];
-  const double mu = (which ? sc->cs : sc->cp) * inv_ces;
-  const double shift = (mu - (have_sum ? sc->ysum : 0.0)) * inv_R;
-  double part = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    const double zi = (double)y[i] + shift;
-    out[i] = (TV)zi;
-    if (out2) out2[i] = split2(zi);
-    part += zi;
+  constexpr int NU_ = 2;
+  __shared__ double sh[NU_ * kThreads];
+  const TV al = (TV)sc->alpha[0], om = (TV)sc->omega[0];
+  const TV kp = (TV)sc->kap[0], ks = (TV)sc->kap[1];
+  const int act = sc->active[0], hf = sc->half[0];
+  TV prh = 0, prr = 0;
+  if (act) {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
+      const TV si = s[i];
+      TV ri;
+      if (hf) {
+        x[i] += al * ((TV)zp[i] + kp);
+        ri = si;
+      } else {
+        x[i] += al * ((TV)zp[i] + kp) + om * ((TV)zs[i] + ks);
+        ri = si - om * t[i];
+      }
+      r[i] = ri;
+      prh += rh[i] * ri;
+      prr += ri * ri;
+    }
   }
-  double v[kNV] = {part, 0, 0, 0, 0, 0};
-  grid_reduce<kNV>(v, gr, sh, [&](double* t) {
-    if (which)
-      sc->sum_s = t[0];
-    else
-      sc->sum_p = t[0];
+  double vv[NU_] = {(double)prh, (double)prr};
+  grid_reduce<NU_>(vv, gr, sh, [&](double* tt) {
+    sc->iters += 1;
+    if (!sc->active[0]) {
+      sc->done = 1;
+      return;
+    }
+    const double rho_new = tt[0], rr = tt[1];
+    sc->rr[0] = rr;
+    bool go = false;
+    if (!isfinite(rr)) {
+      sc->status = 2;
+      sc->active[0] = 0;
+    } else if (rr > 1e8 * sc->bb[0] && sc->bb[0] > 0.0) {
+      sc->status = 5;
+      sc->active[0] = 0;
+    } else if (sc->half[0] || rr <= sc->tol2 * sc->bb[0]) {
+      sc->active[0] = 0;
+    } else if (rho_new == 0.0 || sc->omega[0] == 0.0) {
+      sc->status = 4;
+      sc->active[0] = 0;
+    } else {
+      sc->beta[0] = (rho_new / sc->rho[0]) * (sc->alpha[0] / sc->omega[0]);
+      sc->rho[0] = rho_new;
+      go = true;
+    }
+    if (!go || sc->iters >= sc->maxit) sc->done = 1;
   });
+}
+
+// row sums of an ELL operator in FP64 (A 1)
+template <typename TW>
+__global__ void k_rowsum(int64_t n, int64_t ld, int k, const TW* __restrict__ w,
+                         double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int q = 0; q < k; ++q) a += (double)w[q * ld + i];
+    out[i] = a;
+  }
 }
 
 // ------------------------------------------------- refinement helper kernels
@@ -839,7 +1035,8 @@ template <int K, int NRHS, bool RANK1>
 __global__ void __launch_bounds__(kThreads)
     k_residual64(KOp<double, double> op, Vecs<double, NRHS> x, Vecs<double, NRHS> b,
                  Vecs<double, NRHS> r, const double* sigma_x, double* out4, GridReduce gr) {
-  __shared__ double sh[kNV * kThreads / 32];
+  constexpr int NU_ = 2 * NRHS;
+  __shared__ double sh[NU_ * kThreads];
   const double sig = RANK1 ? *sigma_x : 0.0;
   double prr[2] = {0, 0}, pbb[2] = {0, 0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
@@ -857,9 +1054,14 @@ __global__ void __launch_bounds__(kThreads)
       pbb[q] += bi * bi;
     }
   }
-  double vv[kNV] = {prr[0], pbb[0], prr[1], pbb[1], 0, 0};
-  grid_reduce<kNV>(vv, gr, sh, [&](double* t) {
-    for (int j = 0; j < kNV; ++j) out4[j] = t[j];
+  double vv[NU_];
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) {
+    vv[2 * q] = prr[q];
+    vv[2 * q + 1] = pbb[q];
+  }
+  grid_reduce<NU_>(vv, gr, sh, [&](double* t) {
+    for (int j = 0; j < NU_; ++j) out4[j] = t[j];
   });
 }
 
@@ -1266,7 +1468,8 @@ struct StepPlan {
   double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
   struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
   Amg* amg = nullptr;                 // pressure preconditioner (precond = 1)
-  double *ph = nullptr, *sh = nullptr;  // preconditioned search directions B p, B s
+  double* a1 = nullptr;    // row sums of the FP64 pressure operator
+  float* a1_32 = nullptr;  // row sums of its FP32 copy
   // CUDA graphs of Krylov iteration chunks: one per solve (its operator,
   // vectors and preconditioner) and chunk length, captured on first use on a
   // private stream and replayed on the caller's stream
@@ -1409,11 +1612,17 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
                    "rank-one column copy"));
     TRY(check_cuda(ctx, cudaStreamSynchronize(st), "diagonal sync"));
     TRY(amg_build(ctx, f, hd.data(), hes.data(), &p->amg, st));
-    TRY(palloc(ctx, p, &p->ph, f.M));
-    TRY(palloc(ctx, p, &p->sh, f.M));
+    TRY(palloc(ctx, p, &p->a1, f.M));
+    k_rowsum<double><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, p->Lw, p->a1);
+    TRY(check_cuda(ctx, cudaGetLastError(), "row sums"));
   }
   if (p->mix) {
     TRY(to32(ctx, p, p->Lw, np, &p->Lw32, st));
+    if (f.precond) {
+      k_rowsum<float><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, p->Lw32, p->kw64[0][0]);
+      TRY(check_cuda(ctx, cudaGetLastError(), "row sums"));
+      TRY(to32(ctx, p, p->kw64[0][0], f.M, &p->a1_32, st));
+    }
     TRY(to32(ctx, p, p->es, f.M, &p->es32, st));
     TRY(to32(ctx, p, p->Hw, nv, &p->Hw32, st));
     TRY(to32(ctx, p, f.vv_dx, nv, &p->vv_dx32, st));
@@ -1469,10 +1678,10 @@ void collect_events(StepPlan* P) {
   P->ev_used = 0;
 }
 
-// out = B v (one application of the multigrid preconditioner, 2 nlev + 1 launches)
+// B v = zout + kap[which] (one application of the multigrid preconditioner,
+// 2 nlev launches)
 template <typename TV>
-void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* out, float2* out2,
-            cudaStream_t st) {
+void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, float* zout, cudaStream_t st) {
   const int G = P->grid;
   auto grid_for = [&](int64_t rows) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(G, (rows + kThreads - 1) / kThreads));
@@ -1484,16 +1693,16 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* out, float2* 
         a->lev[l], a->lev[l + 1].n, a->lev[l + 1].r, P->sc);
   const AmgLevel& C = a->lev[a->nlev - 1];
   const AmgLevel& Cf = a->lev[a->nlev >= 2 ? a->nlev - 2 : 0];
-  k_pc_coarse<<<grid_for(a->nc * 32), kThreads, 0, st>>>(a->nc, a->Xc, C.r, C.z, Cf,
-                                                         a->nlev >= 2 ? 1 : 0, P->sc);
+  k_pc_coarse<<<grid_for(a->nc * 32), kThreads, 0, st>>>(
+      a->nc, a->Xc, C.r, a->nlev >= 2 ? C.z : zout, Cf, a->nlev >= 2 ? 1 : 0, P->sc);
   for (int l = a->nlev - 2; l >= 1; --l)
-    k_pc_up<true, false><<<grid_for(a->lev[l].n), kThreads, 0, st>>>(a->lev[l], a->lev[l - 1],
-                                                                     a->lev[l].z, P->sc, P->gr);
+    k_pc_up<true, false><<<grid_for(a->lev[l].n), kThreads, 0, st>>>(
+        a->lev[l], a->lev[l - 1], a->lev[l].z, P->sc, P->gr, which, 0.0, 0.0);
   if (a->nlev >= 2)
-    k_pc_up<false, true><<<G, kThreads, 0, st>>>(a->lev[0], a->lev[0], a->lev[0].z, P->sc,
-                                                 P->gr);
-  k_pc_out<TV><<<G, kThreads, 0, st>>>(n, a->lev[0].z, a->nlev >= 2 ? 1 : 0, a->inv_ces,
-                                       a->inv_R, which, out, out2, P->sc, P->gr);
+    k_pc_up<false, true><<<G, kThreads, 0, st>>>(a->lev[0], a->lev[0], zout, P->sc, P->gr, which,
+                                                 a->inv_ces, a->inv_R);
+  else
+    k_pc_fin1<<<1, 1, 0, st>>>(P->sc, which, a->inv_ces, a->inv_R);
 }
 
 // The graph of `n` iterations of one solve, captured on first use.
@@ -1540,9 +1749,8 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
              cudaStream_t st, bool prof = false, uint32_t seed_base = 0,
              float2* const* p2s = nullptr, float2* const* s2s = nullptr,
-             const Amg* pc = nullptr) {
-  static_assert(sizeof(TV) == 8, "the preconditioned directions are FP64 vectors");
-  Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T, PH, SH;
+             const Amg* pc = nullptr, bool x_zero = false) {
+  Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
   Split<NRHS> P2, S2, none{};
   for (int q = 0; q < NRHS; ++q) {
     P2.v[q] = p2s ? p2s[q] : nullptr;
@@ -1557,17 +1765,11 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     V.v[q] = work[3][q];
     S.v[q] = work[4][q];
     T.v[q] = work[5][q];
-    PH.v[q] = PP.v[q];
-    SH.v[q] = S.v[q];
   }
-  if (pc) {
-    if (NRHS != 1 || !RANK1 || op.rdot)
-      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid preconditioner: pressure solves only");
-    PH.v[0] = (TV*)P->ph;
-    SH.v[0] = (TV*)P->sh;
-  }
+  if (pc && (NRHS != 1 || !RANK1 || op.rdot || !op.a1))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid preconditioner: pressure solves only");
   const float* pcc = pc ? pc->c : nullptr;
-  const int vc_launches = pc ? 2 * pc->nlev + 1 : 0;
+  const int vc_launches = pc ? 2 * pc->nlev : 0;
   const int G = P->grid;
   double* sigx = P->dscal;
   KScal* h = (KScal*)ctx->host_pinned;
@@ -1592,6 +1794,20 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem),
                        "smem attribute");
+    if constexpr (NRHS == 1 && RANK1) {
+      if (!rc0 && pc)
+        rc0 = check_cuda(ctx,
+                         cudaFuncSetAttribute(k_spmv_pc<K, TW, TV, 0>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "smem attribute");
+      if (!rc0 && pc)
+        rc0 = check_cuda(ctx,
+                         cudaFuncSetAttribute(k_spmv_pc<K, TW, TV, 1>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "smem attribute");
+    }
     if (rc0) return rc0;
   }
   for (int q = 0; q < NRHS; ++q) {
@@ -1603,18 +1819,21 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   // A breakdown of the recurrences (a zero inner product) restarts the method
   // from the current iterate with a fresh shadow residual.
   for (int restart = 0;; ++restart) {
-    if (RANK1) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx, op.rdot);
+    // the caller's x0 = 0 holds only until the first restart
+    const bool xz = x_zero && restart == 0;
+    if (RANK1 && !xz) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx, op.rdot);
     k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
                                                     tol * tol, maxit - total,
                                                     (restart || seed_base)
                                                         ? 0x51ED27u + 977u * seed_base + restart
                                                         : 0u,
-                                                    pc ? none : P2, pcc);
-    P->launches += (RANK1 ? 2 : 1) + (pc ? vc_launches : 0);
-    if (pc) vcycle<TV>(P, pc, PP.v[0], 0, PH.v[0], P2.v[0], st);
+                                                    pc ? none : P2, pcc, xz ? 1 : 0);
+    P->launches += (RANK1 && !xz ? 2 : 1) + (pc ? vc_launches : 0);
+    if (pc) vcycle<TV>(P, pc, PP.v[0], 0, pc->zp, st);
     int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
     if (rc) return rc;
-    int issued = 0, chunk = 4;
+    int issued = 0, chunk = 4, prev_iters = 0;
+    double prev_rel = -1.0;
     const int budget = maxit - total;
     for (;;) {
       rc = check_cuda(ctx, cudaMemcpyAsync(h, P->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st),
@@ -1624,25 +1843,57 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (rc) return rc;
       if (prof) collect_events(P);
       if (h->done || issued >= budget) break;
-      int n = std::min(chunk, budget - issued);
+      // Next chunk: the iterations that the residual's rate over the last
+      // chunk predicts are still needed, plus one (doubling while it has no rate).
+      int n = chunk;
+      double rel = 0.0;
+      for (int q = 0; q < NRHS; ++q)
+        if (h->active[q] && h->bb[q] > 0) rel = fmax(rel, sqrt(h->rr[q] / h->bb[q]));
+      if (prev_rel > 0.0 && rel > 0.0 && rel < prev_rel && h->iters > prev_iters) {
+        const double rate = pow(rel / prev_rel, 1.0 / (double)(h->iters - prev_iters));
+        const double need = log(sqrt(h->tol2) / rel) / log(rate);
+        if (std::isfinite(need)) n = (int)std::min(64.0, std::max(1.0, ceil(need) + 1.0));
+      }
+      prev_rel = rel;
+      prev_iters = h->iters;
+      n = std::min(n, budget - issued);
       if (prof) n = std::min(n, StepPlan::kEv / 4);
       // one chunk of iterations; every kernel returns at once after the solve
       // has finished (sc->done), so a chunk may overshoot harmlessly
       auto issue = [&](cudaStream_t s, int cnt) {
         for (int it = 0; it < cnt; ++it) {
+          if (pc) {  // right-preconditioned: the SpMVs act on B p = zp + kap, B s = zs + kap
+            if constexpr (NRHS == 1 && RANK1) {
+              if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+              k_spmv_pc<K, TW, TV, 0><<<Gs, kThreads, smem, s>>>(op, pc->zp, V.v[0], RH.v[0],
+                                                                   P->sc, P->gr);
+              if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+              k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
+                                                             none, pcc);
+              vcycle<TV>(P, pc, S.v[0], 1, pc->zs, s);
+              if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+              k_spmv_pc<K, TW, TV, 1><<<Gs, kThreads, smem, s>>>(op, pc->zs, T.v[0], S.v[0],
+                                                                   P->sc, P->gr);
+              if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
+              k_update_xr_pc<TV><<<G, kThreads, 0, s>>>(op.n, X.v[0], R.v[0], RH.v[0], pc->zp,
+                                                        pc->zs, S.v[0], T.v[0], P->sc, P->gr);
+              k_update_p<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
+                                                             none, pcc);
+              vcycle<TV>(P, pc, PP.v[0], 0, pc->zp, s);
+            }
+            continue;
+          }
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PH, V, RH, P->sc, P->gr, P2);
+          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PP, V, RH, P->sc, P->gr, P2);
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
           k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
-                                                         pc ? none : S2, pcc);
-          if (pc) vcycle<TV>(P, pc, S.v[0], 1, SH.v[0], S2.v[0], s);
+                                                         S2, pcc);
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-          k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, SH, S, T, P->sc, P->gr, S2);
+          k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, S, S, T, P->sc, P->gr, S2);
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-          k_update_xr<NRHS><<<G, kThreads, 0, s>>>(op.n, X, R, RH, PH, SH, S, T, P->sc, P->gr);
+          k_update_xr<NRHS><<<G, kThreads, 0, s>>>(op.n, X, R, RH, PP, S, S, T, P->sc, P->gr);
           k_update_p<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
-                                                         pc ? none : P2, pcc);
-          if (pc) vcycle<TV>(P, pc, PP.v[0], 0, PH.v[0], P2.v[0], s);
+                                                         P2, pcc);
         }
       };
       if (prof) {
@@ -1651,11 +1902,14 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
         const void* const key[10] = {(const void*)&bicgstab<K, NRHS, RANK1, TW, TV>,
                                      op.idx, op.w, op.es, X.v[0], X.v[NRHS - 1], pc,
                                      P2.v[0], S2.v[0], work[0][0]};
-        cudaGraphExec_t g = nullptr;
-        rc = chunk_graph(ctx, P, key, n, issue, &g);
-        if (rc) return rc;
-        rc = check_cuda(ctx, cudaGraphLaunch(g, st), "graph launch");
-        if (rc) return rc;
+        for (int part = 64; part >= 1; part >>= 1) {  // n as a sum of powers of two
+          if (!(n & part)) continue;
+          cudaGraphExec_t g = nullptr;
+          rc = chunk_graph(ctx, P, key, part, issue, &g);
+          if (rc) return rc;
+          rc = check_cuda(ctx, cudaGraphLaunch(g, st), "graph launch");
+          if (rc) return rc;
+        }
       }
       P->launches += (int64_t)(5 + 2 * vc_launches) * n;
       rc = check_cuda(ctx, cudaGetLastError(), "bicgstab iteration");
@@ -1696,10 +1950,11 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
 }
 
 // FP64 iterative refinement: the residual uses the FP64 operator; each
-// correction solves the FP32-weight operator with FP64 BiCGSTAB recurrences,
-// its SpMVs gathering split FP32 copies with float-float sums (FP32 pipes,
-// 4-byte weights).  A correction that does not lower the FP64 residual is
-// undone and the inner solve repeated with another shadow residual.
+// correction solves the FP32 copy of the operator in FP32 (FP32 weights,
+// vectors and recurrences; the pressure solves with the FP32 V-cycle) to a
+// loose relative tolerance, from the normalised residual.  A correction that
+// does not lower the FP64 residual is undone and the inner solve repeated with
+// another shadow residual.
 template <int NRHS>
 __global__ void k_scale_zero(int64_t n, Vecs<double, NRHS> r, Vecs<double, NRHS> b,
                              Vecs<double, NRHS> e, double inv0, double inv1) {
@@ -1726,16 +1981,17 @@ __global__ void k_addcorr64(int64_t n, Vecs<double, NRHS> x, Vecs<double, NRHS> 
 
 template <int K, int NRHS, bool RANK1>
 int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
-           const KOp<float, double>& op32, double* const* x, const double* const* b, double tol,
+           const KOp<float, float>& op32, double* const* x, const double* const* b, double tol,
            double inner_tol, int maxit, SolveResult* res, int* sweeps, cudaStream_t st,
            bool prof = false) {
-  Vecs<double, NRHS> X, B, R, B64, E64;
+  Vecs<double, NRHS> X, B, R;
+  Vecs<float, NRHS> R32, E32;
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
     B.v[q] = (double*)b[q];
     R.v[q] = P->r64[q];
-    B64.v[q] = P->b64[q];
-    E64.v[q] = P->e64[q];
+    R32.v[q] = P->r32[q];
+    E32.v[q] = P->e32[q];
   }
   const int G = P->grid;
   int used = 0, failures = 0, retries = 0;
@@ -1769,8 +2025,8 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     }
     if (sweep > 0 && (!finite || !(worst < prev_rel))) {
       // the last correction made things worse: undo it and solve again
-      k_addcorr64<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E64, -last_nrm[0],
-                                                NRHS > 1 ? -last_nrm[NRHS - 1] : 0.0);
+      k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, -last_nrm[0],
+                                              NRHS > 1 ? -last_nrm[NRHS - 1] : 0.0);
       P->launches += 1;
       rc = check_cuda(ctx, cudaGetLastError(), "undo correction");
       if (rc) return rc;
@@ -1794,19 +2050,19 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     ++*sweeps;
     const double i0 = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
     const double i1 = NRHS > 1 && nrm[NRHS - 1] > 0 ? 1.0 / nrm[NRHS - 1] : 0.0;
-    k_scale_zero<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, B64, E64, i0, i1);
+    k_to32<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, R32, E32, i0, i1);
     P->launches += 2;  // with the correction below
     SolveResult inner;
-    rc = bicgstab<K, NRHS, RANK1, float, double>(ctx, P, op32, E64.v, B64.v, P->kw64, inner_tol,
-                                                 maxit - used, &inner, st, prof, retries, P->p2,
-                                                 P->s2, RANK1 ? P->amg : nullptr);
+    rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
+                                                maxit - used, &inner, st, prof, retries, nullptr,
+                                                nullptr, RANK1 ? P->amg : nullptr, true);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
     last_nrm[0] = nrm[0];
     last_nrm[1] = nrm[1];
-    k_addcorr64<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E64, nrm[0],
-                                              NRHS > 1 ? nrm[NRHS - 1] : 0.0);
+    k_addcorr<NRHS><<<G, kThreads, 0, st>>>(op64.n, X, E32, nrm[0],
+                                            NRHS > 1 ? nrm[NRHS - 1] : 0.0);
     rc = check_cuda(ctx, cudaGetLastError(), "correction");
     if (rc) return rc;
   }
@@ -1842,9 +2098,9 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     }
   }
   KOp<double, double> H64{f.vv_idx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
-  KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, k, 0, P->es};
-  KOp<float, double> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
-  KOp<float, double> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es, nullptr};
+  KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, k, 0, P->es, nullptr, P->a1};
+  KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
+  KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es32, nullptr, P->a1_32};
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
                 P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,
