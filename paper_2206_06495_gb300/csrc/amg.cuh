@@ -33,7 +33,7 @@
 namespace rbffd {
 
 constexpr int kAmgMaxLevels = 16;
-constexpr int kAmgCoarse = 512;
+constexpr int kAmgCoarse = 2048;  // coarsest level: at most this many rows, solved densely
 constexpr float kAmgOmega = 0.8f;
 constexpr float kAmgCoarseScale = 1.6f;
 
