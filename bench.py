@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=400000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiler capture: set up, take --warmup steps, then one step between "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off); prints its "
+                         "statistics instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -359,13 +363,14 @@ def run_ours(args):
     value = steps_total / (r["ms"] * 1e-3)
     e2e = steps_total / (r["e2e_ms"] * 1e-3)
     agg = r["agg"]
-    # roofline of the dominant kernel: the SpMV of the pressure solve
+    # roofline of the pressure solve's SpMV (k_spmv_pc): per row the stencil's
+    # k column indices and k weights, the operand z (read once), the output,
+    # the dot-product partner, the row sum A 1 and the rank-one column
     k = 28
     if head == "mixed":
-        # FP32 weights, split (hi, lo) FP32 gathers, FP64 output, rh and rank-one column
-        bytes_row, key = 8 * k + 32, "k_spmv_ff_rank1"
+        bytes_row, key = 8 * k + 5 * 4, "k_spmv_pc_fp32"  # FP32 inner solves
     else:
-        bytes_row, key = 12 * k + 32, "k_spmv_fp64_rank1"
+        bytes_row, key = 12 * k + 4 + 4 * 8, "k_spmv_pc_fp64"
     per_launch_ms = r["spmv_ms"] / max(r["spmv_launches"], 1)
     achieved = nd.M * bytes_row / (per_launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic(key, nd.M)
@@ -437,8 +442,43 @@ def run_reference(args):
             "wall_s": time.time() - t0}
 
 
+def profile_step(args):
+    """One fractional step of the benchmark workload between cudaProfilerStart
+    and cudaProfilerStop, after --warmup steps (plan, graphs and caches warm)."""
+    import numpy as np
+    import torch
+
+    from paper_2206_06495_gb300 import build
+    from paper_2206_06495_gb300 import nodesets as ns
+    build.build()
+    from paper_2206_06495_gb300 import rbffd as R
+
+    prec = R.PREC_FP64 if args.only == "fp64" else R.PREC_MIXED
+    ctx = R.Context(28, 7, 3)
+    nd = ns.jittered_cavity(args.n, 2)
+    flow = R.flow_from_nodes(ctx, nd, Re=args.re, dt=args.dt, precision=prec, tol=args.tol,
+                             inner_tol=1e-2, max_iter=args.max_iter)
+    gu_h = np.zeros(nd.N)
+    gu_h[nd.v_wall == ns.WALL_TOP] = 1.0
+    gu = torch.as_tensor(gu_h, device="cuda")
+    gv = torch.zeros_like(gu)
+    st = R.State.zeros(flow)
+    for _ in range(args.warmup):
+        R.step(ctx, flow, st, gu, gv, 1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    s = R.step(ctx, flow, st, gu, gv, 1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return {"profile_step": "mixed" if prec == R.PREC_MIXED else "fp64", "M": nd.M, "N": nd.N,
+            "stats": s}
+
+
 def main():
     args = parse()
+    if args.profile_step:
+        print(json.dumps(profile_step(args)))
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))
