@@ -359,7 +359,8 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
   a->inv_ces = 1.0 / ces;
   a->inv_R = 1.0 / (double)M;
   if ((rc = upload(ctx, a, hc, &a->c, st)) || (rc = upload(ctx, a, hce, &a->ce, st)) ||
-      (rc = aalloc(ctx, a, &a->zp, M)) || (rc = aalloc(ctx, a, &a->zs, M)))
+      (rc = aalloc(ctx, a, &a->zp, M)) || (rc = aalloc(ctx, a, &a->zs, M)) ||
+      (rc = aalloc(ctx, a, &a->zpd, M)) || (rc = aalloc(ctx, a, &a->zsd, M)))
     return fail(rc);
   if ((rc = check_cuda(ctx, cudaStreamSynchronize(st), "multigrid upload"))) return fail(rc);
   *out = a;

@@ -65,7 +65,8 @@ struct Amg {
   // mu = (c . v) / (c . es); the result is z + mu / M (see step.cu)
   float* c = nullptr;   // [M] diag(G) / diag(A)
   float* ce = nullptr;  // [M] c * es
-  float *zp = nullptr, *zs = nullptr;  // [M] V-cycle results for p and s (B v = z + kap)
+  float *zp = nullptr, *zs = nullptr;     // [M] V-cycle results for p and s (B v = z + kap), FP32 solves
+  double *zpd = nullptr, *zsd = nullptr;  // the same for FP64 solves
   double inv_ces = 0.0;
   double inv_R = 0.0;
   std::vector<int> sizes;  // rows per level (host copy, for reports)

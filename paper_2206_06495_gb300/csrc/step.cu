@@ -15,14 +15,16 @@
 //             on wall rows, which are identity rows (Eq. u_ss);
 //   pressure: S (L - e 1^T) x = S b, L = D^(P,P)_Lap inside and the Neumann
 //             row n_x D_x + n_y D_y on boundary rows, e = indicator of interior
-//             rows, S = diag(1/L_ii) inside and diag(1/sum_j |L_ij|) on
-//             boundary rows.  L annihilates constants, so the rank-one term
+//             rows, S = diag(1/L_ii) (1/sum_j |L_ij| on a row whose diagonal
+//             vanishes).  L annihilates constants, so the rank-one term
 //             fixes the constant mode: x = p~ + c 1 for the mean-zero solution
 //             p~ of the bordered system [L e; 1^T 0] (the multiplier c absorbs
 //             the incompatibility of the non-symmetric L in the interior rows),
 //             and p~ = x - mean(x).
 // FP64 precision: BiCGSTAB in FP64.  MIXED: FP64 iterative refinement whose
-// corrections come from FP32 BiCGSTAB on FP32 copies of the scaled operators.
+// corrections come from FP32 solves on FP32 copies of the scaled operators.
+// Pressure solves are right-preconditioned by the multigrid V-cycle of
+// amg.cuh (one application per search direction).
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -202,62 +204,6 @@ struct Vecs {
   TV* v[NRHS];
 };
 
-// Split FP32 copies (hi, lo) of the vectors an FP32-weight operator gathers
-// inside an FP64 Krylov solve (null when the operator is not FP32 x FP64).
-template <int NRHS>
-struct Split {
-  float2* v[NRHS];
-};
-
-template <typename TW, typename TV>
-struct IsFF {
-  static constexpr bool value = false;
-};
-template <>
-struct IsFF<float, double> {
-  static constexpr bool value = true;
-};
-
-// exact product and sum of two floats (Dekker / Knuth), for float-float sums
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = a * b;
-  e = fmaf(a, b, -p);
-}
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// sum_s w[s][i] * x[idx[s][i]] with FP32 weights and x split into (hi, lo):
-// the products and the running sum are kept as float-float pairs, so the
-// result carries about 44 bits although every operation is FP32.
-template <int K, int NRHS>
-__device__ __forceinline__ void gather_ff(const KOp<float, double>& op, int64_t i,
-                                          const float2* const* x2, double* acc) {
-  float sh[NRHS], sl[NRHS];
-#pragma unroll
-  for (int r = 0; r < NRHS; ++r) sh[r] = sl[r] = 0.f;
-  const int k = K > 0 ? K : op.k;
-#pragma unroll(K > 0 ? K : 1)
-  for (int s = 0; s < k; ++s) {
-    const int j = op.idx[s * op.ld + i];
-    const float w = op.w[s * op.ld + i];
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) {
-      const float2 xj = x2[r][j];
-      float p, e, t, te;
-      two_prod(w, xj.x, p, e);
-      e = fmaf(w, xj.y, e);
-      two_sum(sh[r], p, t, te);
-      sh[r] = t;
-      sl[r] += te + e;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < NRHS; ++r) acc[r] = (double)sh[r] + (double)sl[r];
-}
-
 // the same sums with idx and w read from a staged tile
 template <int K, int NRHS, typename TW, typename TV>
 __device__ __forceinline__ void gather_tile(const EllStage<K, TW>* t, int tid, const TV* const* x,
@@ -272,31 +218,6 @@ __device__ __forceinline__ void gather_tile(const EllStage<K, TW>* t, int tid, c
 #pragma unroll
     for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
   }
-}
-
-template <int K, int NRHS>
-__device__ __forceinline__ void gather_tile_ff(const EllStage<K, float>* t, int tid,
-                                               const float2* const* x2, double* acc) {
-  float sh[NRHS], sl[NRHS];
-#pragma unroll
-  for (int r = 0; r < NRHS; ++r) sh[r] = sl[r] = 0.f;
-#pragma unroll
-  for (int s = 0; s < K; ++s) {
-    const int j = t->idx[s * kTileRows + tid];
-    const float w = t->w[s * kTileRows + tid];
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) {
-      const float2 xj = x2[r][j];
-      float p, e, u, ue;
-      two_prod(w, xj.x, p, e);
-      e = fmaf(w, xj.y, e);
-      two_sum(sh[r], p, u, ue);
-      sh[r] = u;
-      sl[r] += ue + e;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < NRHS; ++r) acc[r] = (double)sh[r] + (double)sl[r];
 }
 
 // ----------------------------------------------------------- Krylov kernels
@@ -335,8 +256,7 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_init(KOp<TW, TV> op, Vecs<TV, NRHS> x, Vecs<TV, NRHS> b, Vecs<TV, NRHS> r,
            Vecs<TV, NRHS> rh, Vecs<TV, NRHS> p, const double* sigma_x, KScal* sc, GridReduce gr,
-           double tol2, int maxit, uint32_t seed, Split<NRHS> p2, const float* __restrict__ pcc,
-           int x_zero) {
+           double tol2, int maxit, uint32_t seed, const float* __restrict__ pcc, int x_zero) {
   using A = typename Acc<TV>::t;
   constexpr int NU_ = kNV;
   __shared__ double sh[NU_ * kThreads];
@@ -362,7 +282,6 @@ __global__ void __launch_bounds__(kThreads)
       r.v[q][i] = (TV)ri;
       rh.v[q][i] = (TV)(sgn * ri);
       p.v[q][i] = (TV)ri;
-      if (IsFF<TW, TV>::value && p2.v[q]) p2.v[q][i] = split2((double)ri);
       prr[q] += ri * ri;
       pbb[q] += bi * bi;
       prh[q] += sgn * ri * ri;
@@ -408,7 +327,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
-             GridReduce gr, Split<NRHS> p2) {
+             GridReduce gr) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
   constexpr int NU_ = NRHS;
@@ -439,10 +358,7 @@ __global__ void __launch_bounds__(kThreads)
       const int64_t i = row0 + threadIdx.x;
       if (i < op.n) {
         A acc[NRHS];
-        if constexpr (IsFF<TW, TV>::value)
-          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)p2.v, acc);
-        else
-          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)p.v, acc);
+        gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)p.v, acc);
         finish_row(i, acc);
       }
     }
@@ -450,10 +366,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
          i += (int64_t)gridDim.x * kThreads) {
       A acc[NRHS];
-      if constexpr (IsFF<TW, TV>::value)
-        gather_ff<K, NRHS>(op, i, (const float2* const*)p2.v, acc);
-      else
-        gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
+      gather_rows<K, NRHS>(op, i, (const TV* const*)p.v, acc);
       finish_row(i, acc);
     }
   }
@@ -479,8 +392,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_s(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> v, Vecs<TV, NRHS> s, KScal* sc,
-               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> s2,
-               const float* __restrict__ pcc) {
+               GridReduce gr, const TV* __restrict__ rdot, const float* __restrict__ pcc) {
   using A = TV;
   if (sc->done) return;
   constexpr int NU_ = 3;
@@ -500,7 +412,6 @@ __global__ void __launch_bounds__(kThreads)
       if (!act[q]) continue;
       const A si = r.v[q][i] - al[q] * v.v[q][i];
       s.v[q][i] = si;
-      if (s2.v[0]) s2.v[q][i] = split2((double)si);
       pss[q] += si * si;
       if (RANK1) psum += pcc ? (A)pcc[i] * si : (rdot ? rdot[i] * si : si);
     }
@@ -523,7 +434,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> sres, Vecs<TV, NRHS> t, KScal* sc,
-             GridReduce gr, Split<NRHS> s2) {
+             GridReduce gr) {
   using A = typename Acc<TV>::t;
   if (sc->done) return;
   constexpr int NU_ = 2 * NRHS;
@@ -555,10 +466,7 @@ __global__ void __launch_bounds__(kThreads)
       const int64_t i = row0 + threadIdx.x;
       if (i < op.n) {
         A acc[NRHS];
-        if constexpr (IsFF<TW, TV>::value)
-          gather_tile_ff<K, NRHS>(tile, threadIdx.x, (const float2* const*)s2.v, acc);
-        else
-          gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)s.v, acc);
+        gather_tile<K, NRHS>(tile, threadIdx.x, (const TV* const*)s.v, acc);
         finish_row(i, acc);
       }
     }
@@ -566,10 +474,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < op.n;
          i += (int64_t)gridDim.x * kThreads) {
       A acc[NRHS];
-      if constexpr (IsFF<TW, TV>::value)
-        gather_ff<K, NRHS>(op, i, (const float2* const*)s2.v, acc);
-      else
-        gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
+      gather_rows<K, NRHS>(op, i, (const TV* const*)s.v, acc);
       finish_row(i, acc);
     }
   }
@@ -679,8 +584,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int NRHS, bool RANK1, typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_p(int64_t n, Vecs<TV, NRHS> r, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, KScal* sc,
-               GridReduce gr, const TV* __restrict__ rdot, Split<NRHS> p2,
-               const float* __restrict__ pcc) {
+               GridReduce gr, const TV* __restrict__ rdot, const float* __restrict__ pcc) {
   using A = TV;
   if (sc->done) return;
   constexpr int NU_ = 1;
@@ -701,7 +605,6 @@ __global__ void __launch_bounds__(kThreads)
       if (!act[q]) continue;
       const A pi = r.v[q][i] + be[q] * (p.v[q][i] - om[q] * v.v[q][i]);
       p.v[q][i] = pi;
-      if (p2.v[0]) p2.v[q][i] = split2((double)pi);
       if (RANK1) psum += pcc ? (A)pcc[i] * pi : (rdot ? rdot[i] * pi : pi);
     }
   }
@@ -795,10 +698,11 @@ __device__ __forceinline__ void prolong_to(const AmgLevel& Fine, int64_t row, fl
 }
 
 // Coarsest level: z = X r with the dense inverse X (one warp per row), then
-// the correction of the next finer level.
+// the correction of the next finer level (has_fine) or the result itself.
+template <typename TZ>
 __global__ void __launch_bounds__(kThreads)
     k_pc_coarse(int64_t nc, const float* __restrict__ X, const float* __restrict__ r,
-                float* __restrict__ z, AmgLevel Fine, int has_fine, const KScal* sc) {
+                TZ* __restrict__ z, AmgLevel Fine, int has_fine, const KScal* sc) {
   if (sc->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -807,24 +711,26 @@ __global__ void __launch_bounds__(kThreads)
     for (int64_t j = lane; j < nc; j += 32) acc += X[row * nc + j] * r[j];
     acc = warp_sum(acc);
     if (lane == 0) {
-      z[row] = acc;
-      if (has_fine) prolong_to(Fine, row, acc);
+      if (has_fine)
+        prolong_to(Fine, row, acc);
+      else
+        z[row] = (TZ)acc;
     }
   }
 }
 
 // One post-smoothing sweep on a level whose x already holds the coarse-grid
 // correction: z = x + omega D^-1 (r - G x).  Levels above 0 then add their
-// correction to the next finer level (PROLONG); level 0 reduces sum(z) into
-// sc->ysum (REDUCE).
-template <bool PROLONG, bool REDUCE>
+// correction to the next finer level (PROLONG; z is not stored); level 0
+// stores z in the solve's precision and reduces its sum (REDUCE).
+template <bool PROLONG, bool REDUCE, typename TZ>
 __global__ void __launch_bounds__(kThreads)
-    k_pc_up(AmgLevel F, AmgLevel Fine, float* __restrict__ z, KScal* sc, GridReduce gr,
+    k_pc_up(AmgLevel F, AmgLevel Fine, TZ* __restrict__ z, KScal* sc, GridReduce gr,
             int which, double inv_ces, double inv_R) {
   if (sc->done) return;
   constexpr int NU_ = 1;
   __shared__ double sh[NU_ * kThreads];
-  double part = 0.0;
+  float part = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < F.n;
        i += (int64_t)gridDim.x * kThreads) {
     const float xi = F.x[i];
@@ -835,12 +741,15 @@ __global__ void __launch_bounds__(kThreads)
       ax += F.val[q * F.ld + i] * F.x[j];
     }
     const float zi = xi + F.wd[i] * (F.r[i] - ax);
-    z[i] = zi;
-    if (PROLONG) prolong_to(Fine, i, zi);
-    if (REDUCE) part += (double)zi;
+    if (PROLONG) {
+      prolong_to(Fine, i, zi);
+    } else {
+      z[i] = (TZ)zi;
+      if (REDUCE) part += zi;
+    }
   }
   if (REDUCE) {
-    double v[NU_] = {part};
+    double v[NU_] = {(double)part};
     grid_reduce<NU_>(v, gr, sh, [&](double* t) { pc_finish(sc, which, t[0], inv_ces, inv_R); });
   }
 }
@@ -851,15 +760,14 @@ __global__ void k_pc_fin1(KScal* sc, int which, double inv_ces, double inv_R) {
   pc_finish(sc, which, 0.0, inv_ces, inv_R);
 }
 
-// sum_s w[s][i] z[idx[s][i]] for a float vector z: FP64 sums for FP64
-// weights; float-float sums of exact products for FP32 weights in an FP64
-// solve; FP32 sums in an FP32 solve.
+// sum_s w[s][i] z[idx[s][i]]: FP64 sums in an FP64 solve, FP32 sums in an
+// FP32 solve.
 template <typename TW, typename TV>
 struct ZAcc;
 template <>
 struct ZAcc<double, double> {
   double a = 0.0;
-  __device__ __forceinline__ void add(double w, float z) { a += w * (double)z; }
+  __device__ __forceinline__ void add(double w, double z) { a += w * z; }
   __device__ __forceinline__ double get() const { return a; }
 };
 template <>
@@ -867,18 +775,6 @@ struct ZAcc<float, float> {  // FP32 inner solves: plain FP32 sums
   float a = 0.f;
   __device__ __forceinline__ void add(float w, float z) { a = fmaf(w, z, a); }
   __device__ __forceinline__ float get() const { return a; }
-};
-template <>
-struct ZAcc<float, double> {
-  float h = 0.f, l = 0.f;
-  __device__ __forceinline__ void add(float w, float z) {
-    float p, e, u, ue;
-    two_prod(w, z, p, e);
-    two_sum(h, p, u, ue);
-    h = u;
-    l += ue + e;
-  }
-  __device__ __forceinline__ double get() const { return (double)h + (double)l; }
 };
 
 // Preconditioned-solve SpMVs with the operand B v = z + kap (pressure, one
@@ -888,7 +784,7 @@ struct ZAcc<float, double> {
 // (t, s), (t, t) -> omega.
 template <int K, typename TW, typename TV, int WHICH>
 __global__ void __launch_bounds__(kThreads)
-    k_spmv_pc(KOp<TW, TV> op, const float* __restrict__ z, TV* __restrict__ y,
+    k_spmv_pc(KOp<TW, TV> op, const TV* __restrict__ z, TV* __restrict__ y,
               const TV* __restrict__ dotv, KScal* sc, GridReduce gr) {
   if (sc->done) return;
   constexpr int NU_ = 2;
@@ -961,7 +857,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_update_xr_pc(int64_t n, TV* __restrict__ x, TV* __restrict__ r, const TV* __restrict__ rh,
-                   const float* __restrict__ zp, const float* __restrict__ zs,
+                   const TV* __restrict__ zp, const TV* __restrict__ zs,
                    const TV* __restrict__ s, const TV* __restrict__ t, KScal* sc, GridReduce gr) {
   if (sc->done) return;
   constexpr int NU_ = 2;
@@ -1462,8 +1358,6 @@ struct StepPlan {
   float* kw32[7][2] = {};
   float *e32[2] = {}, *r32[2] = {};
   double* r64[2] = {};
-  double *e64[2] = {}, *b64[2] = {};     // FP64 correction and right side of inner solves
-  float2 *p2[2] = {}, *s2[2] = {};       // split copies gathered by FP32-weight SpMVs
   KScal* sc = nullptr;
   double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
   struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
@@ -1647,10 +1541,6 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       TRY(palloc(ctx, p, &p->e32[b], nmax));
       TRY(palloc(ctx, p, &p->r32[b], nmax));
       TRY(palloc(ctx, p, &p->r64[b], nmax));
-      TRY(palloc(ctx, p, &p->e64[b], nmax));
-      TRY(palloc(ctx, p, &p->b64[b], nmax));
-      TRY(palloc(ctx, p, &p->p2[b], nmax));
-      TRY(palloc(ctx, p, &p->s2[b], nmax));
     }
   }
 #undef TRY
@@ -1678,10 +1568,22 @@ void collect_events(StepPlan* P) {
   P->ev_used = 0;
 }
 
+// The V-cycle results of p (which 0) and s (which 1) in the solve's precision.
+template <typename TV>
+TV* zbuf(const Amg* a, int which);
+template <>
+float* zbuf<float>(const Amg* a, int which) {
+  return which ? a->zs : a->zp;
+}
+template <>
+double* zbuf<double>(const Amg* a, int which) {
+  return which ? a->zsd : a->zpd;
+}
+
 // B v = zout + kap[which] (one application of the multigrid preconditioner,
 // 2 nlev launches)
 template <typename TV>
-void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, float* zout, cudaStream_t st) {
+void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStream_t st) {
   const int G = P->grid;
   auto grid_for = [&](int64_t rows) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(G, (rows + kThreads - 1) / kThreads));
@@ -1693,13 +1595,13 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, float* zout, cuda
         a->lev[l], a->lev[l + 1].n, a->lev[l + 1].r, P->sc);
   const AmgLevel& C = a->lev[a->nlev - 1];
   const AmgLevel& Cf = a->lev[a->nlev >= 2 ? a->nlev - 2 : 0];
-  k_pc_coarse<<<grid_for(a->nc * 32), kThreads, 0, st>>>(
-      a->nc, a->Xc, C.r, a->nlev >= 2 ? C.z : zout, Cf, a->nlev >= 2 ? 1 : 0, P->sc);
+  k_pc_coarse<TV><<<grid_for(a->nc * 32), kThreads, 0, st>>>(a->nc, a->Xc, C.r, zout, Cf,
+                                                             a->nlev >= 2 ? 1 : 0, P->sc);
   for (int l = a->nlev - 2; l >= 1; --l)
-    k_pc_up<true, false><<<grid_for(a->lev[l].n), kThreads, 0, st>>>(
+    k_pc_up<true, false, float><<<grid_for(a->lev[l].n), kThreads, 0, st>>>(
         a->lev[l], a->lev[l - 1], a->lev[l].z, P->sc, P->gr, which, 0.0, 0.0);
   if (a->nlev >= 2)
-    k_pc_up<false, true><<<G, kThreads, 0, st>>>(a->lev[0], a->lev[0], zout, P->sc, P->gr, which,
+    k_pc_up<false, true, TV><<<G, kThreads, 0, st>>>(a->lev[0], a->lev[0], zout, P->sc, P->gr, which,
                                                  a->inv_ces, a->inv_R);
   else
     k_pc_fin1<<<1, 1, 0, st>>>(P->sc, which, a->inv_ces, a->inv_R);
@@ -1748,14 +1650,8 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
              cudaStream_t st, bool prof = false, uint32_t seed_base = 0,
-             float2* const* p2s = nullptr, float2* const* s2s = nullptr,
              const Amg* pc = nullptr, bool x_zero = false) {
   Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
-  Split<NRHS> P2, S2, none{};
-  for (int q = 0; q < NRHS; ++q) {
-    P2.v[q] = p2s ? p2s[q] : nullptr;
-    S2.v[q] = s2s ? s2s[q] : nullptr;
-  }
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
     B.v[q] = (TV*)b[q];
@@ -1827,9 +1723,9 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
                                                     (restart || seed_base)
                                                         ? 0x51ED27u + 977u * seed_base + restart
                                                         : 0u,
-                                                    pc ? none : P2, pcc, xz ? 1 : 0);
+                                                    pcc, xz ? 1 : 0);
     P->launches += (RANK1 && !xz ? 2 : 1) + (pc ? vc_launches : 0);
-    if (pc) vcycle<TV>(P, pc, PP.v[0], 0, pc->zp, st);
+    if (pc) vcycle<TV>(P, pc, PP.v[0], 0, zbuf<TV>(pc, 0), st);
     int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
     if (rc) return rc;
     int issued = 0, chunk = 4, prev_iters = 0;
@@ -1865,35 +1761,36 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
           if (pc) {  // right-preconditioned: the SpMVs act on B p = zp + kap, B s = zs + kap
             if constexpr (NRHS == 1 && RANK1) {
               if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-              k_spmv_pc<K, TW, TV, 0><<<Gs, kThreads, smem, s>>>(op, pc->zp, V.v[0], RH.v[0],
+              k_spmv_pc<K, TW, TV, 0><<<Gs, kThreads, smem, s>>>(op, zbuf<TV>(pc, 0), V.v[0], RH.v[0],
                                                                    P->sc, P->gr);
               if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
               k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
-                                                             none, pcc);
-              vcycle<TV>(P, pc, S.v[0], 1, pc->zs, s);
+                                                             pcc);
+              vcycle<TV>(P, pc, S.v[0], 1, zbuf<TV>(pc, 1), s);
               if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-              k_spmv_pc<K, TW, TV, 1><<<Gs, kThreads, smem, s>>>(op, pc->zs, T.v[0], S.v[0],
+              k_spmv_pc<K, TW, TV, 1><<<Gs, kThreads, smem, s>>>(op, zbuf<TV>(pc, 1), T.v[0], S.v[0],
                                                                    P->sc, P->gr);
               if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-              k_update_xr_pc<TV><<<G, kThreads, 0, s>>>(op.n, X.v[0], R.v[0], RH.v[0], pc->zp,
-                                                        pc->zs, S.v[0], T.v[0], P->sc, P->gr);
+              k_update_xr_pc<TV><<<G, kThreads, 0, s>>>(op.n, X.v[0], R.v[0], RH.v[0],
+                                                        zbuf<TV>(pc, 0), zbuf<TV>(pc, 1), S.v[0],
+                                                        T.v[0], P->sc, P->gr);
               k_update_p<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
-                                                             none, pcc);
-              vcycle<TV>(P, pc, PP.v[0], 0, pc->zp, s);
+                                                             pcc);
+              vcycle<TV>(P, pc, PP.v[0], 0, zbuf<TV>(pc, 0), s);
             }
             continue;
           }
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PP, V, RH, P->sc, P->gr, P2);
+          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PP, V, RH, P->sc, P->gr);
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
           k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
-                                                         S2, pcc);
+                                                         pcc);
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
-          k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, S, S, T, P->sc, P->gr, S2);
+          k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, S, S, T, P->sc, P->gr);
           if (prof) cudaEventRecord(P->ev[P->ev_used++], s);
           k_update_xr<NRHS><<<G, kThreads, 0, s>>>(op.n, X, R, RH, PP, S, S, T, P->sc, P->gr);
           k_update_p<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
-                                                         P2, pcc);
+                                                         pcc);
         }
       };
       if (prof) {
@@ -1901,7 +1798,7 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       } else {
         const void* const key[10] = {(const void*)&bicgstab<K, NRHS, RANK1, TW, TV>,
                                      op.idx, op.w, op.es, X.v[0], X.v[NRHS - 1], pc,
-                                     P2.v[0], S2.v[0], work[0][0]};
+                                     work[0][0], nullptr, nullptr};
         for (int part = 64; part >= 1; part >>= 1) {  // n as a sum of powers of two
           if (!(n & part)) continue;
           cudaGraphExec_t g = nullptr;
@@ -1955,30 +1852,6 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
 // loose relative tolerance, from the normalised residual.  A correction that
 // does not lower the FP64 residual is undone and the inner solve repeated with
 // another shadow residual.
-template <int NRHS>
-__global__ void k_scale_zero(int64_t n, Vecs<double, NRHS> r, Vecs<double, NRHS> b,
-                             Vecs<double, NRHS> e, double inv0, double inv1) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    b.v[0][i] = r.v[0][i] * inv0;
-    e.v[0][i] = 0.0;
-    if (NRHS > 1) {
-      b.v[NRHS - 1][i] = r.v[NRHS - 1][i] * inv1;
-      e.v[NRHS - 1][i] = 0.0;
-    }
-  }
-}
-
-template <int NRHS>
-__global__ void k_addcorr64(int64_t n, Vecs<double, NRHS> x, Vecs<double, NRHS> e, double n0,
-                            double n1) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x.v[0][i] += n0 * e.v[0][i];
-    if (NRHS > 1) x.v[NRHS - 1][i] += n1 * e.v[NRHS - 1][i];
-  }
-}
-
 template <int K, int NRHS, bool RANK1>
 int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
            const KOp<float, float>& op32, double* const* x, const double* const* b, double tol,
@@ -2054,8 +1927,8 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     P->launches += 2;  // with the correction below
     SolveResult inner;
     rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
-                                                maxit - used, &inner, st, prof, retries, nullptr,
-                                                nullptr, RANK1 ? P->amg : nullptr, true);
+                                                maxit - used, &inner, st, prof, retries,
+                                                RANK1 ? P->amg : nullptr, true);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
@@ -2157,7 +2030,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                               &sweeps, st, prof);
     else
       rc = bicgstab<K, 1, true, double, double>(ctx, P, L64, px, pbv, P->kw64, f.tol, f.max_iter,
-                                                &pr, st, prof, 0, nullptr, nullptr, P->amg);
+                                                &pr, st, prof, 0, P->amg);
     if (rc) return rc;
     if (stats) {
       stats->poisson_iters += pr.iters;
