@@ -51,6 +51,26 @@ def parse():
 
 
 # ----------------------------------------------------------------- helpers
+def replica_seed(rank: int) -> int:
+    """Seed of the cavity a rank simulates: replicas of the workload, one per GPU."""
+    return 2 + rank
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps: int, world: int, ms_max: float) -> float:
+    """Steps per second of the whole job: every rank's steps over the slowest rank's time."""
+    return steps * world / (ms_max * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -203,7 +223,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     ctx = R.Context(28, 7, 3)
-    nd = ns.jittered_cavity(args.n, 2 + rank)
+    nd = ns.jittered_cavity(args.n, replica_seed(rank))
     t_setup = time.time()
     flows = {}
     for name, prec in (("mixed", R.PREC_MIXED), ("fp64", R.PREC_FP64)):
@@ -262,11 +282,7 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         windows.append((w0, time.time()))
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
         res[name] = {"ms": ms, "agg": agg, "relres": s["poisson_relres"]}
         # per-launch CUDA events around every pressure-solve SpMV need eager
         # launches (the timed steps replay CUDA graphs): one more step, profiled
@@ -294,11 +310,7 @@ def run_ours(args):
             v_p.copy_(st.v, non_blocking=True)
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1), world)
         res[name]["e2e_ms"] = ems
     if sampler:
         sampler.stop()
@@ -359,9 +371,8 @@ def run_ours(args):
         return {"metric": METRIC, "value": None, "unit": UNIT, "error": failed}
     head = "mixed" if "mixed" in res else "fp64"
     r = res[head]
-    steps_total = args.steps * world
-    value = steps_total / (r["ms"] * 1e-3)
-    e2e = steps_total / (r["e2e_ms"] * 1e-3)
+    value = whole_job_rate(args.steps, world, r["ms"])
+    e2e = whole_job_rate(args.steps, world, r["e2e_ms"])
     agg = r["agg"]
     # roofline of the pressure solve's SpMV (k_spmv_pc): per row the stencil's
     # k column indices and k weights, the operand z (read once), the output,

@@ -652,10 +652,30 @@ __global__ void __launch_bounds__(kThreads)
     r0[i] = c[i] * (float)v[i] - mu * ce[i];
 }
 
+// sum_s G_off[i][s] * get(column) over a level's off-diagonal row.  W > 0:
+// the loop is unrolled to W predicated slots so that every load of the row is
+// in flight at once (the level's width is at most W); W = 0: a plain loop.
+template <int W, typename Get>
+__device__ __forceinline__ float graph_row(const AmgLevel& F, int64_t i, Get get) {
+  float ax = 0.f;
+  if constexpr (W > 0) {
+#pragma unroll
+    for (int s = 0; s < W; ++s)
+      if (s < F.width) ax += F.val[s * F.ld + i] * get(F.idx[s * F.ld + i]);
+  } else {
+    for (int s = 0; s < F.width; ++s) ax += F.val[s * F.ld + i] * get(F.idx[s * F.ld + i]);
+  }
+  return ax;
+}
+
+// the unrolled width for a level: 8, 16 or 32 slots, or 0 (plain loop)
+inline int width_bucket(int w) { return w <= 8 ? 8 : w <= 16 ? 16 : w <= 32 ? 32 : 0; }
+
 // Pre-smoothing from zero (x = omega D^-1 r) and restriction of its residual:
 // rc[I] = sum over the rows i of aggregate I of (r - G x)_i.  Four lanes per
 // aggregate, one per row (aggregates hold at most four rows), summed by a
 // fixed shuffle tree; neighbours' x values are formed from their r on the fly.
+template <int W>
 __global__ void __launch_bounds__(kThreads)
     k_pc_restrict(AmgLevel F, int64_t nc, float* __restrict__ rc, const KScal* sc) {
   if (sc->done) return;
@@ -672,12 +692,8 @@ __global__ void __launch_bounds__(kThreads)
       const float ri = F.r[i];
       const float xi = F.wd[i] * ri;
       F.x[i] = xi;
-      float ax = F.diag[i] * xi;
-#pragma unroll 4
-      for (int s = 0; s < F.width; ++s) {
-        const int32_t j = F.idx[s * F.ld + i];
-        ax += F.val[s * F.ld + i] * (F.wd[j] * F.r[j]);
-      }
+      const float ax =
+          F.diag[i] * xi + graph_row<W>(F, i, [&](int32_t j) { return F.wd[j] * F.r[j]; });
       res = ri - ax;
     }
     res += __shfl_xor_sync(0xffffffffu, res, 1);
@@ -708,6 +724,7 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
   for (int64_t row = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; row < nc; row += nw) {
     float acc = 0.f;
+#pragma unroll 8
     for (int64_t j = lane; j < nc; j += 32) acc += X[row * nc + j] * r[j];
     acc = warp_sum(acc);
     if (lane == 0) {
@@ -723,7 +740,7 @@ __global__ void __launch_bounds__(kThreads)
 // correction: z = x + omega D^-1 (r - G x).  Levels above 0 then add their
 // correction to the next finer level (PROLONG; z is not stored); level 0
 // stores z in the solve's precision and reduces its sum (REDUCE).
-template <bool PROLONG, bool REDUCE, typename TZ>
+template <bool PROLONG, bool REDUCE, typename TZ, int W>
 __global__ void __launch_bounds__(kThreads)
     k_pc_up(AmgLevel F, AmgLevel Fine, TZ* __restrict__ z, KScal* sc, GridReduce gr,
             int which, double inv_ces, double inv_R) {
@@ -734,12 +751,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < F.n;
        i += (int64_t)gridDim.x * kThreads) {
     const float xi = F.x[i];
-    float ax = F.diag[i] * xi;
-#pragma unroll 4
-    for (int q = 0; q < F.width; ++q) {
-      const int32_t j = F.idx[q * F.ld + i];
-      ax += F.val[q * F.ld + i] * F.x[j];
-    }
+    const float ax = F.diag[i] * xi + graph_row<W>(F, i, [&](int32_t j) { return F.x[j]; });
     const float zi = xi + F.wd[i] * (F.r[i] - ax);
     if (PROLONG) {
       prolong_to(Fine, i, zi);
@@ -1590,19 +1602,47 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
   };
   const int64_t n = a->lev[0].n;
   k_pc_in<TV><<<G, kThreads, 0, st>>>(n, v, a->c, a->ce, which, a->inv_ces, P->sc, a->lev[0].r);
-  for (int l = 0; l + 1 < a->nlev; ++l)
-    k_pc_restrict<<<grid_for(a->lev[l + 1].n * 4), kThreads, 0, st>>>(
-        a->lev[l], a->lev[l + 1].n, a->lev[l + 1].r, P->sc);
+  for (int l = 0; l + 1 < a->nlev; ++l) {
+    const AmgLevel& F = a->lev[l];
+    const int gb = grid_for(a->lev[l + 1].n * 4);
+    switch (width_bucket(F.width)) {
+      case 8: k_pc_restrict<8><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
+      case 16: k_pc_restrict<16><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
+      case 32: k_pc_restrict<32><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
+      default: k_pc_restrict<0><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc);
+    }
+  }
   const AmgLevel& C = a->lev[a->nlev - 1];
   const AmgLevel& Cf = a->lev[a->nlev >= 2 ? a->nlev - 2 : 0];
   k_pc_coarse<TV><<<grid_for(a->nc * 32), kThreads, 0, st>>>(a->nc, a->Xc, C.r, zout, Cf,
                                                              a->nlev >= 2 ? 1 : 0, P->sc);
-  for (int l = a->nlev - 2; l >= 1; --l)
-    k_pc_up<true, false, float><<<grid_for(a->lev[l].n), kThreads, 0, st>>>(
-        a->lev[l], a->lev[l - 1], a->lev[l].z, P->sc, P->gr, which, 0.0, 0.0);
-  if (a->nlev >= 2)
-    k_pc_up<false, true, TV><<<G, kThreads, 0, st>>>(a->lev[0], a->lev[0], zout, P->sc, P->gr, which,
-                                                 a->inv_ces, a->inv_R);
+  for (int l = a->nlev - 2; l >= 1; --l) {
+    const AmgLevel& F = a->lev[l];
+    const int gb = grid_for(F.n);
+#define RBFFD_UP(Wb)                                                                         \
+  k_pc_up<true, false, float, Wb><<<gb, kThreads, 0, st>>>(F, a->lev[l - 1], F.z, P->sc, P->gr, \
+                                                           which, 0.0, 0.0)
+    switch (width_bucket(F.width)) {
+      case 8: RBFFD_UP(8); break;
+      case 16: RBFFD_UP(16); break;
+      case 32: RBFFD_UP(32); break;
+      default: RBFFD_UP(0);
+    }
+#undef RBFFD_UP
+  }
+  if (a->nlev >= 2) {
+    const AmgLevel& F = a->lev[0];
+#define RBFFD_UP0(Wb)                                                                      \
+  k_pc_up<false, true, TV, Wb><<<G, kThreads, 0, st>>>(F, F, zout, P->sc, P->gr, which, \
+                                                       a->inv_ces, a->inv_R)
+    switch (width_bucket(F.width)) {
+      case 8: RBFFD_UP0(8); break;
+      case 16: RBFFD_UP0(16); break;
+      case 32: RBFFD_UP0(32); break;
+      default: RBFFD_UP0(0);
+    }
+#undef RBFFD_UP0
+  }
   else
     k_pc_fin1<<<1, 1, 0, st>>>(P->sc, which, a->inv_ces, a->inv_R);
 }
