@@ -340,8 +340,10 @@ def run_ours(args):
         wb = 8 if wname == "fp64" else 4
         bytes_row = k * 4 + k * wb + 2 * wb  # idx, weights, y written, x read once
         gbs = nd.N * bytes_row / per / 1e9
+        thr, bps = R.apply_op_shape(ctx, idx, w, nd.N, nd.N, x.dtype)
         spmv[wname] = {"rows": nd.N, "bytes_per_row": bytes_row, "us": per * 1e6,
-                       "achieved_gbs": gbs, "frac": gbs / hbm}
+                       "achieved_gbs": gbs, "frac": gbs / hbm,
+                       "launch": {"threads": thr, "blocks_per_sm": bps, "picked_by": "autotuner"}}
 
     # batched weight build: V->V stencils (3 operators) of this node set, and the
     # measured FP64 FMA peak it is held against

@@ -165,10 +165,25 @@ typedef struct rbffd_ell {
  * approximates L f(x^alpha)).  x has n_cols entries and y n_rows, both of
  * xy_dtype (RBFFD_F64 or RBFFD_F32).  With beta == 0, y is not read.
  * Accumulation is in FP64 for FP64 weights and in FP32 for FP32 weights.
- * Asynchronous.  Errors: INVALID_ARG, CUDA.
+ * Asynchronous, except that the first call for an operator shape (rows
+ * rounded to a power of two, stencil size, weight and vector types) in a
+ * context autotunes the launch shape: it times each candidate block size and
+ * grid on this operator into context scratch (synchronising `stream`; skipped
+ * while the stream is being captured) and keeps the fastest.  Every shape
+ * adds a row's terms in the same order, so results do not depend on the
+ * choice.  Errors: INVALID_ARG, CUDA.
  */
 int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
                    double beta, int32_t xy_dtype, cudaStream_t stream);
+
+/*
+ * rbffd_apply_op_shape - the launch shape rbffd_apply_op uses for this
+ * operator shape in this context (threads per block, blocks per SM): the
+ * autotuner's choice once a call has tuned it, the default before.  HOST
+ * outputs.  Errors: INVALID_ARG.
+ */
+int rbffd_apply_op_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, int32_t* threads,
+                         int32_t* blocks_per_sm);
 
 /*
  * Staggered flow problem (Section 3).  Every operator is FP64 ELL with the

@@ -178,6 +178,18 @@ int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, d
   return spmv_apply(ctx, D, x, y, alpha, beta, xy_dtype, stream);
 }
 
+int rbffd_apply_op_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, int32_t* threads,
+                         int32_t* blocks_per_sm) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!D || !threads || !blocks_per_sm) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  int t = 0, b = 0;
+  const int rc = spmv_shape(ctx, D, xy_dtype, &t, &b);
+  *threads = t;
+  *blocks_per_sm = b;
+  return rc;
+}
+
 static int check_flow(rbffd_ctx* ctx, const rbffd_flow* flow) {
   if (!flow) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null flow");
   const rbffd_flow& f = *flow;

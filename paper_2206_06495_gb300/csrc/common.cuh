@@ -7,6 +7,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "rbffd.h"
 
@@ -103,6 +105,8 @@ struct rbffd_ctx {
   size_t scratch_bytes = 0;
   void* host_pinned = nullptr;  // small pinned buffer for status words
   rbffd::StepPlan* plan = nullptr;
+  // launch shapes the SpMV autotuner picked, per operator shape key
+  std::vector<std::pair<uint64_t, int>> spmv_shapes;
 };
 
 namespace rbffd {
@@ -123,6 +127,8 @@ int weights_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na
                   int64_t* bad_node, cudaStream_t st);
 int spmv_apply(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
                double beta, int32_t xy_dtype, cudaStream_t st);
+int spmv_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, int* threads,
+               int* blocks_per_sm);
 int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st);
 void step_plan_free(struct StepPlan* p);

@@ -1793,7 +1793,9 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       prev_rel = rel;
       prev_iters = h->iters;
       n = std::min(n, budget - issued);
-      if (prof) n = std::min(n, StepPlan::kEv / 4);
+      // profiled solves: one iteration per chunk, so no timed launch is one
+      // that returned at once after convergence
+      if (prof) n = 1;
       // one chunk of iterations; every kernel returns at once after the solve
       // has finished (sc->done), so a chunk may overshoot harmlessly
       auto issue = [&](cudaStream_t s, int cnt) {

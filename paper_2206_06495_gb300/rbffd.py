@@ -114,6 +114,8 @@ PROTOTYPES = {
                                   C.c_void_p]),
     "rbffd_apply_op": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
+    "rbffd_apply_op_shape": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_int32,
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "rbffd_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC), C.c_void_p,
                              C.c_void_p, C.c_int32, C.POINTER(Stats), C.c_void_p]),
     "rbffd_adjoint_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC),
@@ -247,6 +249,18 @@ def apply_op(ctx: Context, idx, w, n_rows: int, n_cols: int, x, y=None, alpha: f
     ctx.check(lib().rbffd_apply_op(ctx.handle, C.byref(D), _ptr(x), _ptr(y), alpha, beta, xy,
                                    _stream()))
     return y
+
+
+def apply_op_shape(ctx: Context, idx, w, n_rows: int, n_cols: int, x_dtype) -> tuple[int, int]:
+    """rbffd_apply_op_shape: (threads per block, blocks per SM) of the SpMV launch."""
+    torch = _torch()
+    D = Ell(idx=_ptr(idx).value, w=_ptr(w).value, n_rows=n_rows, n_cols=n_cols,
+            ld=idx.shape[1], n=idx.shape[0], w_dtype=F64 if w.dtype == torch.float64 else F32)
+    t, b = C.c_int32(0), C.c_int32(0)
+    ctx.check(lib().rbffd_apply_op_shape(ctx.handle, C.byref(D),
+                                         F64 if x_dtype == torch.float64 else F32,
+                                         C.byref(t), C.byref(b)))
+    return t.value, b.value
 
 
 @dataclass

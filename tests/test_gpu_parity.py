@@ -196,3 +196,22 @@ def test_step_config0_500_steps(R, ctx, precision, tol):
     du = np.abs(st.u.cpu().numpy() - s.u).max()
     dv = np.abs(st.v.cpu().numpy() - s.v).max()
     assert du < tol and dv < tol, (du, dv, stats)
+
+
+def test_apply_op_autotuned_shape_is_a_candidate_and_result_independent(R):
+    """rbffd_apply_op picks its launch shape by timing candidates on first use;
+    every shape adds each row's terms in the same order, so two contexts (which
+    may pick different shapes) return identical bits."""
+    nd = ns.jittered_cavity(60, 7)
+    outs = []
+    for _ in range(2):
+        ctx = R.Context(28, 7, 3)
+        idx, w, _ = R.build_weights(ctx, _d(nd.vx), _d(nd.vy), _d(nd.vx), _d(nd.vy), R.OP_LAP)
+        f, *_ = ns.wave_test_function(nd.vx, nd.vy)
+        for wdt, x in ((w[0], _d(f)), (w[0].float(), _d(f).float())):
+            y = R.apply_op(ctx, idx, wdt, nd.N, nd.N, x)
+            t, b = R.apply_op_shape(ctx, idx, wdt, nd.N, nd.N, x.dtype)
+            assert (t, b) in {(128, 4), (128, 8), (128, 16), (256, 2), (256, 4), (256, 8),
+                              (512, 2), (512, 4)}
+            outs.append(y.cpu().numpy())
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
