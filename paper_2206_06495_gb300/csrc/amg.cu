@@ -168,6 +168,30 @@ void galerkin(const HostCsr& A, const std::vector<int32_t>& agg, int32_t nc, Hos
   }
 }
 
+// B[p][q] = A[old[p]][old[q]] (newidx = inverse of old); columns sorted again.
+void permute(const HostCsr& A, const std::vector<int32_t>& old, const std::vector<int32_t>& newidx,
+             HostCsr* B) {
+  B->n = A.n;
+  B->ptr.assign(A.n + 1, 0);
+  B->col.clear();
+  B->val.clear();
+  B->diag.assign(A.n, 0.0);
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t p = 0; p < A.n; ++p) {
+    const int32_t i = old[p];
+    row.clear();
+    for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) row.emplace_back(newidx[A.col[k]], A.val[k]);
+    std::sort(row.begin(), row.end(),
+              [](const auto& u, const auto& v) { return u.first < v.first; });
+    for (auto& rv : row) {
+      B->col.push_back(rv.first);
+      B->val.push_back(rv.second);
+    }
+    B->diag[p] = A.diag[i];
+    B->ptr[p + 1] = (int64_t)B->col.size();
+  }
+}
+
 // Dense inverse of (A + sigma 1 1^T + eps diag(A)) by Cholesky, row-major.
 // sigma lifts the constant null vector of the Laplacian to the mean diagonal;
 // eps = 1e-10 keeps the factorisation defined if the graph falls apart.
@@ -293,6 +317,43 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
   if (!coarse_inverse(L.back(), &Xd))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "coarsest pressure graph matrix is not positive");
 
+  // Nested ordering, coarsest to finest: the coarsest level keeps its order,
+  // and each finer level lists its rows aggregate by aggregate in the coarser
+  // level's order (rows of one aggregate in their previous order).  Every
+  // aggregate's rows are then contiguous (children of coarse row I are rows
+  // cptr[I] .. cptr[I+1]-1), so restriction and prolongation touch
+  // consecutive rows.
+  const int nl = (int)L.size();
+  std::vector<std::vector<int32_t>> oldi(nl), newi(nl), cptrs(nl);
+  oldi[nl - 1].resize(L[nl - 1].n);
+  newi[nl - 1].resize(L[nl - 1].n);
+  for (int64_t i = 0; i < L[nl - 1].n; ++i) oldi[nl - 1][i] = newi[nl - 1][i] = (int32_t)i;
+  for (int l = nl - 2; l >= 0; --l) {
+    const int64_t n = L[l].n;
+    const int64_t nc = L[l + 1].n;
+    std::vector<int64_t> cnt(nc + 1, 0);
+    for (int64_t i = 0; i < n; ++i) ++cnt[newi[l + 1][aggs[l][i]] + 1];
+    for (int64_t I = 0; I < nc; ++I) cnt[I + 1] += cnt[I];
+    std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
+    oldi[l].resize(n);
+    newi[l].resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t p = cur[newi[l + 1][aggs[l][i]]]++;
+      oldi[l][p] = (int32_t)i;
+      newi[l][i] = (int32_t)p;
+    }
+    cptrs[l].assign(cnt.begin(), cnt.end());
+    int cw = 0;
+    for (int64_t I = 0; I < nc; ++I) cw = std::max<int>(cw, (int)(cnt[I + 1] - cnt[I]));
+    if (cw > 4)  // two pairwise passes make aggregates of at most four rows
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid aggregate of %d rows", cw);
+  }
+  for (int l = 0; l < nl - 1; ++l) {
+    HostCsr B;
+    permute(L[l], oldi[l], newi[l], &B);
+    L[l] = std::move(B);
+  }
+
   Amg* a = new Amg();
   auto fail = [&](int code) {
     amg_free(a);
@@ -324,36 +385,29 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
       hd[i] = (float)A.diag[i];
       hwd[i] = A.diag[i] > 0.0 ? (float)(kAmgOmega / A.diag[i]) : 0.f;
     }
-    std::vector<int64_t> cptr;
-    std::vector<int32_t> cidx;
-    const int32_t nc = (int32_t)L[l + 1].n;
-    children(aggs[l], nc, &cptr, &cidx);
-    int cw = 1;
-    for (int32_t I = 0; I < nc; ++I) cw = std::max<int>(cw, (int)(cptr[I + 1] - cptr[I]));
-    if (cw > 4)  // two pairwise passes make aggregates of at most four rows
-      return fail(set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid aggregate of %d rows", cw));
-    g.cw = cw;
-    g.ld_c = round_up(nc, 32);
-    std::vector<int32_t> hch((size_t)cw * g.ld_c, -1);
-    for (int32_t I = 0; I < nc; ++I)
-      for (int64_t c = cptr[I]; c < cptr[I + 1]; ++c) hch[(c - cptr[I]) * g.ld_c + I] = cidx[c];
     if ((rc = upload(ctx, a, hidx, &g.idx, st)) || (rc = upload(ctx, a, hval, &g.val, st)) ||
         (rc = upload(ctx, a, hd, &g.diag, st)) || (rc = upload(ctx, a, hwd, &g.wd, st)) ||
-        (rc = upload(ctx, a, aggs[l], &g.agg, st)) || (rc = upload(ctx, a, hch, &g.ch, st)))
+        (rc = upload(ctx, a, cptrs[l], &g.cptr, st)))
       return fail(rc);
   }
   a->nc = L.back().n;
   std::vector<float> hX(Xd.begin(), Xd.end());
   if ((rc = upload(ctx, a, hX, &a->Xc, st))) return fail(rc);
   // level-0 scaling: the scaled pressure rows approximate rows of G divided by diag(G)
+  // (stored in the level-0 order: entry p belongs to P-node oldi[0][p])
   std::vector<float> hc(M), hce(M);
   double ces = 0.0;
-  for (int64_t i = 0; i < M; ++i) {
-    const double ci = diag_a[i] != 0.0 ? L[0].diag[i] / diag_a[i] : L[0].diag[i];
-    hc[i] = (float)ci;
-    hce[i] = (float)(ci * es[i]);
-    ces += ci * es[i];
+  for (int64_t p = 0; p < M; ++p) {
+    const int32_t i = oldi[0][p];
+    const double ci = diag_a[i] != 0.0 ? L[0].diag[p] / diag_a[i] : L[0].diag[p];
+    hc[p] = (float)ci;
+    hce[p] = (float)(ci * es[i]);
   }
+  for (int64_t i = 0; i < M; ++i) {  // in P-node order, like the scalar it normalises
+    const int32_t p = newi[0][i];
+    ces += (diag_a[i] != 0.0 ? L[0].diag[p] / diag_a[i] : L[0].diag[p]) * es[i];
+  }
+  if ((rc = upload(ctx, a, oldi[0], &a->perm0, st))) return fail(rc);
   if (!(ces != 0.0) || !std::isfinite(ces)) return fail(set_error(ctx, RBFFD_ERR_INVALID_ARG,
                                                                   "pressure rank-one column is zero"));
   a->inv_ces = 1.0 / ces;

@@ -15,10 +15,11 @@
 // G: edge weight 1/|x_a - x_b|^2; an edge between two boundary P-nodes is left
 // out (boundary rows of the pressure system are one-sided Neumann rows on
 // interior nodes) unless one of its ends has no other edge to an interior node.
-// Hierarchy: two passes of pairwise matching by strongest coupling per level
-// (aggregates of up to 4 nodes), Galerkin coarse matrices P^T G P with
-// piecewise-constant P, down to at most kAmgCoarse nodes, where the dense
-// inverse of (G_c + sigma 1 1^T) is applied.  Smoother: one damped Jacobi
+// Hierarchy: two passes of pairwise matching by strongest normalised coupling
+// per level (aggregates of up to 4 nodes), Galerkin coarse matrices P^T G P
+// with piecewise-constant P, down to at most kAmgCoarse nodes, where the dense
+// inverse of (G_c + sigma 1 1^T) is applied.  Every level is renumbered so that
+// each aggregate's rows are contiguous (level 0 through the permutation perm0).  Smoother: one damped Jacobi
 // sweep before and after the coarse correction, which is scaled by
 // kAmgCoarseScale (the usual over-correction of plain aggregation).
 // The hierarchy is built once per flow description on the host (like a
@@ -47,10 +48,8 @@ struct AmgLevel {
   float* val = nullptr;    // [width][ld] off-diagonal entries (<= 0)
   float* diag = nullptr;   // [n]
   float* wd = nullptr;     // [n] omega / diag
-  int32_t* agg = nullptr;  // [n] row of level l + 1 that row i belongs to
-  int cw = 0;              // most rows in one aggregate
-  int64_t ld_c = 0;        // leading dimension of ch
-  int32_t* ch = nullptr;   // [cw][ld_c] rows of aggregate I (level l + 1 row), -1 padding
+  int32_t* cptr = nullptr;  // [n(l+1) + 1]: rows cptr[I] .. cptr[I+1]-1 form aggregate I
+                            // (row I of level l + 1); at most four rows each
   float* r = nullptr;      // right side at this level
   float* x = nullptr;      // pre-smoothed iterate
   float* z = nullptr;      // level result (after the post-smoothing sweep)
@@ -60,6 +59,7 @@ struct Amg {
   int nlev = 0;
   AmgLevel lev[kAmgMaxLevels];
   float* Xc = nullptr;  // [nc][nc] dense inverse on the coarsest level
+  int32_t* perm0 = nullptr;  // [M] level-0 row p is P-node perm0[p] (the nested order)
   int64_t nc = 0;
   // level-0 map of a residual v of the scaled pressure system: r0 = c v - mu ce,
   // mu = (c . v) / (c . es); the result is z + mu / M (see step.cu)

@@ -639,17 +639,18 @@ __device__ __forceinline__ void pc_finish(KScal* sc, int which, double zsum, dou
     sc->sum_p = mu;
 }
 
-// r0 = c v - mu ce (which = 0: v = p, mu from sc->cp; 1: v = s, from sc->cs)
+// r0 = c v - mu ce in the hierarchy's level-0 order (row p is P-node perm0[p];
+// which = 0: v = p, mu from sc->cp; 1: v = s, from sc->cs)
 template <typename TV>
 __global__ void __launch_bounds__(kThreads)
     k_pc_in(int64_t n, const TV* __restrict__ v, const float* __restrict__ c,
-            const float* __restrict__ ce, int which, double inv_ces, const KScal* sc,
-            float* __restrict__ r0) {
+            const float* __restrict__ ce, const int32_t* __restrict__ perm0, int which,
+            double inv_ces, const KScal* sc, float* __restrict__ r0) {
   if (sc->done) return;
   const float mu = (float)((which ? sc->cs : sc->cp) * inv_ces);
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads)
-    r0[i] = c[i] * (float)v[i] - mu * ce[i];
+    r0[i] = c[i] * (float)v[perm0[i]] - mu * ce[i];
 }
 
 // sum_s G_off[i][s] * get(column) over a level's off-diagonal row.  W > 0:
@@ -672,45 +673,50 @@ __device__ __forceinline__ float graph_row(const AmgLevel& F, int64_t i, Get get
 inline int width_bucket(int w) { return w <= 8 ? 8 : w <= 16 ? 16 : w <= 32 ? 32 : 0; }
 
 // Pre-smoothing from zero (x = omega D^-1 r) and restriction of its residual:
-// rc[I] = sum over the rows i of aggregate I of (r - G x)_i.  Four lanes per
-// aggregate, one per row (aggregates hold at most four rows), summed by a
-// fixed shuffle tree; neighbours' x values are formed from their r on the fly.
+// rc[I] = sum over the rows i of aggregate I of (r - G x)_i.  A block takes 64
+// consecutive aggregates, whose rows are the consecutive rows cptr[I0] ..
+// (at most 256): one thread per row (coalesced), the residuals staged in
+// shared memory and summed per aggregate in row order.  Neighbours' x values
+// are formed from their r on the fly.
+constexpr int kRB = 64;  // aggregates per block (at most 4 rows each)
+
 template <int W>
 __global__ void __launch_bounds__(kThreads)
     k_pc_restrict(AmgLevel F, int64_t nc, float* __restrict__ rc, const KScal* sc) {
   if (sc->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t total = nc * 4;
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  // the loop condition is uniform across a warp (stride is a multiple of 32)
-  for (int64_t t = blockIdx.x * (int64_t)kThreads + threadIdx.x; t - lane < total; t += stride) {
-    const int64_t I = t >> 2;
-    const int q = (int)(t & 3);
-    float res = 0.f;
-    const int32_t i = (t < total && q < F.cw) ? F.ch[q * F.ld_c + I] : -1;
-    if (i >= 0) {
+  __shared__ float res[kThreads];
+  for (int64_t I0 = blockIdx.x * (int64_t)kRB; I0 < nc; I0 += (int64_t)gridDim.x * kRB) {
+    const int64_t I1 = I0 + kRB < nc ? I0 + kRB : nc;
+    const int64_t f0 = F.cptr[I0], f1 = F.cptr[I1];
+    const int64_t i = f0 + threadIdx.x;
+    float rv = 0.f;
+    if (i < f1) {
       const float ri = F.r[i];
       const float xi = F.wd[i] * ri;
       F.x[i] = xi;
       const float ax =
           F.diag[i] * xi + graph_row<W>(F, i, [&](int32_t j) { return F.wd[j] * F.r[j]; });
-      res = ri - ax;
+      rv = ri - ax;
     }
-    res += __shfl_xor_sync(0xffffffffu, res, 1);
-    res += __shfl_xor_sync(0xffffffffu, res, 2);
-    if (q == 0 && t < total) rc[I] = res;
+    res[threadIdx.x] = rv;
+    __syncthreads();
+    if (threadIdx.x < kRB && I0 + threadIdx.x < I1) {
+      const int64_t I = I0 + threadIdx.x;
+      float acc = 0.f;
+      for (int64_t c = F.cptr[I]; c < F.cptr[I + 1]; ++c) acc += res[c - f0];
+      rc[I] = acc;
+    }
+    __syncthreads();
   }
 }
 
 // x_fine[i] += s * z for the rows i of aggregate `row` (the coarse-grid
-// correction of the finer level, written by the coarse level's thread)
+// correction of the finer level, written by the coarse level's thread; the
+// rows are consecutive)
 __device__ __forceinline__ void prolong_to(const AmgLevel& Fine, int64_t row, float z) {
   const float v = kAmgCoarseScale * z;
-  for (int q = 0; q < Fine.cw; ++q) {
-    const int32_t c = Fine.ch[q * Fine.ld_c + row];
-    if (c < 0) break;
-    Fine.x[c] += v;
-  }
+  const int32_t c1 = Fine.cptr[row + 1];
+  for (int32_t c = Fine.cptr[row]; c < c1; ++c) Fine.x[c] += v;
 }
 
 // Coarsest level: z = X r with the dense inverse X (one warp per row), then
@@ -742,8 +748,8 @@ __global__ void __launch_bounds__(kThreads)
 // stores z in the solve's precision and reduces its sum (REDUCE).
 template <bool PROLONG, bool REDUCE, typename TZ, int W>
 __global__ void __launch_bounds__(kThreads)
-    k_pc_up(AmgLevel F, AmgLevel Fine, TZ* __restrict__ z, KScal* sc, GridReduce gr,
-            int which, double inv_ces, double inv_R) {
+    k_pc_up(AmgLevel F, AmgLevel Fine, TZ* __restrict__ z, const int32_t* __restrict__ perm0,
+            KScal* sc, GridReduce gr, int which, double inv_ces, double inv_R) {
   if (sc->done) return;
   constexpr int NU_ = 1;
   __shared__ double sh[NU_ * kThreads];
@@ -756,7 +762,7 @@ __global__ void __launch_bounds__(kThreads)
     if (PROLONG) {
       prolong_to(Fine, i, zi);
     } else {
-      z[i] = (TZ)zi;
+      z[perm0[i]] = (TZ)zi;  // back to P-node order
       if (REDUCE) part += zi;
     }
   }
@@ -1601,10 +1607,12 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
     return (int)std::max<int64_t>(1, std::min<int64_t>(G, (rows + kThreads - 1) / kThreads));
   };
   const int64_t n = a->lev[0].n;
-  k_pc_in<TV><<<G, kThreads, 0, st>>>(n, v, a->c, a->ce, which, a->inv_ces, P->sc, a->lev[0].r);
+  k_pc_in<TV><<<G, kThreads, 0, st>>>(n, v, a->c, a->ce, a->perm0, which, a->inv_ces, P->sc,
+                                       a->lev[0].r);
   for (int l = 0; l + 1 < a->nlev; ++l) {
     const AmgLevel& F = a->lev[l];
-    const int gb = grid_for(a->lev[l + 1].n * 4);
+    const int gb = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)G * 2, (a->lev[l + 1].n + kRB - 1) / kRB));
     switch (width_bucket(F.width)) {
       case 8: k_pc_restrict<8><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
       case 16: k_pc_restrict<16><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
@@ -1620,8 +1628,8 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
     const AmgLevel& F = a->lev[l];
     const int gb = grid_for(F.n);
 #define RBFFD_UP(Wb)                                                                         \
-  k_pc_up<true, false, float, Wb><<<gb, kThreads, 0, st>>>(F, a->lev[l - 1], F.z, P->sc, P->gr, \
-                                                           which, 0.0, 0.0)
+  k_pc_up<true, false, float, Wb><<<gb, kThreads, 0, st>>>(F, a->lev[l - 1], F.z, nullptr,   \
+                                                           P->sc, P->gr, which, 0.0, 0.0)
     switch (width_bucket(F.width)) {
       case 8: RBFFD_UP(8); break;
       case 16: RBFFD_UP(16); break;
@@ -1633,8 +1641,8 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
   if (a->nlev >= 2) {
     const AmgLevel& F = a->lev[0];
 #define RBFFD_UP0(Wb)                                                                      \
-  k_pc_up<false, true, TV, Wb><<<G, kThreads, 0, st>>>(F, F, zout, P->sc, P->gr, which, \
-                                                       a->inv_ces, a->inv_R)
+  k_pc_up<false, true, TV, Wb><<<G, kThreads, 0, st>>>(F, F, zout, a->perm0, P->sc, P->gr, \
+                                                       which, a->inv_ces, a->inv_R)
     switch (width_bucket(F.width)) {
       case 8: RBFFD_UP0(8); break;
       case 16: RBFFD_UP0(16); break;
