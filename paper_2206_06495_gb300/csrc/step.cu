@@ -2041,9 +2041,12 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     const double* hb[2] = {P->ru, P->rv};
     SolveResult hr;
     int sweeps = 0;
+    // The viscous operator is well conditioned: its FP32 inner solves go to the
+    // square of the inner tolerance (each FP64 residual of the 3M-row, two-sided
+    // solve costs more than a few extra FP32 iterations).
     if (MIX)
-      rc = refine<K, 2, false>(ctx, P, H64, H32, hx, hb, f.tol, f.inner_tol, f.max_iter, &hr,
-                               &sweeps, st);
+      rc = refine<K, 2, false>(ctx, P, H64, H32, hx, hb, f.tol, f.inner_tol * f.inner_tol,
+                               f.max_iter, &hr, &sweeps, st);
     else
       rc = bicgstab<K, 2, false, double, double>(ctx, P, H64, hx, hb, P->kw64, f.tol, f.max_iter,
                                                  &hr, st);
