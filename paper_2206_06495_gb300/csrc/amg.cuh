@@ -36,7 +36,7 @@ namespace rbffd {
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAmgCoarse = 2048;  // coarsest level: at most this many rows, solved densely
 constexpr float kAmgOmega = 0.8f;
-constexpr float kAmgCoarseScale = 1.6f;
+constexpr float kAmgCoarseScale = 2.0f;
 
 // One level of the hierarchy (device arrays).  Rows of level l + 1 are the
 // aggregates of level l.  The coarsest level holds only r, z and the dense

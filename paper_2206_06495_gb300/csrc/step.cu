@@ -1691,6 +1691,9 @@ int chunk_graph(rbffd_ctx* ctx, StepPlan* P, const void* const (&key)[10], int n
   return RBFFD_OK;
 }
 
+constexpr int kRestartLen = 50;    // preconditioned cycle length
+constexpr int kMaxRestarts = 400;  // restarts of one solve before giving up
+
 // BiCGSTAB on op x = b; with pc (pressure solves only, one right side, no
 // rdot), right-preconditioned: p^ = B p, s^ = B s, the SpMVs act on p^ and s^,
 // and x gathers alpha p^ + omega s^, so r stays the true residual recurrence.
@@ -1778,7 +1781,11 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     if (rc) return rc;
     int issued = 0, chunk = 4, prev_iters = 0;
     double prev_rel = -1.0;
-    const int budget = maxit - total;
+    // Preconditioned solves restart every kRestartLen iterations from the
+    // current iterate (true residual, fresh shadow residual): on some node
+    // sets the preconditioned BiCGSTAB recurrences otherwise stagnate for
+    // thousands of iterations.
+    const int budget = pc ? std::min(maxit - total, kRestartLen) : maxit - total;
     for (;;) {
       rc = check_cuda(ctx, cudaMemcpyAsync(h, P->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st),
                       "scalar copy");
@@ -1883,7 +1890,10 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
               sizeof(TV) == 8 ? "fp64" : "fp32", NRHS, restart, h->iters, worst, h->status);
     const bool breakdown = h->status == 1 || h->status == 3 || h->status == 4;
     const bool diverged = h->status == 5;
-    if (conv || !(breakdown || diverged) || total >= maxit || restart >= 50) break;
+    const bool cycle_end = pc && !h->done && h->iters >= budget;  // restart, keep x
+    if (conv || !(breakdown || diverged || cycle_end) || total >= maxit ||
+        restart >= kMaxRestarts)
+      break;
     if (diverged) {  // start again from the initial iterate
       for (int q = 0; q < NRHS; ++q) {
         rc = check_cuda(ctx, cudaMemcpyAsync(x[q], work[6][q], sizeof(TV) * op.n,
