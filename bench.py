@@ -385,7 +385,8 @@ def run_ours(args):
     else:
         bytes_row, key = 12 * k + 4 + 4 * 8, "k_spmv_pc_fp64"
     per_launch_ms = r["spmv_ms"] / max(r["spmv_launches"], 1)
-    achieved = nd.M * bytes_row / (per_launch_ms * 1e-3) / 1e9
+    achieved = (nd.M * bytes_row / (per_launch_ms * 1e-3) / 1e9
+                if r["spmv_launches"] > 0 and per_launch_ms > 0 else None)
     traffic = profiled_traffic(key, nd.M)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -405,11 +406,13 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nd.N * 8,
                 "d2h_bytes_per_step": 2 * nd.N * 8},
         "roofline": {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                     "traffic": traffic,
                      "bytes_per_row": bytes_row, "rows": nd.M, "peak_kind": peak_kind,
                      "launches_timed": r["spmv_launches"], "us_per_launch": per_launch_ms * 1e3,
-                     "timing": "CUDA events around every launch of this kernel in one eager "
-                               "step right after the timed steps"},
+                     "timing": "CUDA events recorded by graph nodes around every launch of "
+                               "this kernel in one profiled step right after the timed "
+                               "steps (launches that found the solve finished excluded)"},
         "spmv": spmv,
         "weights": weights,
         "clocks": sampler.summary(windows) if sampler else None,
