@@ -383,7 +383,7 @@ def run_ours(args):
     if head == "mixed":
         bytes_row, key = 8 * k + 5 * 4, "k_spmv_pc_fp32"  # FP32 inner solves
     else:
-        bytes_row, key = 12 * k + 4 + 4 * 8, "k_spmv_pc_fp64"
+        bytes_row, key = 12 * k + 5 * 8, "k_spmv_pc_fp64"  # z gathered as FP64
     per_launch_ms = r["spmv_ms"] / max(r["spmv_launches"], 1)
     achieved = (nd.M * bytes_row / (per_launch_ms * 1e-3) / 1e9
                 if r["spmv_launches"] > 0 and per_launch_ms > 0 else None)
