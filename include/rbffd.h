@@ -276,6 +276,9 @@ typedef struct rbffd_stats {
   int64_t launches;         /* kernels launched by this call                  */
   int64_t spmv_launches;    /* profile: timed SpMV launches of the pressure solves */
   double spmv_ms;           /* profile: their summed durations, milliseconds  */
+  int64_t spmv_batch_launches; /* profile: the same SpMV relaunched back to back after
+                                  each pressure solve (20 per solve)            */
+  double spmv_batch_ms;     /* profile: their summed durations, milliseconds  */
 } rbffd_stats;
 
 /*

@@ -84,7 +84,8 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("helm_iters", C.c_int64), ("poisson_iters", C.c_int64),
                 ("refinements", C.c_int64), ("helm_relres", C.c_double),
                 ("poisson_relres", C.c_double), ("launches", C.c_int64),
-                ("spmv_launches", C.c_int64), ("spmv_ms", C.c_double)]
+                ("spmv_launches", C.c_int64), ("spmv_ms", C.c_double),
+                ("spmv_batch_launches", C.c_int64), ("spmv_batch_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
