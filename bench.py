@@ -314,6 +314,7 @@ def run_ours(args):
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1), world)
         res[name]["e2e_ms"] = ems
+        res[name]["state"] = st  # both precisions take the same steps from rest
     if sampler:
         sampler.stop()
 
@@ -432,6 +433,17 @@ def run_ours(args):
         "clocks": sampler.summary(windows) if sampler else None,
         "failed": failed,
     }
+    if "mixed" in res and "fp64" in res:
+        # the mixed-precision fields against the FP64 path after the same steps
+        a, b = res["mixed"]["state"], res["fp64"]["state"]
+
+        def rel(x, y):
+            return float((x - y).abs().max() / y.abs().max().clamp_min(1e-300))
+        out["mixed_vs_fp64"] = {
+            "steps": 2 * args.steps + args.warmup + 1,
+            "u_max_abs": float((a.u - b.u).abs().max()), "v_max_abs": float((a.v - b.v).abs().max()),
+            "u_rel": rel(a.u, b.u), "v_rel": rel(a.v, b.v),
+            "p_rel": rel(a.p, b.p), "pt_rel": rel(a.pt, b.pt)}
     for name in res:
         rr = res[name]
         out[name] = {"steps_per_s": args.steps / (rr["ms"] * 1e-3),

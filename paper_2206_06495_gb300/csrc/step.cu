@@ -1375,8 +1375,8 @@ struct StepPlan {
   int* err = nullptr;
   double *Lw = nullptr, *es = nullptr, *scale = nullptr, *Hw = nullptr;
   float *Lw32 = nullptr, *es32 = nullptr, *Hw32 = nullptr;
-  float *vv_dx32 = nullptr, *vv_dy32 = nullptr, *vv_lap32 = nullptr, *pv_dx32 = nullptr,
-        *pv_dy32 = nullptr, *pp_lap32 = nullptr, *vp_dx32 = nullptr, *vp_dy32 = nullptr;
+  float *vv_dx32 = nullptr, *vv_dy32 = nullptr, *vv_lap32 = nullptr, *pp_lap32 = nullptr,
+        *vp_dx32 = nullptr, *vp_dy32 = nullptr;
   // stage vectors
   double *us = nullptr, *vs = nullptr, *ru = nullptr, *rv = nullptr, *uss = nullptr,
          *vss = nullptr, *pb = nullptr, *px = nullptr;
@@ -1556,8 +1556,6 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     TRY(to32(ctx, p, f.vv_dx, nv, &p->vv_dx32, st));
     TRY(to32(ctx, p, f.vv_dy, nv, &p->vv_dy32, st));
     TRY(to32(ctx, p, f.vv_lap, nv, &p->vv_lap32, st));
-    TRY(to32(ctx, p, f.pv_dx, np, &p->pv_dx32, st));
-    TRY(to32(ctx, p, f.pv_dy, np, &p->pv_dy32, st));
     TRY(to32(ctx, p, f.pp_lap, np, &p->pp_lap32, st));
     TRY(to32(ctx, p, f.vp_dx, nv, &p->vp_dx32, st));
     TRY(to32(ctx, p, f.vp_dy, nv, &p->vp_dy32, st));
@@ -2094,8 +2092,6 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   const void* vdx = MIX ? (const void*)P->vv_dx32 : (const void*)f.vv_dx;
   const void* vdy = MIX ? (const void*)P->vv_dy32 : (const void*)f.vv_dy;
   const void* vlap = MIX ? (const void*)P->vv_lap32 : (const void*)f.vv_lap;
-  const void* pdx = MIX ? (const void*)P->pv_dx32 : (const void*)f.pv_dx;
-  const void* pdy = MIX ? (const void*)P->pv_dy32 : (const void*)f.pv_dy;
   const void* plap = MIX ? (const void*)P->pp_lap32 : (const void*)f.pp_lap;
   const void* gdx = MIX ? (const void*)P->vp_dx32 : (const void*)f.vp_dx;
   const void* gdy = MIX ? (const void*)P->vp_dy32 : (const void*)f.vp_dy;
@@ -2165,9 +2161,12 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
       k_split<<<G, kThreads, 0, st>>>(f.N, P->uss, P->uss2);
       k_split<<<G, kThreads, 0, st>>>(f.N, P->vss, P->vss2);
     }
-    DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, pdx,      pdy,          P->uss,
+    // The divergence is the right side of the pressure solve and nearly zero:
+    // FP32 weights would leave their rounding (relative to the terms, not to
+    // their small sum) in p~, so both precisions take it with FP64 weights.
+    DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, f.pv_dx,  f.pv_dy,      P->uss,
                P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb};
-    k_divergence<K, MIX><<<G, kThreads, 0, st>>>(da);
+    k_divergence<K, false><<<G, kThreads, 0, st>>>(da);
     if (P->px_step != s->j) {  // warm start from the state's p~ unless px is current
       rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
                                            cudaMemcpyDeviceToDevice, st),
