@@ -1,13 +1,14 @@
 // The fractional step of Section 3 on the GPU: explicit stages as fused ELL
 // kernels, implicit stages as BiCGSTAB solves built on the same ELL streams.
 //
-// Layout: every operator is slot-major ELL (idx[s*ld+i], w[s*ld+i]); vectors
-// are plain FP64 arrays, and in MIXED precision every vector that an FP32
-// operator gathers also has a split FP32 copy (hi, lo) with hi + lo == x to
-// about 2^-48 relative.  FP32 derivative operators gather differences
-// (x_j - x_ref) = (hi_j - hi_ref) + (lo_j - lo_ref) against the stencil's
-// nearest node, so the cancellation of a derivative stencil happens before
-// the rounding to FP32 rather than after it.
+// Layout: every operator is slot-major ELL (idx[s*ld+i], w[s*ld+i]); state
+// vectors are plain FP64 arrays.  In MIXED precision the explicit stages use
+// FP32 weights, and every vector they gather also has a split FP32 copy
+// (hi, lo) with hi + lo == x to about 2^-48 relative: FP32 derivative
+// operators gather differences (x_j - x_ref) = (hi_j - hi_ref) + (lo_j - lo_ref)
+// against the stencil's nearest node, so the cancellation of a derivative
+// stencil happens before the rounding to FP32 rather than after it.  The
+// divergence (the pressure solve's right side) keeps FP64 weights.
 //
 // Implicit solves (rows scaled as below, relative residual on the scaled
 // system):
@@ -55,9 +56,8 @@ bool trace_on() {
 struct KScal {
   double rho[2], alpha[2], omega[2], beta[2];
   double rr[2], bb[2];
-  double sum_p, sum_s, sum_x;
+  double sum_p, sum_s;
   double cp, cs;  // preconditioned solves: (c . p), (c . s) of the multigrid's level-0 map
-  double ysum;    // preconditioned solves: sum of the V-cycle result before its shift
   double kap[2];  // preconditioned solves: B p = zp + kap[0], B s = zs + kap[1]
   double tol2;
   int active[2];
