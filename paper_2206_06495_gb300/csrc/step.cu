@@ -86,6 +86,9 @@ struct KOp {
   const TV* es;    // rank-one column, or null
   const TV* rdot;  // rank-one row (y += es * (rdot . x)); null = all ones
   const TV* a1 = nullptr;  // A 1 (row sums): the product with a constant shift
+  // tile records of (idx, w) in the layout of one EllStage each (null: none):
+  // a staged SpMV then moves a whole tile with one bulk copy
+  const unsigned char* tiles = nullptr;
 };
 
 template <typename T>
@@ -175,9 +178,14 @@ template <int K, typename TW>
 __device__ __forceinline__ bool stage_tile(EllStage<K, TW>* tile, uint64_t* bar, uint32_t& phase,
                                            const int32_t* __restrict__ gidx,
                                            const TW* __restrict__ gw, int64_t ld, int64_t row0,
-                                           int* err) {
+                                           int* err, const unsigned char* tiles = nullptr) {
   __syncthreads();  // every thread is done with the previous tile
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && tiles) {
+    // one record per tile, already in the EllStage layout: one copy
+    constexpr uint32_t rec = (uint32_t)sizeof(EllStage<K, TW>);
+    mbar_expect_tx(bar, rec);
+    bulk_g2s(tile, tiles + (row0 / kTileRows) * (int64_t)rec, rec, bar);
+  } else if (threadIdx.x == 0) {
     const int64_t left = ld - row0;
     const uint32_t rows = (uint32_t)(left < kTileRows ? left : kTileRows);  // multiple of 32
     const uint32_t bi = rows * 4u, bw = rows * (uint32_t)sizeof(TW);
@@ -837,7 +845,9 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
     for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
       const int64_t row0 = tix * kTileRows;
-      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err,
+                             op.tiles))
+        break;
       const int64_t i = row0 + threadIdx.x;
       if (i < op.n) {
         ZAcc<TW, TV> acc;
@@ -1362,6 +1372,26 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restr
 }  // namespace
 
 // ------------------------------------------------------------------ plan
+// Tile records of a slot-major ELL operator: record t holds idx[s][t*256 + r]
+// and then w[s][t*256 + r] for s < k, r < 256 (rows past ld: index 0,
+// weight 0), which is the layout of one EllStage.
+template <typename TW>
+__global__ void __launch_bounds__(kThreads)
+    k_tile_records(int64_t ld, int k, int64_t ntiles, const int32_t* __restrict__ idx,
+                   const TW* __restrict__ w, unsigned char* __restrict__ out) {
+  const int64_t per = (int64_t)k * kTileRows;
+  const int64_t rec = per * (int64_t)(sizeof(int32_t) + sizeof(TW));
+  for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < ntiles * per;
+       e += (int64_t)gridDim.x * kThreads) {
+    const int64_t t = e / per, rem = e - t * per;
+    const int64_t s = rem / kTileRows, row = t * kTileRows + (rem - s * kTileRows);
+    const bool in = row < ld;
+    reinterpret_cast<int32_t*>(out + t * rec)[rem] = in ? idx[s * ld + row] : 0;
+    reinterpret_cast<TW*>(out + t * rec + per * (int64_t)sizeof(int32_t))[rem] =
+        in ? w[s * ld + row] : (TW)0;
+  }
+}
+
 struct StepPlan {
   rbffd_flow key;
   int k = 0;
@@ -1394,6 +1424,9 @@ struct StepPlan {
   Amg* amg = nullptr;                 // pressure preconditioner (precond = 1)
   double* a1 = nullptr;    // row sums of the FP64 pressure operator
   float* a1_32 = nullptr;  // row sums of its FP32 copy
+  // tile records of the pressure operator the preconditioned solves apply
+  // (FP32 weights in MIXED precision, FP64 otherwise)
+  unsigned char* Lt = nullptr;
   // CUDA graphs of Krylov iteration chunks: one per solve (its operator,
   // vectors and preconditioner) and chunk length, captured on first use on a
   // private stream and replayed on the caller's stream
@@ -1574,6 +1607,19 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       TRY(palloc(ctx, p, &p->r32[b], nmax));
       TRY(palloc(ctx, p, &p->r64[b], nmax));
     }
+  }
+  if (f.precond) {
+    const int64_t ntiles = (f.M + kTileRows - 1) / kTileRows;
+    const size_t wsz = p->mix ? sizeof(float) : sizeof(double);
+    const size_t rec = (size_t)p->k * kTileRows * (sizeof(int32_t) + wsz);
+    TRY(palloc(ctx, p, &p->Lt, rec * (size_t)ntiles));
+    if (p->mix)
+      k_tile_records<float><<<p->grid, kThreads, 0, st>>>(f.ld_p, p->k, ntiles, p->Lidx,
+                                                           p->Lw32, p->Lt);
+    else
+      k_tile_records<double><<<p->grid, kThreads, 0, st>>>(f.ld_p, p->k, ntiles, p->Lidx,
+                                                            p->Lw, p->Lt);
+    TRY(check_cuda(ctx, cudaGetLastError(), "tile records"));
   }
 #undef TRY
   *out = p;
@@ -2120,6 +2166,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, k, 0, P->es, nullptr, P->a1};
   KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
   KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es32, nullptr, P->a1_32};
+  if (f.precond) (MIX ? L32.tiles : L64.tiles) = P->Lt;
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
                 P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,
