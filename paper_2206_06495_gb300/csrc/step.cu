@@ -369,7 +369,9 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
     for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
       const int64_t row0 = tix * kTileRows;
-      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err,
+                             op.tiles))
+        break;
       const int64_t i = row0 + threadIdx.x;
       if (i < op.n) {
         A acc[NRHS];
@@ -478,7 +480,9 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t ntiles = (op.n + kTileRows - 1) / kTileRows;
     for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
       const int64_t row0 = tix * kTileRows;
-      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err)) break;
+      if (!stage_tile<K, TW>(tile, &bar, phase, op.idx, op.w, op.ld, row0, &sc->stage_err,
+                             op.tiles))
+        break;
       const int64_t i = row0 + threadIdx.x;
       if (i < op.n) {
         A acc[NRHS];
@@ -1424,9 +1428,10 @@ struct StepPlan {
   Amg* amg = nullptr;                 // pressure preconditioner (precond = 1)
   double* a1 = nullptr;    // row sums of the FP64 pressure operator
   float* a1_32 = nullptr;  // row sums of its FP32 copy
-  // tile records of the pressure operator the preconditioned solves apply
-  // (FP32 weights in MIXED precision, FP64 otherwise)
+  // tile records of the pressure and viscous operators the Krylov solves
+  // apply (FP32 weights in MIXED precision, FP64 otherwise)
   unsigned char* Lt = nullptr;
+  unsigned char* Ht = nullptr;
   // CUDA graphs of Krylov iteration chunks: one per solve (its operator,
   // vectors and preconditioner) and chunk length, captured on first use on a
   // private stream and replayed on the caller's stream
@@ -1608,18 +1613,22 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       TRY(palloc(ctx, p, &p->r64[b], nmax));
     }
   }
-  if (f.precond) {
-    const int64_t ntiles = (f.M + kTileRows - 1) / kTileRows;
+  {
     const size_t wsz = p->mix ? sizeof(float) : sizeof(double);
     const size_t rec = (size_t)p->k * kTileRows * (sizeof(int32_t) + wsz);
-    TRY(palloc(ctx, p, &p->Lt, rec * (size_t)ntiles));
-    if (p->mix)
-      k_tile_records<float><<<p->grid, kThreads, 0, st>>>(f.ld_p, p->k, ntiles, p->Lidx,
-                                                           p->Lw32, p->Lt);
-    else
-      k_tile_records<double><<<p->grid, kThreads, 0, st>>>(f.ld_p, p->k, ntiles, p->Lidx,
-                                                            p->Lw, p->Lt);
-    TRY(check_cuda(ctx, cudaGetLastError(), "tile records"));
+    auto records = [&](int64_t rows, int64_t ld, const int32_t* idx, const double* w64,
+                       const float* w32, unsigned char** out) -> int {
+      const int64_t ntiles = (rows + kTileRows - 1) / kTileRows;
+      int rc = palloc(ctx, p, out, rec * (size_t)ntiles);
+      if (rc) return rc;
+      if (p->mix)
+        k_tile_records<float><<<p->grid, kThreads, 0, st>>>(ld, p->k, ntiles, idx, w32, *out);
+      else
+        k_tile_records<double><<<p->grid, kThreads, 0, st>>>(ld, p->k, ntiles, idx, w64, *out);
+      return check_cuda(ctx, cudaGetLastError(), "tile records");
+    };
+    TRY(records(f.N, f.ld_v, f.vv_idx, p->Hw, p->Hw32, &p->Ht));
+    if (f.precond) TRY(records(f.M, f.ld_p, p->Lidx, p->Lw, p->Lw32, &p->Lt));
   }
 #undef TRY
   *out = p;
@@ -2167,6 +2176,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
   KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es32, nullptr, P->a1_32};
   if (f.precond) (MIX ? L32.tiles : L64.tiles) = P->Lt;
+  (MIX ? H32.tiles : H64.tiles) = P->Ht;
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
                 P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,
