@@ -171,7 +171,8 @@ typedef struct rbffd_ell {
  * grid on this operator into context scratch (synchronising `stream`; skipped
  * while the stream is being captured) and keeps the fastest.  Every shape
  * adds a row's terms in the same order, so results do not depend on the
- * choice.  Errors: INVALID_ARG, CUDA.
+ * choice.  An operator with n_rows == 0 is a no-op (its arrays, x and y may
+ * then be null).  Errors: INVALID_ARG (null pointer, bad shape or dtype), CUDA.
  */
 int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, double alpha,
                    double beta, int32_t xy_dtype, cudaStream_t stream);

@@ -166,15 +166,15 @@ int rbffd_apply_op(rbffd_ctx* ctx, const rbffd_ell* D, const void* x, void* y, d
                    double beta, int32_t xy_dtype, cudaStream_t stream) {
   if (!ctx) return RBFFD_ERR_INVALID_ARG;
   ctx->err.clear();
-  if (!D || !D->idx || !D->w || !x || !y)
-    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  if (!D) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
   if (D->n_rows < 0 || D->n_cols < 1 || D->n < 1 || D->n > kMaxStencil || D->ld < D->n_rows ||
       D->ld % 32)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad operator shape");
   if ((D->w_dtype != RBFFD_F64 && D->w_dtype != RBFFD_F32) ||
       (xy_dtype != RBFFD_F64 && xy_dtype != RBFFD_F32))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad dtype");
-  if (D->n_rows == 0) return RBFFD_OK;
+  if (D->n_rows == 0) return RBFFD_OK;  // nothing to read or write
+  if (!D->idx || !D->w || !x || !y) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
   return spmv_apply(ctx, D, x, y, alpha, beta, xy_dtype, stream);
 }
 

@@ -1031,6 +1031,17 @@ __global__ void k_addcorr(int64_t n, Vecs<double, NRHS> x, Vecs<float, NRHS> e32
   }
 }
 
+// Initial guess of a pressure solve from the two previous solutions (linear
+// extrapolation in time): x = 2 x_prev - x_prev2, and x_prev2 takes x_prev.
+__global__ void k_extrapolate(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = x[i];
+    x[i] = 2.0 * t - x_prev2[i];
+    x_prev2[i] = t;
+  }
+}
+
 __global__ void k_split(int64_t n, const double* __restrict__ x, float2* __restrict__ x2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -1415,6 +1426,8 @@ struct StepPlan {
   double *us = nullptr, *vs = nullptr, *ru = nullptr, *rv = nullptr, *uss = nullptr,
          *vss = nullptr, *pb = nullptr, *px = nullptr;
   int64_t px_step = -1;  // step index whose pressure solve left its solution in px
+  double* pxp = nullptr;   // the pressure solution of the step before px's
+  int64_t pxp_step = -1;   // px_step of pxp's solution when it was current
   float2 *u2 = nullptr, *v2 = nullptr, *us2 = nullptr, *vs2 = nullptr, *uss2 = nullptr,
          *vss2 = nullptr, *pt2 = nullptr, *px2 = nullptr;
   // Krylov work (6 vectors x 2 right sides) in FP64 and FP32
@@ -1533,6 +1546,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   TRY(palloc(ctx, p, &p->vss, f.N));
   TRY(palloc(ctx, p, &p->pb, f.M));
   TRY(palloc(ctx, p, &p->px, f.M));
+  TRY(palloc(ctx, p, &p->pxp, f.M));
   for (int a = 0; a < 7; ++a)
     for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw64[a][b], nmax));
   TRY(palloc(ctx, p, &p->sc, 1));
@@ -2224,11 +2238,27 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, f.pv_dx,  f.pv_dy,      P->uss,
                P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb};
     k_divergence<K, false><<<G, kThreads, 0, st>>>(da);
-    if (P->px_step != s->j) {  // warm start from the state's p~ unless px is current
+    // Initial guess: the linear extrapolation of the two previous steps'
+    // solutions when both are at hand, else the previous solution, else the
+    // state's p~.  Any guess leaves the converged solution the same; a better
+    // one saves iterations (p~ changes smoothly from step to step).
+    if (P->px_step != s->j) {
       rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
                                            cudaMemcpyDeviceToDevice, st),
                       "warm start");
       if (rc) return rc;
+      P->pxp_step = -1;
+    } else {
+      if (P->pxp_step == s->j - 1) {
+        k_extrapolate<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp);
+        rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
+      } else {
+        rc = check_cuda(ctx, cudaMemcpyAsync(P->pxp, P->px, sizeof(double) * f.M,
+                                             cudaMemcpyDeviceToDevice, st),
+                        "previous solution");
+      }
+      if (rc) return rc;
+      P->pxp_step = s->j;
     }
     double* px[1] = {P->px};
     const double* pbv[1] = {P->pb};

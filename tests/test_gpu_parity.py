@@ -140,6 +140,23 @@ def test_invalid_args_rejected(R, ctx):
         R.Context(28, 6, 3)  # even exponent
 
 
+def test_empty_inputs_are_no_ops(R, ctx):
+    """No alpha-nodes and no operator rows: the calls succeed and touch nothing."""
+    rng = np.random.default_rng(4)
+    e = _d(np.zeros(0))
+    bx, by = _d(rng.random(40)), _d(rng.random(40))
+    idx, w, bad = R.build_weights(ctx, e, e, bx, by, R.OP_DX | R.OP_LAP)
+    assert bad == -1 and tuple(w.shape) == (2, 28, 32)
+    idx.fill_(0)
+    w.fill_(1.0)
+    y = R.apply_op(ctx, idx, w[0], 0, 40, _d(np.ones(40)))
+    assert y.numel() == 0
+    # a zero-row operator leaves an existing output alone
+    y = _d(np.full(3, 7.0))
+    R.apply_op(ctx, idx, w[0], 0, 40, _d(np.ones(40)), y, alpha=2.0, beta=0.5)
+    assert (y.cpu().numpy() == 7.0).all()
+
+
 @pytest.mark.parametrize("wdt", ["f64", "f32"])
 def test_apply_op_matches_csr(R, ctx, wdt):
     nd = ns.jittered_cavity(33, 7)
