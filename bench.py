@@ -231,12 +231,12 @@ def run_ours(args):
             continue
         if not flows:
             base = R.flow_from_nodes(ctx, nd, Re=args.re, dt=args.dt, precision=prec,
-                                     tol=args.tol, inner_tol=1e-2, max_iter=args.max_iter)
+                                     tol=args.tol, inner_tol=5e-3, max_iter=args.max_iter)
             flows[name] = base
         else:
             b0 = next(iter(flows.values()))
             flows[name] = R.Flow(N=b0.N, M=b0.M, tensors=b0.tensors, Re=args.re, dt=args.dt,
-                                 precision=prec, tol=args.tol, inner_tol=1e-2,
+                                 precision=prec, tol=args.tol, inner_tol=5e-3,
                                  max_iter=args.max_iter)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
@@ -504,7 +504,7 @@ def profile_step(args):
     ctx = R.Context(28, 7, 3)
     nd = ns.jittered_cavity(args.n, 2)
     flow = R.flow_from_nodes(ctx, nd, Re=args.re, dt=args.dt, precision=prec, tol=args.tol,
-                             inner_tol=1e-2, max_iter=args.max_iter)
+                             inner_tol=5e-3, max_iter=args.max_iter)
     gu_h = np.zeros(nd.N)
     gu_h[nd.v_wall == ns.WALL_TOP] = 1.0
     gu = torch.as_tensor(gu_h, device="cuda")

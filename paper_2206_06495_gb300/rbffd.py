@@ -274,7 +274,7 @@ class Flow:
     dt: float
     precision: int = PREC_FP64
     tol: float = 1e-12
-    inner_tol: float = 1e-2
+    inner_tol: float = 5e-3
     max_iter: int = 20000
     km_mode: int = 1
     overwrite_bc: int = 1
