@@ -4,6 +4,7 @@
 // it every iterate of the solver, is the same from run to run.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "amg.cuh"
@@ -270,6 +271,48 @@ int download(rbffd_ctx* ctx, const T* d, size_t count, std::vector<T>* h, cudaSt
 
 }  // namespace
 
+// Level-0 block records (see Level0Rec) from the host copies of level 0.
+template <int W>
+int level0_records(rbffd_ctx* ctx, Amg* a, const AmgLevel& g, const std::vector<int32_t>& hidx,
+                   const std::vector<float>& hval, const std::vector<float>& hd,
+                   const std::vector<float>& hwd, const std::vector<int32_t>& cptr,
+                   const std::vector<int32_t>& perm0, int64_t nc, cudaStream_t st) {
+  const int64_t nrec = (nc + kRecAggs - 1) / kRecAggs;
+  std::vector<Level0Rec<W>> recs((size_t)nrec);
+  for (int64_t b = 0; b < nrec; ++b) {
+    Level0Rec<W>& R = recs[(size_t)b];
+    memset(&R, 0, sizeof(R));
+    const int64_t I0 = b * kRecAggs, I1 = std::min<int64_t>(I0 + kRecAggs, nc);
+    const int64_t f0 = cptr[I0], f1 = cptr[I1];
+    if (f1 - f0 > kRecRows)
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid block of %lld rows",
+                       (long long)(f1 - f0));
+    R.f0 = (int32_t)f0;
+    R.nrows = (int32_t)(f1 - f0);
+    R.nagg = (int32_t)(I1 - I0);
+    for (int64_t I = I0; I <= I1; ++I) R.off[I - I0] = (int32_t)(cptr[I] - f0);
+    for (int r = 0; r < kRecRows; ++r) {
+      const int64_t i = f0 + r;
+      const bool in = i < f1;
+      for (int s = 0; s < W; ++s) {
+        const bool slot = in && s < g.width;
+        R.idx[s * kRecRows + r] = slot ? hidx[(size_t)s * g.ld + i] : (int32_t)f0;
+        R.val[s * kRecRows + r] = slot ? hval[(size_t)s * g.ld + i] : 0.f;
+      }
+      R.diag[r] = in ? hd[i] : 0.f;
+      R.wd[r] = in ? hwd[i] : 0.f;
+      R.perm0[r] = in ? perm0[i] : 0;
+    }
+  }
+  std::vector<unsigned char> bytes(sizeof(Level0Rec<W>) * (size_t)nrec);
+  memcpy(bytes.data(), recs.data(), bytes.size());
+  const int rc = upload(ctx, a, bytes, &a->rec0, st);
+  if (rc) return rc;
+  a->rec0_w = W;
+  a->rec0_n = nrec;
+  return RBFFD_OK;
+}
+
 void amg_free(Amg* a) {
   if (!a) return;
   for (void* p : a->allocs) cudaFree(p);
@@ -389,6 +432,13 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
         (rc = upload(ctx, a, hd, &g.diag, st)) || (rc = upload(ctx, a, hwd, &g.wd, st)) ||
         (rc = upload(ctx, a, cptrs[l], &g.cptr, st)))
       return fail(rc);
+    if (l == 0 && width <= 16) {
+      rc = width <= 8 ? level0_records<8>(ctx, a, g, hidx, hval, hd, hwd, cptrs[0], oldi[0],
+                                          L[1].n, st)
+                      : level0_records<16>(ctx, a, g, hidx, hval, hd, hwd, cptrs[0], oldi[0],
+                                           L[1].n, st);
+      if (rc) return fail(rc);
+    }
   }
   a->nc = L.back().n;
   std::vector<float> hX(Xd.begin(), Xd.end());

@@ -792,6 +792,111 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Level 0 from block records (Level0Rec): a block stages the record of its
+// 64 aggregates with one bulk copy (bounded wait; a copy that does not land
+// sets *err and ends the block's work), then runs the same arithmetic in the
+// same order as k_pc_restrict / k_pc_up on those rows.
+static_assert(kRB == kRecAggs && kThreads == kRecRows, "level-0 record shape");
+
+template <int W>
+__device__ __forceinline__ bool stage_rec(Level0Rec<W>* rec, uint64_t* bar, uint32_t& phase,
+                                          const unsigned char* __restrict__ recs, int64_t b,
+                                          int* err) {
+  __syncthreads();  // every thread is done with the previous record
+  if (threadIdx.x == 0) {
+    constexpr uint32_t bytes = (uint32_t)sizeof(Level0Rec<W>);
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(rec, recs + b * (int64_t)bytes, bytes, bar);
+  }
+  long long spins = 0;
+  bool ok;
+  while (!(ok = mbar_try_wait(bar, phase)) && ++spins < kSpinLimit) {
+  }
+  if (!__syncthreads_and(ok ? 1 : 0)) {
+    if (threadIdx.x == 0) atomicOr(err, 4);
+    spins = 0;
+    while (!mbar_try_wait(bar, phase) && ++spins < kSpinLimit) {
+    }
+    return false;
+  }
+  phase ^= 1u;
+  return true;
+}
+
+// sum_s val[s] * get(idx[s]) over a record row's slots (slot s < width)
+template <int W, typename Get>
+__device__ __forceinline__ float rec_row(const Level0Rec<W>& R, int width, int r, Get get) {
+  float ax = 0.f;
+#pragma unroll
+  for (int s = 0; s < W; ++s)
+    if (s < width) ax += R.val[s * kRecRows + r] * get(R.idx[s * kRecRows + r]);
+  return ax;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+    k_pc_restrict0(AmgLevel F, int64_t nrec, const unsigned char* __restrict__ recs,
+                   float* __restrict__ rc, KScal* sc) {
+  if (sc->done) return;
+  __shared__ __align__(128) Level0Rec<W> rec;
+  __shared__ float res[kThreads];
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  const int t = threadIdx.x;
+  for (int64_t b = blockIdx.x; b < nrec; b += gridDim.x) {
+    if (!stage_rec<W>(&rec, &bar, phase, recs, b, &sc->stage_err)) break;
+    float rv = 0.f;
+    if (t < rec.nrows) {
+      const int64_t i = (int64_t)rec.f0 + t;
+      const float ri = F.r[i];
+      const float xi = rec.wd[t] * ri;
+      F.x[i] = xi;
+      const float ax =
+          rec.diag[t] * xi + rec_row<W>(rec, F.width, t, [&](int32_t j) { return F.wd[j] * F.r[j]; });
+      rv = ri - ax;
+    }
+    res[t] = rv;
+    __syncthreads();
+    if (t < rec.nagg) {
+      float acc = 0.f;
+      for (int c = rec.off[t]; c < rec.off[t + 1]; ++c) acc += res[c];
+      rc[b * kRB + t] = acc;
+    }
+  }
+}
+
+template <typename TZ, int W>
+__global__ void __launch_bounds__(kThreads)
+    k_pc_up0(AmgLevel F, int64_t nrec, const unsigned char* __restrict__ recs,
+             TZ* __restrict__ z, KScal* sc, GridReduce gr, int which, double inv_ces,
+             double inv_R) {
+  if (sc->done) return;
+  constexpr int NU_ = 1;
+  __shared__ double sh[NU_ * kThreads];
+  __shared__ __align__(128) Level0Rec<W> rec;
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  const int t = threadIdx.x;
+  float part = 0.f;
+  for (int64_t b = blockIdx.x; b < nrec; b += gridDim.x) {
+    if (!stage_rec<W>(&rec, &bar, phase, recs, b, &sc->stage_err)) break;
+    if (t < rec.nrows) {
+      const int64_t i = (int64_t)rec.f0 + t;
+      const float xi = F.x[i];
+      const float ax = rec.diag[t] * xi + rec_row<W>(rec, F.width, t, [&](int32_t j) { return F.x[j]; });
+      const float zi = xi + rec.wd[t] * (F.r[i] - ax);
+      z[rec.perm0[t]] = (TZ)zi;  // back to P-node order
+      part += zi;
+    }
+  }
+  double v[NU_] = {(double)part};
+  grid_reduce<NU_>(v, gr, sh, [&](double* t2) { pc_finish(sc, which, t2[0], inv_ces, inv_R); });
+}
+
 // one-level hierarchy: the lifted coarse solve is already mean-free
 __global__ void k_pc_fin1(KScal* sc, int which, double inv_ces, double inv_R) {
   if (sc->done) return;
@@ -1705,6 +1810,13 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
     const AmgLevel& F = a->lev[l];
     const int gb = (int)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)G * 2, (a->lev[l + 1].n + kRB - 1) / kRB));
+    if (l == 0 && a->rec0) {
+      if (a->rec0_w == 8)
+        k_pc_restrict0<8><<<gb, kThreads, 0, st>>>(F, a->rec0_n, a->rec0, a->lev[1].r, P->sc);
+      else
+        k_pc_restrict0<16><<<gb, kThreads, 0, st>>>(F, a->rec0_n, a->rec0, a->lev[1].r, P->sc);
+      continue;
+    }
     switch (width_bucket(F.width)) {
       case 8: k_pc_restrict<8><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
       case 16: k_pc_restrict<16><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc); break;
@@ -1730,7 +1842,15 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
     }
 #undef RBFFD_UP
   }
-  if (a->nlev >= 2) {
+  if (a->nlev >= 2 && a->rec0) {
+    const int gu = (int)std::max<int64_t>(1, std::min<int64_t>(G, a->rec0_n));
+    if (a->rec0_w == 8)
+      k_pc_up0<TV, 8><<<gu, kThreads, 0, st>>>(a->lev[0], a->rec0_n, a->rec0, zout, P->sc, P->gr,
+                                                which, a->inv_ces, a->inv_R);
+    else
+      k_pc_up0<TV, 16><<<gu, kThreads, 0, st>>>(a->lev[0], a->rec0_n, a->rec0, zout, P->sc,
+                                                 P->gr, which, a->inv_ces, a->inv_R);
+  } else if (a->nlev >= 2) {
     const AmgLevel& F = a->lev[0];
 #define RBFFD_UP0(Wb)                                                                      \
   k_pc_up<false, true, TV, Wb><<<G, kThreads, 0, st>>>(F, F, zout, a->perm0, P->sc, P->gr, \
