@@ -271,16 +271,19 @@ int download(rbffd_ctx* ctx, const T* d, size_t count, std::vector<T>* h, cudaSt
 
 }  // namespace
 
-// Level-0 block records (see Level0Rec) from the host copies of level 0.
+// Block records (see LevelRec) of level l from its host copies.  aux: the
+// level-0 P-node index of each row (l = 0, perm0) or the rows of the finer
+// level below each row (l > 0, the finer level's aggregate offsets).
 template <int W>
-int level0_records(rbffd_ctx* ctx, Amg* a, const AmgLevel& g, const std::vector<int32_t>& hidx,
-                   const std::vector<float>& hval, const std::vector<float>& hd,
-                   const std::vector<float>& hwd, const std::vector<int32_t>& cptr,
-                   const std::vector<int32_t>& perm0, int64_t nc, cudaStream_t st) {
+int level_records(rbffd_ctx* ctx, Amg* a, int l, const AmgLevel& g,
+                  const std::vector<int32_t>& hidx, const std::vector<float>& hval,
+                  const std::vector<float>& hd, const std::vector<float>& hwd,
+                  const std::vector<int32_t>& cptr, const std::vector<int32_t>& aux, int64_t nc,
+                  cudaStream_t st) {
   const int64_t nrec = (nc + kRecAggs - 1) / kRecAggs;
-  std::vector<Level0Rec<W>> recs((size_t)nrec);
+  std::vector<LevelRec<W>> recs((size_t)nrec);
   for (int64_t b = 0; b < nrec; ++b) {
-    Level0Rec<W>& R = recs[(size_t)b];
+    LevelRec<W>& R = recs[(size_t)b];
     memset(&R, 0, sizeof(R));
     const int64_t I0 = b * kRecAggs, I1 = std::min<int64_t>(I0 + kRecAggs, nc);
     const int64_t f0 = cptr[I0], f1 = cptr[I1];
@@ -301,15 +304,17 @@ int level0_records(rbffd_ctx* ctx, Amg* a, const AmgLevel& g, const std::vector<
       }
       R.diag[r] = in ? hd[i] : 0.f;
       R.wd[r] = in ? hwd[i] : 0.f;
-      R.perm0[r] = in ? perm0[i] : 0;
     }
+    // aux: nrows entries on level 0, nrows + 1 above it (children of the last row end there)
+    const int naux = l == 0 ? R.nrows : R.nrows + 1;
+    for (int r = 0; r < naux; ++r) R.aux[r] = aux[(size_t)(f0 + r)];
   }
-  std::vector<unsigned char> bytes(sizeof(Level0Rec<W>) * (size_t)nrec);
+  std::vector<unsigned char> bytes(sizeof(LevelRec<W>) * (size_t)nrec);
   memcpy(bytes.data(), recs.data(), bytes.size());
-  const int rc = upload(ctx, a, bytes, &a->rec0, st);
+  const int rc = upload(ctx, a, bytes, &a->rec[l], st);
   if (rc) return rc;
-  a->rec0_w = W;
-  a->rec0_n = nrec;
+  a->rec_w[l] = W;
+  a->rec_n[l] = nrec;
   return RBFFD_OK;
 }
 
@@ -432,11 +437,12 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
         (rc = upload(ctx, a, hd, &g.diag, st)) || (rc = upload(ctx, a, hwd, &g.wd, st)) ||
         (rc = upload(ctx, a, cptrs[l], &g.cptr, st)))
       return fail(rc);
-    if (l == 0 && width <= 16) {
-      rc = width <= 8 ? level0_records<8>(ctx, a, g, hidx, hval, hd, hwd, cptrs[0], oldi[0],
-                                          L[1].n, st)
-                      : level0_records<16>(ctx, a, g, hidx, hval, hd, hwd, cptrs[0], oldi[0],
-                                           L[1].n, st);
+    if (width <= 16) {
+      const std::vector<int32_t>& aux = l == 0 ? oldi[0] : cptrs[l - 1];
+      rc = width <= 8 ? level_records<8>(ctx, a, l, g, hidx, hval, hd, hwd, cptrs[l], aux,
+                                         L[l + 1].n, st)
+                      : level_records<16>(ctx, a, l, g, hidx, hval, hd, hwd, cptrs[l], aux,
+                                          L[l + 1].n, st);
       if (rc) return fail(rc);
     }
   }

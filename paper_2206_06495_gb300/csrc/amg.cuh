@@ -55,24 +55,26 @@ struct AmgLevel {
   float* z = nullptr;      // level result (after the post-smoothing sweep)
 };
 
-// Level-0 block records.  The level-0 restriction gives each block the
-// kRecAggs consecutive aggregates 64 b .. 64 b + 63 of level 1, whose rows are
-// the consecutive level-0 rows f0 .. f0 + nrows - 1 (at most kRecRows).  The
-// record of block b holds what is static about those rows (graph row, its
-// diagonal and Jacobi weight, P-node index) in the layout one bulk copy
-// stages into shared memory; the level-0 sweep takes the same blocks.
+// Block records of a level.  The restriction of level l gives each block the
+// kRecAggs consecutive aggregates 64 b .. 64 b + 63 of level l + 1, whose rows
+// are the consecutive level-l rows f0 .. f0 + nrows - 1 (at most kRecRows).
+// The record of block b holds what is static about those rows (graph row, its
+// diagonal and Jacobi weight, and aux: on level 0 the P-node index of each
+// row, above it the first row on level l - 1 of each row's aggregate, nrows + 1
+// entries) in the layout one bulk copy stages into shared memory; the sweep
+// of the level takes the same blocks.
 constexpr int kRecAggs = 64;
 constexpr int kRecRows = 256;
 
 template <int W>
-struct Level0Rec {
+struct LevelRec {
   int32_t f0, nrows, nagg, pad;
   int32_t off[kRecAggs + 4];  // aggregate I = 64 b + t: rows f0 + off[t] .. f0 + off[t+1] - 1
   int32_t idx[W * kRecRows];  // slot s of row f0 + r at [s * kRecRows + r]
   float val[W * kRecRows];
   float diag[kRecRows];
   float wd[kRecRows];
-  int32_t perm0[kRecRows];
+  int32_t aux[kRecRows + 4];
 };
 
 struct Amg {
@@ -89,9 +91,10 @@ struct Amg {
   double *zpd = nullptr, *zsd = nullptr;  // the same for FP64 solves
   double inv_ces = 0.0;
   double inv_R = 0.0;
-  unsigned char* rec0 = nullptr;  // level-0 block records (Level0Rec<rec0_w>), or null
-  int rec0_w = 0;                 // their slot count: 8 or 16 (level-0 width at most that)
-  int64_t rec0_n = 0;             // number of records (blocks of kRecAggs aggregates)
+  // block records of each level with a restriction (LevelRec<rec_w[l]>), or null
+  unsigned char* rec[kAmgMaxLevels] = {};
+  int rec_w[kAmgMaxLevels] = {};      // slot count: 8 or 16 (the level's width at most that)
+  int64_t rec_n[kAmgMaxLevels] = {};  // number of records (blocks of kRecAggs aggregates)
   std::vector<int> sizes;  // rows per level (host copy, for reports)
   std::vector<void*> allocs;
 };

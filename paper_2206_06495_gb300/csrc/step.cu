@@ -792,19 +792,19 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Level 0 from block records (Level0Rec): a block stages the record of its
-// 64 aggregates with one bulk copy (bounded wait; a copy that does not land
-// sets *err and ends the block's work), then runs the same arithmetic in the
-// same order as k_pc_restrict / k_pc_up on those rows.
+// Levels from block records (LevelRec): a block stages the record of its 64
+// aggregates with one bulk copy (bounded wait; a copy that does not land sets
+// the solve's stage error and ends the block's work), then runs the same
+// arithmetic in the same order as k_pc_restrict / k_pc_up on those rows.
 static_assert(kRB == kRecAggs && kThreads == kRecRows, "level-0 record shape");
 
 template <int W>
-__device__ __forceinline__ bool stage_rec(Level0Rec<W>* rec, uint64_t* bar, uint32_t& phase,
+__device__ __forceinline__ bool stage_rec(LevelRec<W>* rec, uint64_t* bar, uint32_t& phase,
                                           const unsigned char* __restrict__ recs, int64_t b,
                                           int* err) {
   __syncthreads();  // every thread is done with the previous record
   if (threadIdx.x == 0) {
-    constexpr uint32_t bytes = (uint32_t)sizeof(Level0Rec<W>);
+    constexpr uint32_t bytes = (uint32_t)sizeof(LevelRec<W>);
     mbar_expect_tx(bar, bytes);
     bulk_g2s(rec, recs + b * (int64_t)bytes, bytes, bar);
   }
@@ -825,7 +825,7 @@ __device__ __forceinline__ bool stage_rec(Level0Rec<W>* rec, uint64_t* bar, uint
 
 // sum_s val[s] * get(idx[s]) over a record row's slots (slot s < width)
 template <int W, typename Get>
-__device__ __forceinline__ float rec_row(const Level0Rec<W>& R, int width, int r, Get get) {
+__device__ __forceinline__ float rec_row(const LevelRec<W>& R, int width, int r, Get get) {
   float ax = 0.f;
 #pragma unroll
   for (int s = 0; s < W; ++s)
@@ -835,10 +835,10 @@ __device__ __forceinline__ float rec_row(const Level0Rec<W>& R, int width, int r
 
 template <int W>
 __global__ void __launch_bounds__(kThreads)
-    k_pc_restrict0(AmgLevel F, int64_t nrec, const unsigned char* __restrict__ recs,
+    k_pc_restrict_rec(AmgLevel F, int64_t nrec, const unsigned char* __restrict__ recs,
                    float* __restrict__ rc, KScal* sc) {
   if (sc->done) return;
-  __shared__ __align__(128) Level0Rec<W> rec;
+  __shared__ __align__(128) LevelRec<W> rec;
   __shared__ float res[kThreads];
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(kThreads)
   if (sc->done) return;
   constexpr int NU_ = 1;
   __shared__ double sh[NU_ * kThreads];
-  __shared__ __align__(128) Level0Rec<W> rec;
+  __shared__ __align__(128) LevelRec<W> rec;
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
@@ -889,12 +889,38 @@ __global__ void __launch_bounds__(kThreads)
       const float xi = F.x[i];
       const float ax = rec.diag[t] * xi + rec_row<W>(rec, F.width, t, [&](int32_t j) { return F.x[j]; });
       const float zi = xi + rec.wd[t] * (F.r[i] - ax);
-      z[rec.perm0[t]] = (TZ)zi;  // back to P-node order
+      z[rec.aux[t]] = (TZ)zi;  // back to P-node order
       part += zi;
     }
   }
   double v[NU_] = {(double)part};
   grid_reduce<NU_>(v, gr, sh, [&](double* t2) { pc_finish(sc, which, t2[0], inv_ces, inv_R); });
+}
+
+// levels above 0: the post-smoothing sweep adds its result, scaled, to the
+// finer level's rows of each row's aggregate
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+    k_pc_up_rec(AmgLevel F, AmgLevel Fine, int64_t nrec, const unsigned char* __restrict__ recs,
+                KScal* sc) {
+  if (sc->done) return;
+  __shared__ __align__(128) LevelRec<W> rec;
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  const int t = threadIdx.x;
+  for (int64_t b = blockIdx.x; b < nrec; b += gridDim.x) {
+    if (!stage_rec<W>(&rec, &bar, phase, recs, b, &sc->stage_err)) break;
+    if (t < rec.nrows) {
+      const int64_t i = (int64_t)rec.f0 + t;
+      const float xi = F.x[i];
+      const float ax = rec.diag[t] * xi + rec_row<W>(rec, F.width, t, [&](int32_t j) { return F.x[j]; });
+      const float zi = xi + rec.wd[t] * (F.r[i] - ax);
+      const float v = kAmgCoarseScale * zi;
+      for (int32_t c = rec.aux[t]; c < rec.aux[t + 1]; ++c) Fine.x[c] += v;
+    }
+  }
 }
 
 // one-level hierarchy: the lifted coarse solve is already mean-free
@@ -1810,11 +1836,13 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
     const AmgLevel& F = a->lev[l];
     const int gb = (int)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)G * 2, (a->lev[l + 1].n + kRB - 1) / kRB));
-    if (l == 0 && a->rec0) {
-      if (a->rec0_w == 8)
-        k_pc_restrict0<8><<<gb, kThreads, 0, st>>>(F, a->rec0_n, a->rec0, a->lev[1].r, P->sc);
+    if (a->rec[l]) {
+      if (a->rec_w[l] == 8)
+        k_pc_restrict_rec<8><<<gb, kThreads, 0, st>>>(F, a->rec_n[l], a->rec[l],
+                                                      a->lev[l + 1].r, P->sc);
       else
-        k_pc_restrict0<16><<<gb, kThreads, 0, st>>>(F, a->rec0_n, a->rec0, a->lev[1].r, P->sc);
+        k_pc_restrict_rec<16><<<gb, kThreads, 0, st>>>(F, a->rec_n[l], a->rec[l],
+                                                       a->lev[l + 1].r, P->sc);
       continue;
     }
     switch (width_bucket(F.width)) {
@@ -1830,6 +1858,16 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
                                                              a->nlev >= 2 ? 1 : 0, P->sc);
   for (int l = a->nlev - 2; l >= 1; --l) {
     const AmgLevel& F = a->lev[l];
+    if (a->rec[l]) {
+      const int gbr = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)G * 2, a->rec_n[l]));
+      if (a->rec_w[l] == 8)
+        k_pc_up_rec<8><<<gbr, kThreads, 0, st>>>(F, a->lev[l - 1], a->rec_n[l], a->rec[l],
+                                                 P->sc);
+      else
+        k_pc_up_rec<16><<<gbr, kThreads, 0, st>>>(F, a->lev[l - 1], a->rec_n[l], a->rec[l],
+                                                  P->sc);
+      continue;
+    }
     const int gb = grid_for(F.n);
 #define RBFFD_UP(Wb)                                                                         \
   k_pc_up<true, false, float, Wb><<<gb, kThreads, 0, st>>>(F, a->lev[l - 1], F.z, nullptr,   \
@@ -1842,13 +1880,13 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
     }
 #undef RBFFD_UP
   }
-  if (a->nlev >= 2 && a->rec0) {
-    const int gu = (int)std::max<int64_t>(1, std::min<int64_t>(G, a->rec0_n));
-    if (a->rec0_w == 8)
-      k_pc_up0<TV, 8><<<gu, kThreads, 0, st>>>(a->lev[0], a->rec0_n, a->rec0, zout, P->sc, P->gr,
-                                                which, a->inv_ces, a->inv_R);
+  if (a->nlev >= 2 && a->rec[0]) {
+    const int gu = (int)std::max<int64_t>(1, std::min<int64_t>(G, a->rec_n[0]));
+    if (a->rec_w[0] == 8)
+      k_pc_up0<TV, 8><<<gu, kThreads, 0, st>>>(a->lev[0], a->rec_n[0], a->rec[0], zout, P->sc,
+                                                P->gr, which, a->inv_ces, a->inv_R);
     else
-      k_pc_up0<TV, 16><<<gu, kThreads, 0, st>>>(a->lev[0], a->rec0_n, a->rec0, zout, P->sc,
+      k_pc_up0<TV, 16><<<gu, kThreads, 0, st>>>(a->lev[0], a->rec_n[0], a->rec[0], zout, P->sc,
                                                  P->gr, which, a->inv_ces, a->inv_R);
   } else if (a->nlev >= 2) {
     const AmgLevel& F = a->lev[0];
