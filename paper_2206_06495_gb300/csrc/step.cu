@@ -914,11 +914,18 @@ __global__ void __launch_bounds__(kThreads)
     if (!stage_rec<W>(&rec, &bar, phase, recs, b, &sc->stage_err)) break;
     if (t < rec.nrows) {
       const int64_t i = (int64_t)rec.f0 + t;
+      // the finer rows this row corrects (at most four), read with the gathers
+      const int32_t c0 = rec.aux[t], c1 = rec.aux[t + 1];
+      float xf[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xf[q] = c0 + q < c1 ? Fine.x[c0 + q] : 0.f;
       const float xi = F.x[i];
       const float ax = rec.diag[t] * xi + rec_row<W>(rec, F.width, t, [&](int32_t j) { return F.x[j]; });
       const float zi = xi + rec.wd[t] * (F.r[i] - ax);
       const float v = kAmgCoarseScale * zi;
-      for (int32_t c = rec.aux[t]; c < rec.aux[t + 1]; ++c) Fine.x[c] += v;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < c1) Fine.x[c0 + q] = xf[q] + v;
     }
   }
 }
