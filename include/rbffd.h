@@ -210,9 +210,11 @@ int rbffd_apply_op_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, i
  * tol             relative residual of both implicit solves (scaled systems)
  * inner_tol       MIXED only: relative tolerance of each FP32 inner solve
  * max_iter        cap on Krylov iterations per solve (inner iterations summed)
- * km_mode         boundary value of the intermediate velocity (Kim & Moin):
- *                 0 = wall data only, 1 = wall data + dt * tangential part of
- *                 D^(V,P) p~_j (default), 2 = + dt * the full D^(V,P) p~_j
+ * km_mode         boundary value of the intermediate velocity (Kim & Moin,
+ *                 end of Section 3): 2 = wall data + dt * D^(V,P) p~_j, both
+ *                 components as printed (the binding's default); 1 = wall
+ *                 data + dt * the component of D^(V,P) p~_j along the wall
+ *                 tangent; 0 = wall data only
  * overwrite_bc    1 = set wall V-nodes to the wall data after the correction
  * profile         1 = time every SpMV launch of the pressure solves with CUDA
  *                 events on `stream` (reported in rbffd_stats); 0 = off
@@ -288,7 +290,10 @@ typedef struct rbffd_stats {
  *  2. (I - a D^(V,V)_Lap) u** = (I + a D^(V,V)_Lap) u* (Eq. u_ss), wall rows = identity
  *     with the Kim & Moin value (km_mode); likewise v**
  *  3. F = D^(P,V)_x u** + D^(P,V)_y v** (Eq. divergence); D^(P,P)_Lap p~ = F/dt
- *     (Eq. pressure_Poisson) with Neumann boundary rows; p~ has zero mean
+ *     (Eq. pressure_Poisson) at every interior P-node, homogeneous Neumann
+ *     rows at boundary P-nodes; the constant null space is removed by the
+ *     bordered system [L e; 1^T 0] with e = 1 on the boundary rows (the
+ *     multiplier takes up the incompatibility there); p~ has zero mean
  *  4. p = p~ - a D^(P,P)_Lap p~;  u_{j+1} = u** - dt D^(V,P)_x p~, v likewise
  *     (Eq. velocity_next_timestep); wall nodes set to the wall data
  * gu, gv: device double[N], wall data g_{j+1} (used at wall V-nodes only),

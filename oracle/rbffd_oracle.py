@@ -19,7 +19,7 @@ nodes") in the plainest form that numpy/scipy allow:
     the Kim & Moin intermediate-velocity boundary values.  The implicit
     matrices are LU-factorised once, as in the paper (end of Section 3).
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
   R1 local coordinates: shift by the stencil centre, scale by the largest
      centre-to-node distance s; weights of first derivatives are divided by s
      and of the Laplacian by s^2 afterwards.
@@ -31,15 +31,20 @@ Readings of points the paper leaves open (each one is listed in the design doc):
      by its n-1 nearest interior P-nodes (a one-sided stencil that does not
      lean on the other wall nodes, which carry no normal information); the
      constant null space is removed by bordering
-     [L e; 1^T 0][p; lam] = [b; 0], where e is 1 on interior P-rows and 0 on
-     boundary rows (the multiplier absorbs the incompatibility of the
-     non-symmetric L in the interior rows only; the Neumann rows stay
-     homogeneous).  The result is the mean-zero pressure correction.
+     [L e; 1^T 0][p; lam] = [b; 0], where e is 1 on boundary P-rows and 0 on
+     interior rows: every interior row is Eq. pressure_Poisson exactly, and
+     the multiplier absorbs the incompatibility of the non-symmetric L as a
+     uniform normal derivative on the Neumann rows.  (With e on the interior
+     rows instead, each projection leaves a uniform interior divergence
+     lam*dt that the next right side carries again, so it accumulates over
+     the run; on the boundary rows it does not.)  The result is the
+     mean-zero pressure correction.
   R5 boundary V-rows of the Crank-Nicolson solve are identity rows whose
-     right-hand side is the Kim & Moin value: the wall data g_{j+1} plus
-     dt times the tangential component of D^(VP) p~_j along the wall
-     (the normal component is not added: it is zero under the Neumann
-     pressure condition of the continuous problem).
+     right-hand side is the Kim & Moin value of the end of Section 3: the
+     wall data g_{j+1} plus dt D^(VP) p~_j, both components as printed
+     (km_mode 2, the default).  km_mode 1 adds only the component along the
+     wall tangent (the normal one vanishes for the continuous problem under
+     the Neumann pressure condition), km_mode 0 adds nothing.
   R6 after the velocity correction, boundary V-nodes are overwritten with
      g_{j+1} (switchable).
   R7 AB2 at the first step uses C_{-1} = C_0; the flow starts from rest with
@@ -60,11 +65,18 @@ ALL_OPS = (OP_INTERP, OP_DX, OP_DY, OP_LAP)
 # --------------------------------------------------------------------------
 # Stencils (Section 2.2: row i uses the n nearest beta-nodes of alpha-node i)
 # --------------------------------------------------------------------------
-def knn(ax, ay, bx, by, k: int, chunk: int = 256, beta_mask=None, alpha_self=None) -> np.ndarray:
+def knn(ax, ay, bx, by, k: int, chunk: int = 256, beta_mask=None, alpha_self=None,
+        method: str = "auto") -> np.ndarray:
     """Indices of the k nearest beta-nodes of every alpha-node, nearest first.
 
-    Brute force over all beta-nodes; ordering key (d^2, index) with
-    d^2 = dx*dx + dy*dy evaluated one rounded operation at a time.
+    The definition is brute force over all beta-nodes with the ordering key
+    (d^2, index), d^2 = dx*dx + dy*dy evaluated one rounded operation at a
+    time (R3).  For large sets ("auto" above 4e7 node pairs, or "tree") a k-d
+    tree proposes k + 12 candidates per alpha-node; those are ordered by the
+    same key, and a row is kept only when its k-th key is below every key the
+    tree did not return (checked against the farthest candidate with a
+    relative margin of 1e-12); the other rows fall back to brute force.  The
+    result is identical to the brute-force one.
     beta_mask: only beta-nodes with a nonzero mask are candidates.
     alpha_self: beta index of each alpha-node; when given, slot 0 is that
     node and the other k-1 slots are the nearest masked beta-nodes.
@@ -82,10 +94,18 @@ def knn(ax, ay, bx, by, k: int, chunk: int = 256, beta_mask=None, alpha_self=Non
     out = np.empty((ax.size, k), np.int64)
     if alpha_self is not None:
         out[:, 0] = np.asarray(alpha_self)
-        inner = knn(ax, ay, bx, by, kk, chunk, beta_mask, None) if kk > 0 else None
         if kk > 0:
-            out[:, 1:] = inner
+            out[:, 1:] = knn(ax, ay, bx, by, kk, chunk, beta_mask, None, method)
         return out
+    if method == "tree" or (method == "auto" and ax.size * nb > 4e7):
+        return _knn_tree(ax, ay, bx, by, k, allowed, chunk)
+    return _knn_brute(ax, ay, bx, by, k, allowed, chunk)
+
+
+def _knn_brute(ax, ay, bx, by, k, allowed, chunk=256):
+    """Brute-force k nearest: every beta-node's key, the k smallest kept."""
+    nb = bx.size
+    out = np.empty((ax.size, k), np.int64)
     cols = np.arange(nb)
     for s in range(0, ax.size, chunk):
         dx = bx[None, :] - ax[s:s + chunk, None]
@@ -98,6 +118,30 @@ def knn(ax, ay, bx, by, k: int, chunk: int = 256, beta_mask=None, alpha_self=Non
             cand = np.nonzero(row <= kth)[0]
             order = np.lexsort((cols[cand], row[cand]))[:k]
             out[s + r] = cand[order]
+    return out
+
+
+def _knn_tree(ax, ay, bx, by, k, allowed, chunk=256):
+    """k nearest from k-d tree candidates, exact under the (d^2, index) key."""
+    from scipy.spatial import cKDTree
+    cand_ids = np.nonzero(allowed)[0]
+    kq = min(k + 12, cand_ids.size)
+    tree = cKDTree(np.stack([bx[cand_ids], by[cand_ids]], -1))
+    _, nn = tree.query(np.stack([ax, ay], -1), k=kq)
+    nn = cand_ids[np.asarray(nn).reshape(ax.size, kq)]
+    dx = bx[nn] - ax[:, None]
+    dy = by[nn] - ay[:, None]
+    d2 = dx * dx + dy * dy
+    order = np.lexsort((nn, d2), axis=-1)
+    nn = np.take_along_axis(nn, order, -1)
+    d2 = np.take_along_axis(d2, order, -1)
+    out = nn[:, :k].copy()
+    if kq < cand_ids.size:
+        # every beta-node the tree left out is at least as far as its farthest
+        # candidate; a row is exact when its k-th key is strictly closer
+        bad = np.nonzero(~(d2[:, k - 1] < d2[:, -1] * (1.0 - 1e-12)))[0]
+        if bad.size:
+            out[bad] = _knn_brute(ax[bad], ay[bad], bx, by, k, allowed, chunk)
     return out
 
 
@@ -313,13 +357,13 @@ def poisson_matrix(ops: Operators, p_boundary, p_nx, p_ny) -> sp.csr_matrix:
 
     L = D^(P,P)_Lap (Eq. pressure_Poisson) with every boundary P-row replaced
     by n_x D_x + n_y D_y on the one-sided Neumann stencil of that node (R4);
-    e = indicator of interior P-rows.
+    e = indicator of the boundary P-rows.
     """
     M = ops.pp_lap.shape[0]
     bnd = sp.diags(p_boundary.astype(float))
     inn = sp.diags((~p_boundary).astype(float))
     L = inn @ ops.pp_lap + bnd @ (sp.diags(p_nx) @ ops.pn_x + sp.diags(p_ny) @ ops.pn_y)
-    e = sp.csr_matrix((~p_boundary).astype(float)[:, None])
+    e = sp.csr_matrix(p_boundary.astype(float)[:, None])
     one = sp.csr_matrix(np.ones((1, M)))
     return sp.bmat([[L, e], [one, None]], format="csc")
 
@@ -347,8 +391,12 @@ class FractionalStep:
     """Three-stage semi-implicit step of Section 3 on a staggered node set."""
 
     def __init__(self, nodes, Re: float, dt: float, k: int = 28, m: int = 7,
-                 q: int = 3, ops: Operators | None = None, overwrite_bc: bool = True):
+                 q: int = 3, ops: Operators | None = None, overwrite_bc: bool = True,
+                 km_mode: int = 2):
+        if km_mode not in (0, 1, 2):
+            raise ValueError("km_mode is 0, 1 or 2")
         self.nodes = nodes
+        self.km_mode = km_mode
         self.Re = float(Re)
         self.dt = float(dt)
         self.a = self.dt / (2.0 * self.Re)
@@ -421,11 +469,16 @@ class FractionalStep:
         # stage 2: Crank-Nicolson viscous step, Kim & Moin boundary values
         ru = us + a * (o.vv_lap @ us)
         rv = vs + a * (o.vv_lap @ vs)
+        # Kim & Moin: u** = u_{j+1} + dt D^(V,P) p~_j on the wall (R5)
         gpx = o.vp_x @ st.pt
         gpy = o.vp_y @ st.pt
-        gt = self.tx * gpx + self.ty * gpy  # tangential pressure-gradient
-        ru[vb] = gu[vb] + dt * (gt * self.tx)[vb]
-        rv[vb] = gv[vb] + dt * (gt * self.ty)[vb]
+        if self.km_mode == 1:  # the component along the wall tangent only
+            gt = self.tx * gpx + self.ty * gpy
+            gpx, gpy = gt * self.tx, gt * self.ty
+        elif self.km_mode == 0:
+            gpx, gpy = 0.0 * gpx, 0.0 * gpy
+        ru[vb] = gu[vb] + dt * gpx[vb]
+        rv[vb] = gv[vb] + dt * gpy[vb]
         uss = self.H_lu.solve(ru)
         vss = self.H_lu.solve(rv)
         F = o.pv_x @ uss + o.pv_y @ vss
@@ -443,7 +496,8 @@ class AdjointState:
     pt: np.ndarray
 
 
-def adjoint_step(fs: "FractionalStep", st_in: FlowState, lam: AdjointState, km_mode: int = 1):
+def adjoint_step(fs: "FractionalStep", st_in: FlowState, lam: AdjointState,
+                 km_mode: int | None = None):
     """Reverse-mode derivative of one step of FractionalStep.step.
 
     st_in: the forward state the step started from (step j); lam: adjoints of
@@ -453,6 +507,7 @@ def adjoint_step(fs: "FractionalStep", st_in: FlowState, lam: AdjointState, km_m
     factors of H^T and of the bordered matrix's transpose.
     """
     o, dt, a = fs.ops, fs.dt, fs.a
+    km_mode = fs.km_mode if km_mode is None else km_mode
     w = fs.vb
     inner = ~w
     N = st_in.u.size

@@ -15,13 +15,14 @@
 //   viscous:  H x = b, H = I - a_i D^(V,V)_Lap, a_i = dt/(2 Re) inside and 0
 //             on wall rows, which are identity rows (Eq. u_ss);
 //   pressure: S (L - e 1^T) x = S b, L = D^(P,P)_Lap inside and the Neumann
-//             row n_x D_x + n_y D_y on boundary rows, e = indicator of interior
-//             rows, S = diag(1/L_ii) (1/sum_j |L_ij| on a row whose diagonal
-//             vanishes).  L annihilates constants, so the rank-one term
+//             row n_x D_x + n_y D_y on boundary rows, e = indicator of the
+//             boundary rows, S = diag(1/L_ii) (1/sum_j |L_ij| on a row whose
+//             diagonal vanishes).  L annihilates constants, so the rank-one term
 //             fixes the constant mode: x = p~ + c 1 for the mean-zero solution
 //             p~ of the bordered system [L e; 1^T 0] (the multiplier c absorbs
-//             the incompatibility of the non-symmetric L in the interior rows),
-//             and p~ = x - mean(x).
+//             the incompatibility of the non-symmetric L as a uniform normal
+//             derivative on the Neumann rows, so every interior row is
+//             Eq. pressure_Poisson exactly), and p~ = x - mean(x).
 // FP64 precision: BiCGSTAB in FP64.  MIXED: FP64 iterative refinement whose
 // corrections come from FP32 solves on FP32 copies of the scaled operators.
 // Pressure solves are right-preconditioned by the multigrid V-cycle of
@@ -1460,7 +1461,7 @@ __global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __r
         Lidx[s * ld + i] = (int32_t)i;
         Lw[s * ld + i] = s == 0 ? 1.0 : 0.0;
       }
-      es[i] = 0.0;
+      es[i] = -1.0;
       scale[i] = 1.0;
       continue;
     }
@@ -1482,7 +1483,7 @@ __global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __r
     }
     const double sc = diag != 0.0 ? 1.0 / diag : (sabs > 0.0 ? 1.0 / sabs : 1.0);
     for (int s = 0; s < k; ++s) Lw[s * ld + i] *= sc;
-    es[i] = bnd ? 0.0 : -sc;
+    es[i] = bnd ? -sc : 0.0;
     scale[i] = sc;
   }
 }
@@ -2614,7 +2615,7 @@ __global__ void k_adj_setup_vec(int64_t M, const uint8_t* __restrict__ p_bc,
                                 double* __restrict__ inv_scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
        i += (int64_t)gridDim.x * blockDim.x) {
-    e[i] = p_bc[i] ? 0.0 : 1.0;
+    e[i] = p_bc[i] ? 1.0 : 0.0;  // the bordering vector: boundary rows
     inv_scale[i] = 1.0 / scale[i];
   }
 }
@@ -2687,11 +2688,12 @@ __global__ void k_adj_div(int64_t N, TEll t, const double* __restrict__ PxT,
   }
 }
 
-__global__ void k_adj_ze(int64_t M, const double* __restrict__ z, const double* __restrict__ e,
+// adjoint of b = F/dt on the interior rows (the Neumann rows' right side is 0)
+__global__ void k_adj_ze(int64_t M, const double* __restrict__ z, const uint8_t* __restrict__ p_bc,
                          double inv_dt, double* __restrict__ ze) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
        j += (int64_t)gridDim.x * blockDim.x)
-    ze[j] = z[j] * e[j] * inv_dt;
+    ze[j] = p_bc[j] ? 0.0 : z[j] * inv_dt;
 }
 
 // wall rows of the viscous right side: wall data and the Kim & Moin term
@@ -2887,7 +2889,7 @@ int build_adjoint_plan(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, cudaStr
   TRYA(t_weights(ctx, a, a->tvp, f.vp_dy, f.ld_v, nullptr, nullptr, 1.0, &a->GyT, G, st));
   // S L^T: unscale the forward rows (1/s_row), scale the transposed rows (s_col)
   TRYA(t_weights(ctx, a, a->tl, P->Lw, f.ld_p, inv_scale, P->scale, 1.0, &a->LT, G, st));
-  // rank-one column -gamma S 1 with gamma = 1/|sum over interior rows of s|
+  // rank-one column -gamma S 1 with gamma = 1/|sum over boundary rows of s|
   k_sum<double><<<G, kThreads, 0, st>>>(P->scale, f.M, P->gr, P->dscal, a->e);
   k_adj_es<<<G, 256, 0, st>>>(f.M, P->scale, P->dscal, a->es_t);
   TRYA(check_cuda(ctx, cudaGetLastError(), "adjoint set-up"));
@@ -2952,7 +2954,7 @@ int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* fp, const rbffd_state* s, rbff
     return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
                      "adjoint pressure solve: relative residual %.3e after %d iterations",
                      pr.relres, pr.iters);
-  k_adj_ze<<<G, kThreads, 0, st>>>(f.M, A->z, A->e, 1.0 / f.dt, A->rhs);
+  k_adj_ze<<<G, kThreads, 0, st>>>(f.M, A->z, f.p_bc, 1.0 / f.dt, A->rhs);
   k_adj_div<<<G, kThreads, 0, st>>>(f.N, A->tpv, A->PxT, A->PyT, A->rhs, A->luss, A->lvss);
   // transposed viscous solves, two right sides; start from the right sides
   rc = check_cuda(ctx, cudaMemcpyAsync(A->lru, A->luss, sizeof(double) * f.N,

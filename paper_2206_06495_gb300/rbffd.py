@@ -276,7 +276,7 @@ class Flow:
     tol: float = 1e-12
     inner_tol: float = 5e-3
     max_iter: int = 20000
-    km_mode: int = 1
+    km_mode: int = 2
     overwrite_bc: int = 1
     profile: int = 0
     precond: int = 1

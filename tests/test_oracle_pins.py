@@ -74,6 +74,31 @@ def test_knn_brute_force_small_random():
         assert list(idx[i]) == [j for _, j in pairs[:9]]
 
 
+def test_knn_tree_path_equals_brute_force():
+    """The k-d tree candidate path of the oracle's k-NN gives exactly the
+    brute-force stencils: random points, a masked candidate set, one-sided
+    stencils (alpha_self) and an exact lattice full of distance ties."""
+    rng = np.random.default_rng(11)
+    bx, by = rng.random(2500), rng.random(2500)
+    ax, ay = rng.random(600), rng.random(600)
+    for k in (28, 9):
+        assert np.array_equal(O.knn(ax, ay, bx, by, k, method="tree"),
+                              O.knn(ax, ay, bx, by, k, method="brute"))
+    mask = rng.random(2500) < 0.5
+    assert np.array_equal(O.knn(ax, ay, bx, by, 28, beta_mask=mask, method="tree"),
+                          O.knn(ax, ay, bx, by, 28, beta_mask=mask, method="brute"))
+    selfi = np.arange(40)
+    mask2 = np.ones(2500, bool)
+    mask2[:40] = False
+    assert np.array_equal(
+        O.knn(bx[:40], by[:40], bx, by, 28, beta_mask=mask2, alpha_self=selfi, method="tree"),
+        O.knn(bx[:40], by[:40], bx, by, 28, beta_mask=mask2, alpha_self=selfi, method="brute"))
+    n = 25
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x, y = ii.ravel() * 0.1, jj.ravel() * 0.1
+    assert np.array_equal(O.knn(x, y, x, y, 28, method="tree"), O.knn(x, y, x, y, 28, method="brute"))
+
+
 # ---------------------------------------------------------------- weights
 @pytest.mark.parametrize("q", [3, 4])
 def test_polynomial_exactness_all_grids(cavity20, q):
@@ -181,7 +206,11 @@ def test_modified_wavenumber_within_paper_bound():
     """P5 with the paper's printed bound: at k~ Delta r = sqrt(2) the radial
     modified wavenumber of the 28-point (7, 3) operators deviates from k~ by
     at most 1.5 % over wave angles (Section 6), on the collocated grids.
-    Delta r: mean distance to the 6 nearest same-grid nodes (reading R10)."""
+    Delta r: mean distance to the 6 nearest same-grid nodes (reading R10).
+    The paper's bound is read over its grid-wide diagram, so the node mean is
+    held to it; single stencils of these jittered lattices (rougher than the
+    paper's mesh) spread wider, and the 90th percentile over nodes is held
+    to twice the bound so that no stencil family can hide in the mean."""
     bound = _golden("mw_deviation_bounds.txt")["all_angles_bound"]
     nd = ns.jittered_cavity(40, 0)
     h = nd.h
@@ -193,10 +222,12 @@ def test_modified_wavenumber_within_paper_bound():
             kt = np.sqrt(2.0) / dr
             kx, ky = kt * np.cos(th), kt * np.sin(th)
             ks = O.modified_wavenumber(W[O.OP_DX], W[O.OP_DY], idx, ax, ay, ax, ay, kx, ky)
-            assert np.abs(ks[inner].real / kt - 1).mean() < bound
+            d1 = np.abs(ks[inner].real / kt - 1)
+            assert d1.mean() < bound and np.percentile(d1, 90) < 2 * bound
             ph = np.exp(1j * (kx * ax + ky * ay))
             k2 = -(W[O.OP_LAP] * ph[idx]).sum(1) * np.conj(ph)
-            assert np.abs(k2[inner].real / kt ** 2 - 1).mean() < bound
+            d2 = np.abs(k2[inner].real / kt ** 2 - 1)
+            assert d2.mean() < bound and np.percentile(d2, 90) < 2 * bound
         # and the spectral limit: k*/k~ -> 1 as k~ Delta r -> 0
         kt = 0.05 / dr
         ks = O.modified_wavenumber(W[O.OP_DX], W[O.OP_DY], idx, ax, ay, ax, ay, kt, 0.0)
@@ -210,9 +241,9 @@ def _tg(x, y, t, Re):
             -0.25 * (np.cos(2 * x) + np.cos(2 * y)) * e * e)
 
 
-def _tg_run(n, dt, T, Re=10.0):
-    nd = ns.jittered_cavity(n, 0, length=np.pi)
-    fs = O.FractionalStep(nd, Re=Re, dt=dt)
+def _tg_run(n, dt, T, Re=10.0, km_mode=2, ops=None, nd=None):
+    nd = ns.jittered_cavity(n, 0, length=np.pi) if nd is None else nd
+    fs = O.FractionalStep(nd, Re=Re, dt=dt, km_mode=km_mode, ops=ops)
     u0, v0, _ = _tg(nd.vx, nd.vy, 0.0, Re)
     st = fs.initial_state(u0, v0)
     steps = int(round(T / dt))
@@ -239,15 +270,73 @@ def test_taylor_green_spatial_convergence():
     assert ep[-1] < 1e-3 and np.all(ep[1:] < ep[:-1]), ep
 
 
-def test_taylor_green_time_refinement():
-    """Error against a fine-step run on the same nodes falls with dt."""
-    ref = _tg_run(17, 0.000625, 0.2)[1]
-    errs = []
-    for dt in (0.01, 0.005, 0.0025):
-        st = _tg_run(17, dt, 0.2)[1]
-        errs.append(np.abs(st.u - ref.u).max())
-    errs = np.array(errs)
-    assert np.all(errs[:-1] / errs[1:] > 1.8), errs
+TIME_DTS = (0.01, 0.005, 0.0025, 0.00125)
+_time_cache = {}
+
+
+def tg_time_errors(n, km_mode=2):
+    """Velocity errors at T = 0.2 (Re 10) for the steps TIME_DTS against a
+    run with dt = 1.5625e-4 on the same nodes (the time-discretisation error
+    alone).  Cached per (n, km_mode, oracle step function)."""
+    key = (n, km_mode, O.FractionalStep.step, O.FractionalStep.intermediate)
+    if key not in _time_cache:
+        nd = ns.jittered_cavity(n, 0, length=np.pi)
+        ops = O.build_operators(nd)
+        ref = _tg_run(n, 0.00015625, 0.2, km_mode=km_mode, ops=ops, nd=nd)[1]
+        errs = []
+        for dt in TIME_DTS:
+            st = _tg_run(n, dt, 0.2, km_mode=km_mode, ops=ops, nd=nd)[1]
+            errs.append(max(np.abs(st.u - ref.u).max(), np.abs(st.v - ref.v).max()))
+        _time_cache[key] = np.array(errs)
+    return _time_cache[key]
+
+
+def first_order_coefficient(errs):
+    """A of err = A dt + B dt^2 through the two smallest steps."""
+    d1, d2 = TIME_DTS[-2], TIME_DTS[-1]
+    e1, e2 = errs[-2], errs[-1]
+    B = (e1 - 2 * e2) / (d1 * d1 - 2 * d2 * d2)
+    return (e1 - B * d1 * d1) / d1
+
+
+def test_taylor_green_time_order():
+    """App. D: the three-stage step is second order in time.  On a 33 x 33
+    node set the observed order over dt = 1e-2 ... 1.25e-3 is at least 1.8 on
+    every halving (1.87, 1.88, 1.87 when pinned).  Dropping the Kim & Moin
+    wall term makes it first order."""
+    e = tg_time_errors(33)
+    order = np.log2(e[:-1] / e[1:])
+    assert np.all(order >= 1.8), (e, order)
+    assert e[0] < 5e-5, e
+
+
+def test_first_order_time_term_is_a_projection_defect():
+    """Reading of App. D: the printed scheme projects with D^(P,P)_Lap, which
+    differs from D^(P,V) D^(V,P) by the truncation error, so each projection
+    leaves a divergence of order dt times that difference and the scheme
+    carries an O(dt) term.  Its coefficient A (err = A dt + B dt^2) falls at
+    a high power of h (3.3e-4, 7.9e-5, 4.1e-5 on 25^2, 33^2, 41^2 when
+    pinned), so the order on the smallest steps rises toward 2 under
+    refinement (1.54, 1.87, 1.93)."""
+    errs = {n: tg_time_errors(n) for n in (25, 33, 41)}
+    A = [first_order_coefficient(errs[n]) for n in (25, 33, 41)]
+    assert A[1] < A[0] / 3 and A[2] < A[1] / 1.5, A
+    last = [np.log2(errs[n][-2] / errs[n][-1]) for n in (25, 33, 41)]
+    assert last[0] < last[1] < last[2], last
+
+
+def test_kim_moin_modes_agree_and_dropping_the_term_is_first_order():
+    """R5: the wall value of u** with both components of dt D^(V,P) p~_j (the
+    printed formula, km_mode 2) and with the tangential component only
+    (km_mode 1) agree to the spatial truncation level, because the normal
+    component vanishes with the Neumann pressure condition; without the term
+    (km_mode 0) the wall carries an O(dt) slip and the time error is first
+    order and far larger."""
+    e2, e1 = tg_time_errors(33, 2), tg_time_errors(33, 1)
+    assert np.all(np.abs(e1 - e2) < 0.1 * e2), (e1, e2)
+    e0 = tg_time_errors(33, 0)
+    assert np.all(e0 > 20 * e2), (e0, e2)
+    assert np.all(np.log2(e0[:-1] / e0[1:]) < 1.2), e0
 
 
 def test_projection_reduces_divergence():
@@ -316,9 +405,9 @@ def test_cavity_runs_stably_and_keeps_wall_data(cavity20, ops20):
 
 
 # ---------------------------------------------------------------- adjoint
-def _adj_setup(km_mode=1, seed=0):
+def _adj_setup(km_mode=2, seed=0):
     nd = ns.jittered_cavity(12, 4)
-    fs = O.FractionalStep(nd, Re=400.0, dt=2e-3)
+    fs = O.FractionalStep(nd, Re=400.0, dt=2e-3, km_mode=km_mode)
     rng = np.random.default_rng(seed)
     lid = nd.v_wall == ns.WALL_TOP
     g0 = np.zeros(nd.N)
@@ -338,11 +427,12 @@ def _adj_run(fs, nd, gu, u0, steps):
     return sts
 
 
-def test_adjoint_matches_central_differences():
+@pytest.mark.parametrize("km_mode", [2, 1])
+def test_adjoint_matches_central_differences(km_mode):
     """P9: gradients of J = 1/2 sum(u^2 + v^2) after 8 steps with respect to
     per-node lid velocity and to the initial velocity, from the discrete
     adjoint, against central differences of the forward solver (eps 1e-6)."""
-    nd, fs, g0, u0 = _adj_setup()
+    nd, fs, g0, u0 = _adj_setup(km_mode)
     steps = 8
     sts = _adj_run(fs, nd, g0, u0, steps)
     lam = O.AdjointState(sts[-1].u.copy(), sts[-1].v.copy(), np.zeros(nd.N), np.zeros(nd.N),

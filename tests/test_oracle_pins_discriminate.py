@@ -81,3 +81,22 @@ def test_step_mistakes_are_caught_by_taylor_green(monkeypatch, mistake):
         monkeypatch.setattr(O.FractionalStep, "__init__", init)
     with np.errstate(all="ignore"):
         assert _fails(pins.test_taylor_green_spatial_convergence)
+
+
+@pytest.fixture
+def fresh_time_cache():
+    pins._time_cache.clear()
+    yield
+    pins._time_cache.clear()
+
+
+def test_dropped_kim_moin_term_is_caught(monkeypatch, fresh_time_cache):
+    """Dropping the Kim & Moin wall term of u** (end of Section 3) leaves an
+    O(dt) slip at the walls: the App. D time-order pin must fail."""
+    orig_init = O.FractionalStep.__init__
+
+    def init(self, *a, **k):
+        orig_init(self, *a, **k)
+        self.km_mode = 0
+    monkeypatch.setattr(O.FractionalStep, "__init__", init)
+    assert _fails(pins.test_taylor_green_time_order)
