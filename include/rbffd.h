@@ -306,6 +306,19 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
                const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream);
 
 /*
+ * rbffd_debug_set_wait_limit - test hook (no counterpart in the paper): the
+ * number of polls the step's kernels spend on their first wait for a tile or
+ * record staged into shared memory before they give up.  polls = 0 makes
+ * every such wait give up at once; polls < 0 restores the default (2^22).
+ * A kernel that gives up still waits, up to the default limit, for the copies
+ * it issued, sets the solve's error flag and returns; the step then fails
+ * with RBFFD_ERR_CUDA ("... bounded wait") and the context stays usable.
+ * The setting is per process and device (the current one), not per context.
+ * Errors: INVALID_ARG (null ctx), CUDA.
+ */
+int rbffd_debug_set_wait_limit(rbffd_ctx* ctx, int64_t polls);
+
+/*
  * rbffd_probe_fma - measured FMA throughput of the device (no counterpart in
  * the paper): 8 independent FMA chains per thread, 8 blocks of 256 threads
  * per SM, `iters` FMAs per chain, timed with CUDA events on `stream`.

@@ -392,11 +392,18 @@ class FractionalStep:
 
     def __init__(self, nodes, Re: float, dt: float, k: int = 28, m: int = 7,
                  q: int = 3, ops: Operators | None = None, overwrite_bc: bool = True,
-                 km_mode: int = 2):
+                 km_mode: int = 2, viscous_solver: str = "lu"):
+        """viscous_solver: "lu" factorises I - a D_Lap once, as the paper does
+        (end of Section 3); "krylov" solves it at every step with BiCGSTAB to a
+        relative residual of 1e-14 instead (a library routine; for node sets
+        whose LU fill-in is too large: I - a D_Lap is close to I there)."""
         if km_mode not in (0, 1, 2):
             raise ValueError("km_mode is 0, 1 or 2")
+        if viscous_solver not in ("lu", "krylov"):
+            raise ValueError("viscous_solver is 'lu' or 'krylov'")
         self.nodes = nodes
         self.km_mode = km_mode
+        self.viscous_solver = viscous_solver
         self.Re = float(Re)
         self.dt = float(dt)
         self.a = self.dt / (2.0 * self.Re)
@@ -409,7 +416,7 @@ class FractionalStep:
         self.overwrite_bc = overwrite_bc
         self.H = helmholtz_matrix(self.ops, self.vb, self.a)
         self.Pb = poisson_matrix(self.ops, self.pb, nodes.p_nx, nodes.p_ny)
-        self.H_lu = spla.splu(self.H)
+        self.H_lu = spla.splu(self.H) if viscous_solver == "lu" else None
         self.P_lu = spla.splu(self.Pb)
         self._HT_lu = None
         self._PT_lu = None
@@ -479,10 +486,19 @@ class FractionalStep:
             gpx, gpy = 0.0 * gpx, 0.0 * gpy
         ru[vb] = gu[vb] + dt * gpx[vb]
         rv[vb] = gv[vb] + dt * gpy[vb]
-        uss = self.H_lu.solve(ru)
-        vss = self.H_lu.solve(rv)
+        uss = self.solve_viscous(ru)
+        vss = self.solve_viscous(rv)
         F = o.pv_x @ uss + o.pv_y @ vss
         return cu, cv, uss, vss, F
+
+    def solve_viscous(self, r):
+        """(I - a D^(V,V)_Lap) x = r with identity wall rows (Eq. u_ss)."""
+        if self.H_lu is not None:
+            return self.H_lu.solve(r)
+        x, info = spla.bicgstab(self.H, r, x0=r.copy(), rtol=1e-14, atol=0.0, maxiter=2000)
+        if info != 0:
+            raise RuntimeError(f"viscous BiCGSTAB did not converge (info {info})")
+        return x
 
 
 @dataclass

@@ -229,6 +229,12 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
   return step_run(ctx, flow, state, gu, gv, n_steps, stats, stream);
 }
 
+int rbffd_debug_set_wait_limit(rbffd_ctx* ctx, int64_t polls) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  return step_set_wait_limit(ctx, (long long)polls);
+}
+
 int rbffd_adjoint_step(rbffd_ctx* ctx, const rbffd_flow* flow, const rbffd_state* fwd,
                        rbffd_adjoint* lam, double* grad_gu, double* grad_gv, rbffd_stats* stats,
                        cudaStream_t stream) {

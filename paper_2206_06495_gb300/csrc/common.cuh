@@ -132,6 +132,7 @@ int spmv_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, int* thread
 int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st);
 void step_plan_free(struct StepPlan* p);
+int step_set_wait_limit(rbffd_ctx* ctx, long long polls);
 int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* f, const rbffd_state* s, rbffd_adjoint* lam,
                 double* grad_gu, double* grad_gv, rbffd_stats* stats, cudaStream_t st);
 // allocation-free variants on caller-provided device scratch (status codes only)

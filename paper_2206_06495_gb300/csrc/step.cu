@@ -130,6 +130,12 @@ __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, co
 constexpr int kTileRows = 256;
 constexpr long long kSpinLimit = 1ll << 22;  // bounded mbarrier wait (a tile lands in microseconds)
 
+// Polls of the first wait for a staged tile or record (kSpinLimit unless a
+// test lowers it through rbffd_debug_set_wait_limit).  After a failed first
+// wait the block still waits, up to kSpinLimit polls, for the copies it
+// issued, so lowering it never leaves a copy in flight into a finished block.
+__device__ long long g_wait_polls = kSpinLimit;
+
 // Rows are staged whenever the stencil size is a compile-time constant: with
 // every address on chip the gathers never stall the stream (measured at 1M
 // rows: 63 us per FP32 launch staged against 102 us with direct loads).
@@ -197,10 +203,10 @@ __device__ __forceinline__ bool stage_tile(EllStage<K, TW>* tile, uint64_t* bar,
       bulk_g2s(&tile->w[s * kTileRows], gw + s * ld + row0, bw, bar);
     }
   }
+  const long long limit = g_wait_polls;
   long long spins = 0;
-  bool ok;
-  while (!(ok = mbar_try_wait(bar, phase)) && ++spins < kSpinLimit) {
-  }
+  bool ok = false;
+  while (spins < limit && !(ok = mbar_try_wait(bar, phase))) ++spins;
   // one verdict for the whole block, so every thread leaves the loop together
   if (!__syncthreads_and(ok ? 1 : 0)) {
     if (threadIdx.x == 0) atomicOr(err, 4);
@@ -809,10 +815,10 @@ __device__ __forceinline__ bool stage_rec(LevelRec<W>* rec, uint64_t* bar, uint3
     mbar_expect_tx(bar, bytes);
     bulk_g2s(rec, recs + b * (int64_t)bytes, bytes, bar);
   }
+  const long long limit = g_wait_polls;
   long long spins = 0;
-  bool ok;
-  while (!(ok = mbar_try_wait(bar, phase)) && ++spins < kSpinLimit) {
-  }
+  bool ok = false;
+  while (spins < limit && !(ok = mbar_try_wait(bar, phase))) ++spins;
   if (!__syncthreads_and(ok ? 1 : 0)) {
     if (threadIdx.x == 0) atomicOr(err, 4);
     spins = 0;
@@ -2473,6 +2479,11 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
 }
 
 }  // namespace
+
+int step_set_wait_limit(rbffd_ctx* ctx, long long polls) {
+  const long long v = polls < 0 ? kSpinLimit : (polls > kSpinLimit ? kSpinLimit : polls);
+  return check_cuda(ctx, cudaMemcpyToSymbol(g_wait_polls, &v, sizeof(v)), "wait limit");
+}
 
 int step_run(rbffd_ctx* ctx, const rbffd_flow* f, rbffd_state* s, const double* gu,
              const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t st) {

@@ -113,6 +113,7 @@ PROTOTYPES = {
                                               C.POINTER(C.c_int64), C.c_void_p]),
     "rbffd_probe_fma": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                   C.c_void_p]),
+    "rbffd_debug_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "rbffd_apply_op": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "rbffd_apply_op_shape": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_int32,
@@ -365,7 +366,8 @@ class State:
 
 
 def step(ctx: Context, flow: Flow, state: State, gu, gv, n_steps: int = 1) -> dict:
-    """rbffd_step: advance `state` in place by n_steps; returns the statistics."""
+    """rbffd_step: advance `state` in place by n_steps; returns the statistics.
+    On failure the raised RbffdError carries them as `.stats`."""
     fc = flow.cstruct()
     sc = StateC(u=_ptr(state.u).value, v=_ptr(state.v).value, cu_prev=_ptr(state.cu_prev).value,
                 cv_prev=_ptr(state.cv_prev).value, pt=_ptr(state.pt).value,
@@ -374,8 +376,18 @@ def step(ctx: Context, flow: Flow, state: State, gu, gv, n_steps: int = 1) -> di
     rc = lib().rbffd_step(ctx.handle, C.byref(fc), C.byref(sc), _ptr(gu), _ptr(gv), n_steps,
                           C.byref(st), _stream())
     state.j = sc.j
-    ctx.check(rc)
+    try:
+        ctx.check(rc)
+    except RbffdError as e:
+        e.stats = st.as_dict()
+        raise
     return st.as_dict()
+
+
+def debug_set_wait_limit(ctx: Context, polls: int) -> None:
+    """rbffd_debug_set_wait_limit (test hook): polls of the first staged-copy
+    wait; 0 gives up at once, a negative value restores the default."""
+    ctx.check(lib().rbffd_debug_set_wait_limit(ctx.handle, polls))
 
 
 @dataclass

@@ -389,6 +389,22 @@ def test_helmholtz_boundary_rows_are_identity(ops20, cavity20):
         assert np.array_equal(row, e)
 
 
+def test_viscous_krylov_solve_matches_lu(cavity20, ops20):
+    """P8: the oracle's iterative viscous solve (for large node sets) and the
+    LU factorisation of the paper give the same steps (Re 1e4, dt 2e-4)."""
+    nd = cavity20
+    gu, gv = O.lid_bc(nd)
+    outs = []
+    for solver in ("lu", "krylov"):
+        fs = O.FractionalStep(nd, Re=1e4, dt=2e-4, ops=ops20, viscous_solver=solver)
+        st = fs.initial_state()
+        for _ in range(10):
+            st = fs.step(st, gu, gv)
+        outs.append(st)
+    assert np.abs(outs[0].u - outs[1].u).max() < 1e-12
+    assert np.abs(outs[0].pt - outs[1].pt).max() < 1e-10 * np.abs(outs[0].pt).max()
+
+
 def test_cavity_runs_stably_and_keeps_wall_data(cavity20, ops20):
     """Config-0-like cavity (Re 100, dt 2e-3) stays bounded; wall nodes hold
     the lid and no-slip data exactly (reading R6)."""
