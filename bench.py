@@ -9,7 +9,9 @@ correction) through rbffd_step.  The headline is the MIXED path (FP32 SpMVs and
 inner Krylov iterations, FP64 refinement to 1e-10 relative residual); the FP64
 path is timed beside it on the same box.
 
-Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+The timed steps follow --spinup steps from rest (a developed start) and
+--warmup steps.  Prints one JSON line.  `--impl reference` times the CPU
+oracle instead; `--profile-step` and `--profile-ops` are profiler captures.
 """
 from __future__ import annotations
 
@@ -41,8 +43,18 @@ def parse():
     ap.add_argument("--dt", type=float, default=2e-4)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=400000)
+    ap.add_argument("--spinup", type=int, default=200,
+                    help="untimed steps from rest before the warm-up steps (a developed "
+                         "start; the pressure iteration count of the first steps is not typical)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both")
+    ap.add_argument("--profile-ops", action="store_true",
+                    help="profiler capture of the operator kernels: the V->V operators of an "
+                         "n x n cavity, then between cudaProfilerStart/Stop three "
+                         "rbffd_apply_op launches of D_x with FP64 and three with FP32 weights "
+                         "and one rbffd_build_weights of --weights-sample V-nodes; prints the "
+                         "launch sizes")
+    ap.add_argument("--weights-sample", type=int, default=200000)
     ap.add_argument("--profile-step", action="store_true",
                     help="profiler capture: set up, take --warmup steps, then one step between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off); prints its "
@@ -158,15 +170,26 @@ def profiled_traffic(kernel_key: str, rows: int):
 
 
 # ----------------------------------------------------------- CPU baseline
+# The CPU oracle as it stands, timed on this machine's host cores in a child
+# process (BLAS threads pinned to one): fractional steps of a 150 x 150 cavity
+# sample (the largest whose set-up, with the sparse LU of the paper, ends in
+# well under a minute), the stencil-weight build of the benchmark's own V->V
+# family on a sample of its nodes (one thread, and all cores through a spawn
+# pool over independent stencils), and 10 CSR SpMVs of D^(V,V)_x over all of
+# its rows.  Nothing here is extrapolated except the step rate, which is also
+# given per node and scaled to the benchmark's node count by node count.
 ORACLE_SNIPPET = r"""
-import json, sys, time
+import json, os, sys, time
 sys.path.insert(0, {root!r})
+import numpy as np
 from oracle import rbffd_oracle as O
 from paper_2206_06495_gb300 import nodesets as ns
+
+out = {{}}
 nd = ns.jittered_cavity({n}, 2)
 t0 = time.time()
 fs = O.FractionalStep(nd, Re={re}, dt={dt})
-setup = time.time() - t0
+out["setup_s"] = time.time() - t0
 st = fs.initial_state()
 gu, gv = O.lid_bc(nd)
 for _ in range({warm}):
@@ -174,32 +197,105 @@ for _ in range({warm}):
 t0 = time.time()
 for _ in range({steps}):
     st = fs.step(st, gu, gv)
-el = time.time() - t0
-print(json.dumps({{"M": nd.M, "N": nd.N, "setup_s": setup, "step_s": el / {steps}}}))
+out.update(M=nd.M, N=nd.N, step_s=(time.time() - t0) / {steps})
+if {full}:
+    big = ns.jittered_cavity({n_full}, 2)
+    t0 = time.time()
+    iv = O.knn(big.vx, big.vy, big.vx, big.vy, 28)
+    out["knn_s"] = time.time() - t0
+    out["knn_n"] = big.N
+    ns_w = min({n_weights}, big.N)
+    ops = (O.OP_DX, O.OP_DY, O.OP_LAP)
+    t0 = time.time()
+    O.build_weights(big.vx[:ns_w], big.vy[:ns_w], big.vx, big.vy, 28, 7, 3, ops, idx=iv[:ns_w])
+    out["weights_s"] = time.time() - t0
+    out["weights_n"] = ns_w
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    per = 8192
+    n_all = min(big.N, cores * 4 * per)
+    jobs = [(np.stack([big.vx[i:i + per], big.vy[i:i + per]], -1),
+             np.stack([big.vx[iv[i:i + per]], big.vy[iv[i:i + per]]], -1), 7, 3, ops)
+            for i in range(0, n_all, per)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.starmap(O.stencil_weights, jobs[:cores])  # workers warm
+        t0 = time.time()
+        pool.starmap(O.stencil_weights, jobs)
+        out["weights_all_s"] = time.time() - t0
+    out.update(weights_all_n=n_all, cores=cores)
+    w = np.random.default_rng(0).standard_normal((big.N, 28))
+    D = O.csr(iv, w, big.N)
+    f = np.random.default_rng(1).standard_normal(big.N)
+    D @ f
+    t0 = time.time()
+    for _ in range(10):
+        D @ f
+    out.update(spmv_s=(time.time() - t0) / 10, spmv_rows=big.N)
+print(json.dumps(out))
 """
 
 
-def oracle_sample(n=100, steps=5, warm=1, re=1e4, dt=2e-4):
-    """The CPU oracle, as it stands, on a bounded cavity sample, one thread."""
+def host_cpu():
+    """Host core count and CPU model name."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_sample(n=150, steps=5, warm=1, re=1e4, dt=2e-4, full=False, n_full=1000,
+                  n_weights=50000):
+    """Run the oracle snippet in a child process with one BLAS thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, n=n, re=re, dt=dt, warm=warm, steps=steps)
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, re=re, dt=dt, warm=warm, steps=steps,
+                                 full=bool(full), n_full=n_full, n_weights=n_weights)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=900)
+                         timeout=1500)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_record(M_target, n=100, steps=5, warm=1, re=1e4, dt=2e-4):
-    r = oracle_sample(n=n, steps=steps, warm=warm, re=re, dt=dt)
+def cpu_baseline_record(M_target, n_full, re, dt, n=150, steps=5, warm=1):
+    r = oracle_sample(n=n, steps=steps, warm=warm, re=re, dt=dt, full=True, n_full=n_full)
+    cores, model = host_cpu()
     scaled = (1.0 / r["step_s"]) * (r["M"] / M_target)
     return {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle fractional step (dense-LU weights, CSR operators, sparse LU "
-                       f"solves) on a {n}x{n} P-lattice cavity (M={r['M']}, N={r['N']}), "
-                       f"{steps} timed steps after {warm} warm-up, {r['step_s']:.4f} s/step; "
-                       f"scaled to M={M_target} by node count (linear, optimistic for the "
-                       f"oracle); one thread")}
+            "sample": (f"oracle fractional steps (sparse-LU solves, as the paper) on a {n}x{n} "
+                       f"P-lattice cavity sample (M={r['M']}, N={r['N']}), Re={re:g}, dt={dt:g}: "
+                       f"{steps} timed after {warm} warm-up, {r['step_s'] * 1e3:.1f} ms/step "
+                       f"measured, one thread; value = that rate scaled to M={M_target} by "
+                       f"node count"),
+            "host": {"nproc": cores, "cpu_model": model},
+            "measured": {
+                "steps": {"M": r["M"], "N": r["N"], "steps_per_s": 1.0 / r["step_s"],
+                          "node_steps_per_s": r["M"] / r["step_s"], "threads": 1,
+                          "setup_s": r["setup_s"]},
+                "weights": {"family": f"V->V D_x, D_y, Lap (28, 7, 3) of the {n_full}x{n_full} "
+                                      f"cavity",
+                            "knn_stencils_per_s": r["knn_n"] / r["knn_s"],
+                            "stencils_per_s_1thread": r["weights_n"] / r["weights_s"],
+                            "sample_1thread": r["weights_n"],
+                            "stencils_per_s_all_cores": r["weights_all_n"] / r["weights_all_s"],
+                            "sample_all_cores": r["weights_all_n"], "cores": r["cores"]},
+                "spmv": {"rows": r["spmv_rows"], "ms": r["spmv_s"] * 1e3,
+                         "achieved_gbs_352B_per_row": r["spmv_rows"] * 352 / r["spmv_s"] / 1e9,
+                         "threads": 1, "kind": "scipy CSR D^(V,V)_x @ f, 10 timed"}}}
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -256,12 +352,17 @@ def run_ours(args):
         t_wait = time.time()
         while not sampler.rows and time.time() - t_wait < 5.0:
             time.sleep(0.05)
-    for name, flow in flows.items():
+    def spun_up(c, flow):
+        """A state after --spinup + --warmup steps from rest in context c."""
         st = R.State.zeros(flow)
         flow.profile = 0
+        for _ in range(args.spinup + args.warmup):
+            R.step(c, flow, st, gu, gv, 1)
+        return st
+
+    for name, flow in flows.items():
         try:
-            for _ in range(args.warmup):
-                R.step(ctx, flow, st, gu, gv, 1)
+            st = spun_up(ctx, flow)
         except R.RbffdError as e:
             failed[name] = str(e)[:300]
             continue
@@ -269,11 +370,13 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         agg = {"poisson_iters": 0, "helm_iters": 0, "launches": 0, "spmv_ms": 0.0,
                "spmv_launches": 0, "refinements": 0}
+        iters = []
         w0 = time.time()
         e0.record(stream)
         try:
             for _ in range(args.steps):
                 s = R.step(ctx, flow, st, gu, gv, 1)
+                iters.append(s["poisson_iters"])
                 for k in agg:
                     agg[k] += s[k]
         except R.RbffdError as e:
@@ -292,8 +395,14 @@ def run_ours(args):
         res[name]["spmv_ms"], res[name]["spmv_launches"] = s["spmv_ms"], s["spmv_launches"]
         res[name]["spmv_batch_ms"] = s["spmv_batch_ms"]
         res[name]["spmv_batch_launches"] = s["spmv_batch_launches"]
-        # end to end: boundary data in from pinned host memory, velocity out, every step
-        flow.profile = 0
+        res[name]["state"] = st
+        # End to end, on the same steps: a second context takes the same steps
+        # from rest (the path is deterministic, so it reaches the same state
+        # with the same solver history), then the timed steps are taken again
+        # with the step's boundary data copied in from pinned host memory and
+        # the velocity copied out, every step.
+        ctx2 = R.Context(28, 7, 3)
+        st2 = spun_up(ctx2, flow)
         gu_p = torch.empty(nd.N, dtype=torch.float64, pin_memory=True)
         gv_p = torch.empty(nd.N, dtype=torch.float64, pin_memory=True)
         gu_p.copy_(torch.as_tensor(gu_h))
@@ -303,20 +412,25 @@ def run_ours(args):
         gu_d = torch.empty_like(gu)
         gv_d = torch.empty_like(gv)
         barrier()
-        e2e_iters = 0
+        e2e_iters = []
+        w0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
             gu_d.copy_(gu_p, non_blocking=True)
             gv_d.copy_(gv_p, non_blocking=True)
-            e2e_iters += R.step(ctx, flow, st, gu_d, gv_d, 1)["poisson_iters"]
-            u_p.copy_(st.u, non_blocking=True)
-            v_p.copy_(st.v, non_blocking=True)
+            e2e_iters.append(R.step(ctx2, flow, st2, gu_d, gv_d, 1)["poisson_iters"])
+            u_p.copy_(st2.u, non_blocking=True)
+            v_p.copy_(st2.v, non_blocking=True)
         e1.record(stream)
         barrier()
-        ems = max_over_ranks(e0.elapsed_time(e1), world)
-        res[name]["e2e_ms"] = ems
+        windows.append((w0, time.time()))
+        res[name]["e2e_ms"] = max_over_ranks(e0.elapsed_time(e1), world)
+        res[name]["e2e_same_steps"] = e2e_iters == iters
+        res[name]["iters"] = iters
         res[name]["e2e_iters"] = e2e_iters
-        res[name]["state"] = st  # both precisions take the same steps from rest
+        ctx2.close()
+        del st2
+        torch.cuda.empty_cache()
     if sampler:
         sampler.stop()
 
@@ -381,14 +495,16 @@ def run_ours(args):
     value = whole_job_rate(args.steps, world, r["ms"])
     e2e = whole_job_rate(args.steps, world, r["e2e_ms"])
     agg = r["agg"]
-    # roofline of the pressure solve's SpMV (k_spmv_pc): per row the stencil's
-    # k column indices and k weights, the operand z (read once), the output,
-    # the dot-product partner, the row sum A 1 and the rank-one column
+    # roofline of the pressure solve's SpMV (k_spmv_pc): the algorithmic bytes
+    # of a k = 28 stencil SpMV row (k column indices, k weights, the operand
+    # read once, the output written: 232 B in FP32, 352 B in FP64); the
+    # kernel also streams three fused per-row vectors (the dot-product
+    # partner, the row sum A 1 and the rank-one column), listed apart
     k = 28
     if head == "mixed":
-        bytes_row, key = 8 * k + 5 * 4, "k_spmv_pc_fp32"  # FP32 inner solves
+        bytes_row, fused, key = 8 * k + 2 * 4, 3 * 4, "k_spmv_pc_fp32"  # FP32 inner solves
     else:
-        bytes_row, key = 12 * k + 5 * 8, "k_spmv_pc_fp64"  # z gathered as FP64
+        bytes_row, fused, key = 12 * k + 2 * 8, 3 * 8, "k_spmv_pc_fp64"
     # launch duration: back-to-back launches after each profiled pressure solve
     # (primary), and in the solve itself between graph-node events (which add
     # their own gaps)
@@ -399,6 +515,7 @@ def run_ours(args):
     in_step = (nd.M * bytes_row / (in_step_ms * 1e-3) / 1e9
                if r["spmv_launches"] > 0 and in_step_ms > 0 else None)
     traffic = profiled_traffic(key, nd.M)
+    iters_ok = r.get("e2e_same_steps")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
@@ -406,20 +523,31 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"lid-driven cavity Re={args.re:g}, jittered {args.n}x{args.n} "
                                f"P-lattice (M={nd.M}, N={nd.N}), (n,m,q)=(28,7,3), "
-                               f"dt={args.dt:g}, from rest, pressure/viscous solves to "
-                               f"{args.tol:g} relative residual",
+                               f"dt={args.dt:g}, timed after {args.spinup} spin-up and "
+                               f"{args.warmup} warm-up steps from rest, pressure/viscous solves "
+                               f"to {args.tol:g} relative residual",
                    "precision": head, "parallelism": f"replicas{world}",
+                   "spinup_steps": args.spinup,
                    "l2": "working set (operators ~7 GB) exceeds L2; no flush needed"},
         "gpu_launches": agg["launches"],
         "poisson_iters_per_step": agg["poisson_iters"] / args.steps,
         "helm_iters_per_step": agg["helm_iters"] / args.steps,
         "setup_s": t_setup,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nd.N * 8,
-                "d2h_bytes_per_step": 2 * nd.N * 8},
+                "d2h_bytes_per_step": 2 * nd.N * 8,
+                "same_steps": iters_ok,
+                "how": "a second context takes the same spin-up and warm-up steps from rest "
+                       "(deterministic path: same state and solver history), then the timed "
+                       "steps again through rbffd_step with wall data copied in from pinned "
+                       "host memory and u, v copied out every step; same_steps: equal "
+                       "pressure iteration counts step by step"},
         "roofline": {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm if achieved else None,
                      "traffic": traffic,
-                     "bytes_per_row": bytes_row, "rows": nd.M, "peak_kind": peak_kind,
+                     "bytes_per_row": bytes_row, "fused_bytes_per_row": fused,
+                     "frac_with_fused": ((achieved * (bytes_row + fused) / bytes_row) / hbm
+                                         if achieved else None),
+                     "rows": nd.M, "peak_kind": peak_kind,
                      "launches_timed": r["spmv_batch_launches"],
                      "us_per_launch": per_launch_ms * 1e3,
                      "timing": "CUDA events around 20 back-to-back launches of this kernel on "
@@ -442,7 +570,7 @@ def run_ours(args):
         def rel(x, y):
             return float((x - y).abs().max() / y.abs().max().clamp_min(1e-300))
         out["mixed_vs_fp64"] = {
-            "steps": 2 * args.steps + args.warmup + 1,
+            "steps": args.spinup + args.warmup + args.steps + 1,
             "u_max_abs": float((a.u - b.u).abs().max()), "v_max_abs": float((a.v - b.v).abs().max()),
             "u_rel": rel(a.u, b.u), "v_rel": rel(a.v, b.v),
             "p_rel": rel(a.p, b.p), "pt_rel": rel(a.pt, b.pt)}
@@ -453,43 +581,47 @@ def run_ours(args):
                      "poisson_iters_per_step": rr["agg"]["poisson_iters"] / args.steps,
                      "refinements_per_step": rr["agg"]["refinements"] / args.steps,
                      "e2e_steps_per_s": args.steps / (rr["e2e_ms"] * 1e-3),
-                     # the end-to-end steps are the next steps of the same run:
-                     # their pressure iteration counts differ from the timed ones
-                     "e2e_poisson_iters_per_step": rr["e2e_iters"] / args.steps}
+                     "e2e_same_steps": rr["e2e_same_steps"],
+                     "poisson_iters": rr["iters"]}
     if world == 1 and not args.no_cpu_baseline:
         try:
-            out["cpu_baseline"] = cpu_baseline_record(nd.M)
+            out["cpu_baseline"] = cpu_baseline_record(nd.M, args.n, args.re, args.dt)
         except Exception as e:  # reported, never fatal
             out["cpu_baseline"] = {"error": str(e)[:300]}
     return out
 
 
 def run_reference(args):
+    """The CPU oracle as it stands, on a 150 x 150 sample of the workload, one
+    thread: --warmup untimed and --steps timed fractional steps."""
     rank, world, local = dist_env()
     if rank != 0:
         return None
-    n_sample = 60
+    n_sample = 150
     t0 = time.time()
     r = oracle_sample(n=n_sample, steps=args.steps, warm=args.warmup, re=args.re, dt=args.dt)
     M_target = args.n * args.n
     value = (1.0 / r["step_s"]) * (r["M"] / M_target)
-    sample = (f"CPU oracle fractional steps on a {n_sample}x{n_sample} P-lattice cavity "
-              f"(M={r['M']}, N={r['N']}), {args.steps} timed after {args.warmup} warm-up, "
-              f"scaled to M={M_target} by node count; one thread")
+    cores, model = host_cpu()
+    sample = (f"CPU oracle fractional steps (sparse-LU solves) on a {n_sample}x{n_sample} "
+              f"P-lattice cavity sample (M={r['M']}, N={r['N']}), {args.steps} timed after "
+              f"{args.warmup} warm-up, one thread, {r['step_s'] * 1e3:.1f} ms/step measured; "
+              f"value = that rate scaled to M={M_target} by node count")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            # per step of the full-size workload (the sample's time scaled by node
-            # count, like value); the sample's own time is sample_ms_per_step
-            "ms_per_step": 1e3 / value, "sample_ms_per_step": r["step_s"] * 1e3,
+            # the sample's own measured time per step (the timed region is
+            # steps * ms_per_step); value is per step of the full workload
+            "ms_per_step": r["step_s"] * 1e3,
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"lid-driven cavity Re={args.re:g}, jittered "
-                                   f"{args.n}x{args.n} P-lattice (sampled)"},
+                                   f"{args.n}x{args.n} P-lattice, sampled at "
+                                   f"{n_sample}x{n_sample}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": {"nproc": cores, "cpu_model": model}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
-            "wall_s": time.time() - t0}
+            "setup_s": r["setup_s"], "wall_s": time.time() - t0}
 
 
 def profile_step(args):
@@ -524,8 +656,51 @@ def profile_step(args):
             "stats": s}
 
 
+def profile_ops(args):
+    """Operator kernels of the benchmark's node family between
+    cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
+    import numpy as np
+    import torch
+
+    from paper_2206_06495_gb300 import build
+    from paper_2206_06495_gb300 import nodesets as ns
+    build.build()
+    from paper_2206_06495_gb300 import rbffd as R
+
+    ctx = R.Context(28, 7, 3)
+    nd = ns.jittered_cavity(args.n, 2)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")  # noqa: E731
+    vx, vy = d(nd.vx), d(nd.vy)
+    idx, w, _ = R.build_weights(ctx, vx, vy, vx, vy, R.OP_DX | R.OP_DY | R.OP_LAP)
+    wx64, wx32 = w[0].contiguous(), w[0].float().contiguous()
+    f = torch.randn(nd.N, dtype=torch.float64, device="cuda")
+    f32 = f.float()
+    y64, y32 = torch.empty_like(f), torch.empty_like(f32)
+    ns_w = min(args.weights_sample, nd.N)
+    sx, sy = vx[:ns_w].contiguous(), vy[:ns_w].contiguous()
+    for _ in range(2):  # autotune and warm both shapes
+        R.apply_op(ctx, idx, wx64, nd.N, nd.N, f, y64)
+        R.apply_op(ctx, idx, wx32, nd.N, nd.N, f32, y32)
+    R.build_weights(ctx, sx, sy, vx, vy, R.OP_DX | R.OP_DY | R.OP_LAP)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(3):
+        R.apply_op(ctx, idx, wx64, nd.N, nd.N, f, y64)
+    for _ in range(3):
+        R.apply_op(ctx, idx, wx32, nd.N, nd.N, f32, y32)
+    R.build_weights(ctx, sx, sy, vx, vy, R.OP_DX | R.OP_DY | R.OP_LAP)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return {"profile_ops": True, "rows": nd.N, "weights_stencils": ns_w,
+            "spmv_fp64_shape": R.apply_op_shape(ctx, idx, wx64, nd.N, nd.N, f.dtype),
+            "spmv_fp32_shape": R.apply_op_shape(ctx, idx, wx32, nd.N, nd.N, f32.dtype)}
+
+
 def main():
     args = parse()
+    if args.profile_ops:
+        print(json.dumps(profile_ops(args)))
+        return
     if args.profile_step:
         print(json.dumps(profile_step(args)))
         return

