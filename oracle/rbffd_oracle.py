@@ -368,6 +368,23 @@ def poisson_matrix(ops: Operators, p_boundary, p_nx, p_ny) -> sp.csr_matrix:
     return sp.bmat([[L, e], [one, None]], format="csc")
 
 
+def exact_projection_matrices(ops: Operators, v_boundary, v_nx, v_ny):
+    """G0 = D^(V,P) with zero wall rows (x and y), the wall normal field w,
+    and the bordered matrix [[D^(P,V) G0, D^(P,V) w], [1^T, 0]] of the
+    exactly projecting variant (see FractionalStep)."""
+    inner = sp.diags((~v_boundary).astype(float))
+    G0x = (inner @ ops.vp_x).tocsr()
+    G0y = (inner @ ops.vp_y).tocsr()
+    L = (ops.pv_x @ G0x + ops.pv_y @ G0y).tocsr()
+    w_x = np.where(v_boundary, v_nx, 0.0)
+    w_y = np.where(v_boundary, v_ny, 0.0)
+    e = ops.pv_x @ w_x + ops.pv_y @ w_y
+    M = L.shape[0]
+    B = sp.bmat([[L, sp.csr_matrix(e[:, None])], [sp.csr_matrix(np.ones((1, M))), None]],
+                format="csc")
+    return G0x, G0y, w_x, w_y, B
+
+
 def helmholtz_matrix(ops: Operators, v_boundary, a: float) -> sp.csr_matrix:
     """I - a D^(V,V)_Lap (Eq. u_ss, a = dt/(2 Re)) with identity boundary rows (R5)."""
     N = ops.vv_lap.shape[0]
@@ -392,18 +409,47 @@ class FractionalStep:
 
     def __init__(self, nodes, Re: float, dt: float, k: int = 28, m: int = 7,
                  q: int = 3, ops: Operators | None = None, overwrite_bc: bool = True,
-                 km_mode: int = 2, viscous_solver: str = "lu"):
+                 km_mode: int = 2, viscous_solver: str = "lu", projection: str = "paper",
+                 cn_form: str = "printed"):
         """viscous_solver: "lu" factorises I - a D_Lap once, as the paper does
         (end of Section 3); "krylov" solves it at every step with BiCGSTAB to a
         relative residual of 1e-14 instead (a library routine; for node sets
-        whose LU fill-in is too large: I - a D_Lap is close to I there)."""
+        whose LU fill-in is too large: I - a D_Lap is close to I there).
+
+        projection: "paper" is Section 3's step (pressure Poisson with
+        D^(P,P)_Lap, Kim & Moin wall values).  "exact" projects with the
+        composed operator D^(P,V) G0, where G0 is D^(V,P) with its wall rows
+        set to zero, so the corrected velocity is discretely divergence-free
+        at every P-node (the variant the paper's D^(P,P)_Lap approximates):
+          u** : (I - a D_Lap) u** = RHS - dt G0 p~_j inside, u** = g_{j+1} on
+                the walls (the pressure increment form, which needs no Kim &
+                Moin wall term: the projection leaves wall values alone);
+          phi : D^(P,V) G0 phi + mu e = F / dt, 1^T phi = 0, with
+                e = D^(P,V) w and w the outward wall normal at wall V-nodes;
+          u_{j+1} = u** - dt G0 phi - mu dt w,  p~_{j+1} = p~_j + phi,
+          p_{j+1} = p~_{j+1} - a D^(P,P)_Lap phi.
+        D^(P,V) and G0 are not adjoint, so no gradient can remove one
+        component of the divergence; the multiplier mu takes it up as a
+        uniform normal velocity mu dt through the walls (FlowState.lam holds
+        mu dt), which keeps D^(P,V) u_{j+1} = 0 on every row.
+
+        cn_form: "printed" is Eq. u_ss, (I - a D_Lap) u** = (I + a D_Lap) u*;
+        "kim_moin" is the Crank-Nicolson form of Kim & Moin, whose right side
+        is u* + a D_Lap u_j (the printed form adds (dt^2/2Re) D_Lap of the
+        convective update, an O(dt) term)."""
         if km_mode not in (0, 1, 2):
             raise ValueError("km_mode is 0, 1 or 2")
         if viscous_solver not in ("lu", "krylov"):
             raise ValueError("viscous_solver is 'lu' or 'krylov'")
+        if projection not in ("paper", "exact"):
+            raise ValueError("projection is 'paper' or 'exact'")
+        if cn_form not in ("printed", "kim_moin"):
+            raise ValueError("cn_form is 'printed' or 'kim_moin'")
         self.nodes = nodes
         self.km_mode = km_mode
         self.viscous_solver = viscous_solver
+        self.projection = projection
+        self.cn_form = cn_form
         self.Re = float(Re)
         self.dt = float(dt)
         self.a = self.dt / (2.0 * self.Re)
@@ -415,7 +461,11 @@ class FractionalStep:
         self.ty = nodes.v_nx
         self.overwrite_bc = overwrite_bc
         self.H = helmholtz_matrix(self.ops, self.vb, self.a)
-        self.Pb = poisson_matrix(self.ops, self.pb, nodes.p_nx, nodes.p_ny)
+        if projection == "exact":
+            self.G0x, self.G0y, self.w_x, self.w_y, self.Pb = exact_projection_matrices(
+                self.ops, self.vb, nodes.v_nx, nodes.v_ny)
+        else:
+            self.Pb = poisson_matrix(self.ops, self.pb, nodes.p_nx, nodes.p_ny)
         self.H_lu = spla.splu(self.H) if viscous_solver == "lu" else None
         self.P_lu = spla.splu(self.Pb)
         self._HT_lu = None
@@ -449,6 +499,15 @@ class FractionalStep:
         every V-node (only the boundary entries are used)."""
         o, dt, a, vb = self.ops, self.dt, self.a, self.vb
         cu, cv, uss, vss, F = self.intermediate(st, gu, gv)
+        if self.projection == "exact":
+            sol = self.P_lu.solve(np.concatenate([F / dt, [0.0]]))
+            phi, mu = sol[:-1], sol[-1]
+            un = uss - dt * (self.G0x @ phi) - mu * dt * self.w_x
+            vn = vss - dt * (self.G0y @ phi) - mu * dt * self.w_y
+            pt = st.pt + phi
+            p = pt - a * (o.pp_lap @ phi)
+            return FlowState(u=un, v=vn, cu_prev=cu, cv_prev=cv, pt=pt, p=p,
+                             lam=float(mu * dt), j=st.j + 1)
         # stage 3: pressure Poisson, pressure, correction
         b = np.where(self.pb, 0.0, F / dt)
         sol = self.P_lu.solve(np.concatenate([b, [0.0]]))
@@ -474,8 +533,20 @@ class FractionalStep:
         us = st.u + dt * (1.5 * cu - 0.5 * cu_prev)
         vs = st.v + dt * (1.5 * cv - 0.5 * cv_prev)
         # stage 2: Crank-Nicolson viscous step, Kim & Moin boundary values
-        ru = us + a * (o.vv_lap @ us)
-        rv = vs + a * (o.vv_lap @ vs)
+        if self.cn_form == "printed":  # Eq. u_ss
+            ru = us + a * (o.vv_lap @ us)
+            rv = vs + a * (o.vv_lap @ vs)
+        else:
+            ru = us + a * (o.vv_lap @ st.u)
+            rv = vs + a * (o.vv_lap @ st.v)
+        if self.projection == "exact":  # pressure increment form, plain wall data
+            ru -= dt * (self.G0x @ st.pt)
+            rv -= dt * (self.G0y @ st.pt)
+            ru[vb] = gu[vb]
+            rv[vb] = gv[vb]
+            uss = self.solve_viscous(ru)
+            vss = self.solve_viscous(rv)
+            return cu, cv, uss, vss, o.pv_x @ uss + o.pv_y @ vss
         # Kim & Moin: u** = u_{j+1} + dt D^(V,P) p~_j on the wall (R5)
         gpx = o.vp_x @ st.pt
         gpy = o.vp_y @ st.pt
@@ -522,6 +593,8 @@ def adjoint_step(fs: "FractionalStep", st_in: FlowState, lam: AdjointState,
     transpose of the oracle's CSR matrix; the transposed solves use the LU
     factors of H^T and of the bordered matrix's transpose.
     """
+    if fs.projection != "paper" or fs.cn_form != "printed":
+        raise NotImplementedError("the adjoint follows the paper's step (Section 3) only")
     o, dt, a = fs.ops, fs.dt, fs.a
     km_mode = fs.km_mode if km_mode is None else km_mode
     w = fs.vb

@@ -100,3 +100,29 @@ def test_dropped_kim_moin_term_is_caught(monkeypatch, fresh_time_cache):
         self.km_mode = 0
     monkeypatch.setattr(O.FractionalStep, "__init__", init)
     assert _fails(pins.test_taylor_green_time_order)
+
+
+def test_euler_convection_is_caught_by_the_two_mode_pin(monkeypatch):
+    """Forward Euler for the convective term (C_{j-1} = C_j at every step)
+    instead of the Adams-Bashforth history makes the exactly projecting,
+    Kim & Moin Crank-Nicolson step first order on the two-mode flow."""
+    orig = O.FractionalStep.intermediate
+
+    def euler(self, st, gu, gv):
+        return orig(self, O.FlowState(st.u, st.v, st.cu_prev, st.cv_prev, st.pt, st.p,
+                                      st.lam, 0), gu, gv)
+    monkeypatch.setattr(O.FractionalStep, "intermediate", euler)
+    assert _fails(pins.test_exact_projection_with_kim_moin_crank_nicolson_is_second_order)
+
+
+def test_wrong_sign_of_pressure_increment_is_caught(monkeypatch):
+    """The exact projection's predictor with +dt G0 p~_j instead of -dt G0 p~_j."""
+    orig_init = O.FractionalStep.__init__
+
+    def init(self, *a, **k):
+        orig_init(self, *a, **k)
+        if self.projection == "exact":
+            self.G0x, self.G0y = -self.G0x, -self.G0y
+    monkeypatch.setattr(O.FractionalStep, "__init__", init)
+    with np.errstate(all="ignore"):
+        assert _fails(pins.test_exact_projection_taylor_green_space_and_time)
