@@ -58,6 +58,14 @@ extern "C" {
 #define RBFFD_PREC_FP64 0  /* everything in FP64 */
 #define RBFFD_PREC_MIXED 1 /* FP32 SpMVs and inner Krylov, FP64 iterative refinement */
 
+/* projection of rbffd_step (rbffd_flow.projection) */
+#define RBFFD_PROJ_PAPER 0 /* Section 3: pressure Poisson with D^(P,P)_Lap */
+#define RBFFD_PROJ_EXACT 1 /* composed D^(P,V) G0: discretely divergence-free velocity */
+
+/* Crank-Nicolson right side of rbffd_step (rbffd_flow.cn_form) */
+#define RBFFD_CN_PRINTED 0  /* Eq. u_ss: (I + a D_Lap) u*                    */
+#define RBFFD_CN_KIM_MOIN 1 /* Kim & Moin: u* + a D_Lap u_j                   */
+
 typedef struct rbffd_ctx rbffd_ctx;
 
 /* Stencil parameters (n, m, q) of Section 4; the paper selects (28, 7, 3). */
@@ -227,6 +235,27 @@ int rbffd_apply_op_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, i
  *                 staggered node set (each V-node sits at an edge midpoint)
  * p_x, p_y        P-node coordinates, device double[M] (edge weights
  *                 1/|x_a - x_b|^2); all three are read only when precond = 1
+ * projection      RBFFD_PROJ_PAPER (the step below, as in Section 3) or
+ *                 RBFFD_PROJ_EXACT: the pressure operator is the composition
+ *                 D^(P,V) G0 of the divergence with the gradient D^(V,P) whose
+ *                 wall rows are zero (built once per flow description, at most
+ *                 kMaxComposed = 128 entries per row), so the corrected velocity
+ *                 is discretely divergence-free at every P-node.  The paper
+ *                 replaces that composition by D^(P,P)_Lap (Section 3); this
+ *                 variant has no counterpart there.  Its step:
+ *                   u** = g on wall rows; inside, the right side (per cn_form)
+ *                   minus dt G0 p~_j (pressure-increment form; km_mode and
+ *                   overwrite_bc are not used);
+ *                   D^(P,V) G0 phi + mu e = F / dt on every P-node, 1^T phi
+ *                   = 0, e = D^(P,V) w with w the wall normal (v_nx, v_ny) at
+ *                   wall V-nodes;
+ *                   u_{j+1} = u** - dt G0 phi - mu dt w (the one divergence
+ *                   component no gradient can remove leaves as a uniform
+ *                   wall-normal velocity mu dt, reported as wall_flux);
+ *                   p~_{j+1} = p~_j + phi; p_{j+1} = p~_{j+1} - a D^(P,P)_Lap phi
+ * cn_form         RBFFD_CN_PRINTED (Eq. u_ss, the default) or RBFFD_CN_KIM_MOIN
+ *                 (right side u* + a D^(V,V)_Lap u_j, Kim & Moin's
+ *                 Crank-Nicolson form; the printed one adds an O(dt) term)
  */
 typedef struct rbffd_flow {
   int64_t N, M, ld_v, ld_p;
@@ -257,6 +286,8 @@ typedef struct rbffd_flow {
   const int32_t* p_edges;
   int64_t n_edges;
   const double *p_x, *p_y;
+  int32_t projection;
+  int32_t cn_form;
 } rbffd_flow;
 
 /* Solver state at step j (all FP64 device arrays owned by the caller). */
@@ -282,6 +313,8 @@ typedef struct rbffd_stats {
   int64_t spmv_batch_launches; /* profile: the same SpMV relaunched back to back after
                                   each pressure solve (20 per solve)            */
   double spmv_batch_ms;     /* profile: their summed durations, milliseconds  */
+  double wall_flux;         /* RBFFD_PROJ_EXACT: wall-normal velocity mu dt of the
+                               last step; 0 otherwise                          */
 } rbffd_stats;
 
 /*
@@ -346,6 +379,8 @@ typedef struct rbffd_adjoint {
  *        g_{j+1} is ADDED to them (wall entries only)
  * The operators of the step are transposed once per flow description (kept in
  * the context).  Transposed solves use the flow's tol and max_iter.  FP64.
+ * Only the paper's step (projection = RBFFD_PROJ_PAPER, cn_form =
+ * RBFFD_CN_PRINTED) has an adjoint; other flows give INVALID_ARG.
  * A training loop stores checkpoints of forward states and recomputes the
  * states between them before walking backwards.  Errors: as rbffd_step.
  * Synchronises `stream`; stats (HOST, may be NULL) receives the iteration

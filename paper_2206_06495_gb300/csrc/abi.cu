@@ -208,6 +208,9 @@ static int check_flow(rbffd_ctx* ctx, const rbffd_flow* flow) {
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad Re, dt, tolerances or modes");
   if (f.precond != 0 && f.precond != 1)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "precond must be 0 or 1");
+  if ((f.projection != RBFFD_PROJ_PAPER && f.projection != RBFFD_PROJ_EXACT) ||
+      (f.cn_form != RBFFD_CN_PRINTED && f.cn_form != RBFFD_CN_KIM_MOIN))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "projection and cn_form must be 0 or 1");
   if (f.precond && (!f.p_edges || f.n_edges < 1 || f.n_edges > INT32_MAX || !f.p_x || !f.p_y))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "precond = 1 needs p_edges, n_edges, p_x, p_y");
   return RBFFD_OK;
@@ -249,6 +252,9 @@ int rbffd_adjoint_step(rbffd_ctx* ctx, const rbffd_flow* flow, const rbffd_state
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad forward state");
   if (!lam->u || !lam->v || !lam->cu_prev || !lam->cv_prev || !lam->pt)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null adjoint array");
+  if (flow->projection != RBFFD_PROJ_PAPER || flow->cn_form != RBFFD_CN_PRINTED)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                     "the adjoint exists for the paper's step only (projection 0, cn_form 0)");
   return adjoint_run(ctx, flow, fwd, lam, grad_gu, grad_gv, stats, stream);
 }
 

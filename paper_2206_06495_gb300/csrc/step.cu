@@ -1294,9 +1294,15 @@ struct HelmRhsArgs {
   double a, dt;
   int km;
   double *ru, *rv, *xu, *xv;
+  const double *u, *v;  // u_j, v_j (the Kim & Moin Crank-Nicolson form)
+  const float2 *u2, *v2;
+  int cn;    // RBFFD_CN_*
+  int proj;  // RBFFD_PROJ_*
 };
 
-// Stage 2 right side: (I + a D_Lap) u* inside; wall rows: Kim & Moin value
+// Stage 2 right side: u* + a D_Lap (u* or u_j) inside, minus dt G0 p~_j for
+// the exact projection; wall rows: the wall data plus, for the paper's
+// projection, the Kim & Moin term
 template <int K, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_helm_rhs(HelmRhsArgs a) {
   const void* wl[1] = {a.lap};
@@ -1306,14 +1312,22 @@ __global__ void __launch_bounds__(kThreads) k_helm_rhs(HelmRhsArgs a) {
     double bu, bv;
     if (!a.v_bc[i]) {
       double lu, lv;
-      Gather<K, MIX, 1>::run(a.vv_idx, wl, a.ld_v, a.k, i, a.us, a.us2, &lu);
-      Gather<K, MIX, 1>::run(a.vv_idx, wl, a.ld_v, a.k, i, a.vs, a.vs2, &lv);
+      const double* qu = a.cn ? a.u : a.us;
+      const double* qv = a.cn ? a.v : a.vs;
+      Gather<K, MIX, 1>::run(a.vv_idx, wl, a.ld_v, a.k, i, qu, a.cn ? a.u2 : a.us2, &lu);
+      Gather<K, MIX, 1>::run(a.vv_idx, wl, a.ld_v, a.k, i, qv, a.cn ? a.v2 : a.vs2, &lv);
       bu = a.us[i] + a.a * lu;
       bv = a.vs[i] + a.a * lv;
+      if (a.proj) {
+        double g[2];
+        Gather<K, MIX, 2>::run(a.vp_idx, wg, a.ld_v, a.k, i, a.pt, a.pt2, g);
+        bu -= a.dt * g[0];
+        bv -= a.dt * g[1];
+      }
     } else {
       bu = a.gu[i];
       bv = a.gv[i];
-      if (a.km) {
+      if (a.km && !a.proj) {
         double g[2];
         Gather<K, MIX, 2>::run(a.vp_idx, wg, a.ld_v, a.k, i, a.pt, a.pt2, g);
         if (a.km == 1) {
@@ -1345,9 +1359,11 @@ struct DivArgs {
   const double* scale;
   double inv_dt;
   double* b;
+  int proj;  // exact projection: every row is a divergence row
 };
 
 // Stage 3a: F = D^(P,V)_x u** + D^(P,V)_y v**; scaled Poisson right side
+// (0 on the Neumann rows of the paper's projection)
 template <int K, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_divergence(DivArgs a) {
   const void* wx[1] = {a.wdx};
@@ -1357,7 +1373,7 @@ __global__ void __launch_bounds__(kThreads) k_divergence(DivArgs a) {
     double fx, fy;
     Gather<K, MIX, 1>::run(a.idx, wx, a.ld_p, a.k, i, a.uss, a.uss2, &fx);
     Gather<K, MIX, 1>::run(a.idx, wy, a.ld_p, a.k, i, a.vss, a.vss2, &fy);
-    a.b[i] = a.p_bc[i] ? 0.0 : a.scale[i] * (fx + fy) * a.inv_dt;
+    a.b[i] = (a.p_bc[i] && !a.proj) ? 0.0 : a.scale[i] * (fx + fy) * a.inv_dt;
   }
 }
 
@@ -1372,9 +1388,12 @@ struct PresArgs {
   double a;
   double *pt, *p;
   float2* pt2;
+  int proj;
 };
 
-// Stage 3c: p~ = x - mean(x); p = p~ - a D^(P,P)_Lap p~
+// Stage 3c: p~ = x - mean(x); p = p~ - a D^(P,P)_Lap p~.  Exact projection:
+// x - mean(x) is the increment phi, p~ += phi, p = p~ - a D^(P,P)_Lap phi
+// (D_Lap annihilates constants, so it is applied to x).
 template <int K, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_pressure(PresArgs a) {
   const void* wl[1] = {a.lap};
@@ -1383,7 +1402,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure(PresArgs a) {
        i += (int64_t)gridDim.x * kThreads) {
     double l;
     Gather<K, MIX, 1>::run(a.idx, wl, a.ld_p, a.k, i, a.px, a.px2, &l);
-    const double pt = a.px[i] - mean;
+    const double pt = (a.proj ? a.pt[i] : 0.0) + (a.px[i] - mean);
     a.pt[i] = pt;
     a.p[i] = pt - a.a * l;
     if (MIX) a.pt2[i] = split2(pt);
@@ -1404,19 +1423,31 @@ struct CorrArgs {
   int overwrite;
   double *u, *v;
   float2 *u2, *v2;
+  // exact projection: pt/pt2 hold x = phi + const, wall rows move by -c n with
+  // c = -dt (sum x) / esn (the multiplier of the wall-flux column)
+  int proj;
+  const double *sum, *esn, *v_nx, *v_ny;
 };
 
-// Stage 3d: u_{j+1} = u** - dt D^(V,P)_x p~ (Eq. velocity_next_timestep)
+// Stage 3d: u_{j+1} = u** - dt D^(V,P)_x p~ (Eq. velocity_next_timestep).
+// Exact projection: u_{j+1} = u** - dt G0 phi - c w.
 template <int K, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_correct(CorrArgs a) {
   const void* w[2] = {a.wdx, a.wdy};
+  const double c = a.proj ? -a.dt * (*a.sum) / (*a.esn) : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * kThreads) {
-    double g[2];
-    Gather<K, MIX, 2>::run(a.idx, w, a.ld_v, a.k, i, a.pt, a.pt2, g);
-    double un = a.uss[i] - a.dt * g[0];
-    double vn = a.vss[i] - a.dt * g[1];
-    if (a.overwrite && a.v_bc[i]) {
+    double un, vn;
+    if (a.proj && a.v_bc[i]) {
+      un = a.uss[i] - c * a.v_nx[i];
+      vn = a.vss[i] - c * a.v_ny[i];
+    } else {
+      double g[2];
+      Gather<K, MIX, 2>::run(a.idx, w, a.ld_v, a.k, i, a.pt, a.pt2, g);
+      un = a.uss[i] - a.dt * g[0];
+      vn = a.vss[i] - a.dt * g[1];
+    }
+    if (a.overwrite && !a.proj && a.v_bc[i]) {
       un = a.gu[i];
       vn = a.gv[i];
     }
@@ -1494,6 +1525,83 @@ __global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __r
   }
 }
 
+// Composed pressure operator of the exact projection, L = D^(P,V) G0 (G0 =
+// D^(V,P) with zero wall rows).  Row i merges, over the V-nodes v of its
+// divergence stencil that are not on a wall, the products of its weights
+// with the gradient stencil of v; columns appear in first-occurrence order
+// (divergence slot, then gradient slot) and each weight is summed in that
+// order, so the result does not depend on the launch.  Count pass (Lidx ==
+// nullptr): count[i] = the row's distinct columns (kMaxComposed + 1 when it
+// has more).  Build pass: width W (rows padded with (i, 0)), each row divided
+// by its diagonal like the paper's operator, es = -S (D^(P,V) w)_i with w the
+// wall normal at wall V-nodes (the wall-flux column); error bit 8 when a row
+// does not fit.
+constexpr int kMaxComposed = 128;
+
+__global__ void __launch_bounds__(128)
+    k_composed(int64_t M, int64_t ld_p, int k, const int32_t* __restrict__ pv_idx,
+               const double* __restrict__ pv_dx, const double* __restrict__ pv_dy, int64_t ld_v,
+               const int32_t* __restrict__ vp_idx, const double* __restrict__ vp_dx,
+               const double* __restrict__ vp_dy, const uint8_t* __restrict__ v_bc,
+               const double* __restrict__ v_nx, const double* __restrict__ v_ny, int W,
+               int* __restrict__ count, int32_t* __restrict__ Lidx, double* __restrict__ Lw,
+               double* __restrict__ es, double* __restrict__ scale, int* __restrict__ err) {
+  int32_t cols[kMaxComposed];
+  double ws[kMaxComposed];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int nc = 0;
+    bool over = false;
+    double dw = 0.0;
+    for (int s = 0; s < k; ++s) {
+      const int32_t v = pv_idx[s * ld_p + i];
+      const double ax = pv_dx[s * ld_p + i], ay = pv_dy[s * ld_p + i];
+      if (v_bc[v]) {
+        dw += ax * v_nx[v] + ay * v_ny[v];
+        continue;
+      }
+      for (int t = 0; t < k; ++t) {
+        const int32_t c = vp_idx[t * ld_v + v];
+        const double wt = ax * vp_dx[t * ld_v + v] + ay * vp_dy[t * ld_v + v];
+        int q = 0;
+        while (q < nc && cols[q] != c) ++q;
+        if (q == nc) {
+          if (nc == kMaxComposed) {
+            over = true;
+            continue;
+          }
+          cols[nc] = c;
+          ws[nc] = 0.0;
+          ++nc;
+        }
+        ws[q] += wt;
+      }
+    }
+    if (!Lidx) {
+      count[i] = over ? kMaxComposed + 1 : nc;
+      continue;
+    }
+    if (over || nc > W) {
+      atomicOr(err, 8);
+      nc = 0;
+    }
+    double diag = 0.0, sabs = 0.0;
+    for (int q = 0; q < nc; ++q) {
+      if (cols[q] == (int32_t)i) diag += ws[q];
+      sabs += fabs(ws[q]);
+    }
+    const double sc = diag != 0.0 ? 1.0 / diag : (sabs > 0.0 ? 1.0 / sabs : 1.0);
+    for (int q = 0; q < W; ++q) {
+      Lidx[q * ld_p + i] = q < nc ? cols[q] : (int32_t)i;
+      Lw[q * ld_p + i] = q < nc ? ws[q] * sc : 0.0;
+    }
+    es[i] = -sc * dw;
+    scale[i] = sc;
+  }
+}
+
+__global__ void k_store_abs(const double* __restrict__ x, double* __restrict__ y) { *y = fabs(*x); }
+
 // Viscous operator without its identity part: Hw = -a_i D_Lap
 __global__ void k_build_helm(int64_t N, int64_t ld, int k, const double* __restrict__ lap,
                              const uint8_t* __restrict__ v_bc, double a, double* __restrict__ Hw) {
@@ -1555,6 +1663,10 @@ __global__ void __launch_bounds__(kThreads)
 struct StepPlan {
   rbffd_flow key;
   int k = 0;
+  int kL = 0;         // row width of the pressure operator (k, or the composed width)
+  int proj = 0;       // RBFFD_PROJ_*
+  double* esn = nullptr;  // |sum of the raw rank-one column| (exact projection's multiplier scale)
+  double esn_h = 0.0;
   int64_t N = 0, M = 0;
   int grid = 0;
   bool mix = false;
@@ -1653,7 +1765,7 @@ int to32(rbffd_ctx* ctx, StepPlan* p, const double* src, int64_t n, float** dst,
 rbffd_flow plan_key(const rbffd_flow& f) {
   rbffd_flow k = f;
   k.tol = k.inner_tol = 0.0;
-  k.max_iter = k.km_mode = k.overwrite_bc = k.profile = 0;
+  k.max_iter = k.km_mode = k.overwrite_bc = k.profile = k.cn_form = 0;
   return k;
 }
 
@@ -1665,7 +1777,9 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   p->M = f.M;
   p->mix = f.precision == RBFFD_PREC_MIXED;
   p->grid = sm_count() * 8;  // 8 blocks of 256 per SM: full occupancy at 32 registers
-  const int64_t nv = f.ld_v * p->k, np = f.ld_p * p->k;
+  p->proj = f.projection;
+  p->kL = p->k;
+  const int64_t nv = f.ld_v * p->k;
   const int64_t nmax = f.N > f.M ? f.N : f.M;
   int rc = 0;
 #define TRY(x)                   \
@@ -1676,8 +1790,31 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       return rc;                 \
     }                            \
   } while (0)
+  if (p->proj) {
+    // width of the composed operator: the longest merged row
+    int* cnt = nullptr;
+    TRY(palloc(ctx, p, &cnt, f.M));
+    k_composed<<<p->grid, 128, 0, st>>>(f.M, f.ld_p, p->k, f.pv_idx, f.pv_dx, f.pv_dy, f.ld_v,
+                                        f.vp_idx, f.vp_dx, f.vp_dy, f.v_bc, f.v_nx, f.v_ny, 0,
+                                        cnt, nullptr, nullptr, nullptr, nullptr, nullptr);
+    TRY(check_cuda(ctx, cudaGetLastError(), "composed operator count"));
+    std::vector<int> hc(f.M);
+    TRY(check_cuda(ctx, cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * f.M,
+                                        cudaMemcpyDeviceToHost, st), "count copy"));
+    TRY(check_cuda(ctx, cudaStreamSynchronize(st), "count sync"));
+    int W = 1;
+    for (int c : hc) W = c > W ? c : W;
+    if (W > kMaxComposed) {
+      step_plan_free(p);
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                       "composed pressure operator has a row wider than %d entries", kMaxComposed);
+    }
+    p->kL = W;
+  }
+  const int64_t np = f.ld_p * p->kL;
   TRY(palloc(ctx, p, &p->Lw, np));
   TRY(palloc(ctx, p, &p->Lidx, np));
+  TRY(palloc(ctx, p, &p->esn, 1));
   TRY(palloc(ctx, p, &p->bmap, f.M));
   TRY(palloc(ctx, p, &p->err, 1));
   TRY(palloc(ctx, p, &p->es, f.M));
@@ -1702,13 +1839,20 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   const double a = f.dt / (2.0 * f.Re);
   TRY(check_cuda(ctx, cudaMemsetAsync(p->err, 0, sizeof(int), st), "memset"));
   TRY(check_cuda(ctx, cudaMemsetAsync(p->bmap, 0xff, sizeof(int32_t) * f.M, st), "memset"));
-  k_scatter_rows<<<p->grid, kThreads, 0, st>>>(f.nb_p, f.M, f.pn_rows, p->bmap, p->err);
-  k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.p_bc,
-                                                 p->bmap, f.ld_b, f.pn_idx, f.pn_dx, f.pn_dy,
-                                                 f.p_nx, f.p_ny, p->Lidx, p->Lw, p->es,
-                                                 p->scale, p->err);
+  if (p->proj) {
+    k_composed<<<p->grid, 128, 0, st>>>(f.M, f.ld_p, p->k, f.pv_idx, f.pv_dx, f.pv_dy, f.ld_v,
+                                        f.vp_idx, f.vp_dx, f.vp_dy, f.v_bc, f.v_nx, f.v_ny,
+                                        p->kL, nullptr, p->Lidx, p->Lw, p->es, p->scale, p->err);
+  } else {
+    k_scatter_rows<<<p->grid, kThreads, 0, st>>>(f.nb_p, f.M, f.pn_rows, p->bmap, p->err);
+    k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.p_bc,
+                                                   p->bmap, f.ld_b, f.pn_idx, f.pn_dx, f.pn_dy,
+                                                   f.p_nx, f.p_ny, p->Lidx, p->Lw, p->es,
+                                                   p->scale, p->err);
+  }
   // normalise the rank-one column so that the constant mode has eigenvalue 1
   k_sum<double><<<p->grid, kThreads, 0, st>>>(p->es, f.M, p->gr, p->dscal);
+  k_store_abs<<<1, 1, 0, st>>>(p->dscal, p->esn);
   k_scale_by_inv_abs<<<p->grid, kThreads, 0, st>>>(f.M, p->es, p->dscal);
   k_build_helm<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bc, a, p->Hw);
   TRY(check_cuda(ctx, cudaGetLastError(), "plan kernels"));
@@ -1717,17 +1861,25 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     TRY(check_cuda(ctx, cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st),
                    "plan status"));
     TRY(check_cuda(ctx, cudaStreamSynchronize(st), "plan sync"));
+    TRY(check_cuda(ctx, cudaMemcpy(&p->esn_h, p->esn, sizeof(double), cudaMemcpyDeviceToHost),
+                   "rank-one scale"));
     if (herr) {
       step_plan_free(p);
+      if (herr & 8)
+        return set_error(ctx, RBFFD_ERR_INVALID_ARG, "composed pressure operator overflow");
       return set_error(ctx, RBFFD_ERR_INVALID_ARG,
                        "Neumann rows (pn_rows) must list every boundary P-node once (code %d)",
                        herr);
     }
+    if (p->proj && !(p->esn_h > 0.0))
+      return (step_plan_free(p),
+              set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                        "exact projection needs wall V-nodes with normals (v_bc, v_nx, v_ny)"));
   }
   if (f.precond) {
     // multigrid hierarchy of the P-node edge graph, scaled to the pressure rows
     std::vector<double> hd(f.M), hes(f.M);
-    k_diag<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, p->Lidx, p->Lw, p->kw64[0][0]);
+    k_diag<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->kL, p->Lidx, p->Lw, p->kw64[0][0]);
     TRY(check_cuda(ctx, cudaGetLastError(), "diagonal"));
     TRY(check_cuda(ctx, cudaMemcpyAsync(hd.data(), p->kw64[0][0], sizeof(double) * f.M,
                                         cudaMemcpyDeviceToHost, st),
@@ -1738,13 +1890,13 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     TRY(check_cuda(ctx, cudaStreamSynchronize(st), "diagonal sync"));
     TRY(amg_build(ctx, f, hd.data(), hes.data(), &p->amg, st));
     TRY(palloc(ctx, p, &p->a1, f.M));
-    k_rowsum<double><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, p->Lw, p->a1);
+    k_rowsum<double><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->kL, p->Lw, p->a1);
     TRY(check_cuda(ctx, cudaGetLastError(), "row sums"));
   }
   if (p->mix) {
     TRY(to32(ctx, p, p->Lw, np, &p->Lw32, st));
     if (f.precond) {
-      k_rowsum<float><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, p->Lw32, p->kw64[0][0]);
+      k_rowsum<float><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->kL, p->Lw32, p->kw64[0][0]);
       TRY(check_cuda(ctx, cudaGetLastError(), "row sums"));
       TRY(to32(ctx, p, p->kw64[0][0], f.M, &p->a1_32, st));
     }
@@ -1787,7 +1939,9 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       return check_cuda(ctx, cudaGetLastError(), "tile records");
     };
     TRY(records(f.N, f.ld_v, f.vv_idx, p->Hw, p->Hw32, &p->Ht));
-    if (f.precond) TRY(records(f.M, f.ld_p, p->Lidx, p->Lw, p->Lw32, &p->Lt));
+    // the composed operator's width is not the staged tiles' k: its SpMVs
+    // read rows directly
+    if (f.precond && !p->proj) TRY(records(f.M, f.ld_p, p->Lidx, p->Lw, p->Lw32, &p->Lt));
   }
 #undef TRY
   *out = p;
@@ -2358,10 +2512,11 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     if (rc) return rc;
   }
   KOp<double, double> H64{f.vv_idx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
-  KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, k, 0, P->es, nullptr, P->a1};
+  KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, P->kL, 0, P->es, nullptr, P->a1};
   KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
-  KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, k, 0, P->es32, nullptr, P->a1_32};
-  if (f.precond) (MIX ? L32.tiles : L64.tiles) = P->Lt;
+  KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, P->kL, 0, P->es32, nullptr, P->a1_32};
+  const bool proj = P->proj != 0;
+  if (f.precond && !proj) (MIX ? L32.tiles : L64.tiles) = P->Lt;
   (MIX ? H32.tiles : H64.tiles) = P->Ht;
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
@@ -2371,7 +2526,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     HelmRhsArgs ha{f.N,    f.ld_v, k,      f.vv_idx, vlap,   P->us,  P->vs,  P->us2,
                    P->vs2, f.vp_idx, gdx,  gdy,      s->pt,  P->pt2, f.v_bc, f.v_nx,
                    f.v_ny, gu,     gv,     a,        f.dt,   f.km_mode, P->ru, P->rv,
-                   P->uss, P->vss};
+                   P->uss, P->vss, s->u,   s->v,     P->u2,  P->v2, f.cn_form, P->proj};
     k_helm_rhs<K, MIX><<<G, kThreads, 0, st>>>(ha);
     P->launches += 2 + (MIX ? 2 : 0) + 4 + (MIX ? 1 : 0);  // stage kernels of this step
     int rc = check_cuda(ctx, cudaGetLastError(), "stage 1-2 kernels");
@@ -2408,16 +2563,18 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     // FP32 weights would leave their rounding (relative to the terms, not to
     // their small sum) in p~, so both precisions take it with FP64 weights.
     DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, f.pv_dx,  f.pv_dy,      P->uss,
-               P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb};
+               P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb, P->proj};
     k_divergence<K, false><<<G, kThreads, 0, st>>>(da);
     // Initial guess: the linear extrapolation of the two previous steps'
     // solutions when both are at hand, else the previous solution, else the
     // state's p~.  Any guess leaves the converged solution the same; a better
     // one saves iterations (p~ changes smoothly from step to step).
     if (P->px_step != s->j) {
-      rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
-                                           cudaMemcpyDeviceToDevice, st),
-                      "warm start");
+      // the exact projection solves for the increment of p~: start from zero
+      rc = proj ? check_cuda(ctx, cudaMemsetAsync(P->px, 0, sizeof(double) * f.M, st), "zero start")
+                : check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * f.M,
+                                                  cudaMemcpyDeviceToDevice, st),
+                             "warm start");
       if (rc) return rc;
       P->pxp_step = -1;
     } else {
@@ -2436,12 +2593,20 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     const double* pbv[1] = {P->pb};
     SolveResult pr;
     const bool prof = f.profile != 0;
-    if (MIX)
+    if (proj) {  // the composed operator's rows are read directly (runtime width)
+      if (MIX)
+        rc = refine<0, 1, true>(ctx, P, L64, L32, px, pbv, f.tol, f.inner_tol, f.max_iter, &pr,
+                                &sweeps, st, prof);
+      else
+        rc = bicgstab<0, 1, true, double, double>(ctx, P, L64, px, pbv, P->kw64, f.tol,
+                                                  f.max_iter, &pr, st, prof, 0, P->amg);
+    } else if (MIX) {
       rc = refine<K, 1, true>(ctx, P, L64, L32, px, pbv, f.tol, f.inner_tol, f.max_iter, &pr,
                               &sweeps, st, prof);
-    else
+    } else {
       rc = bicgstab<K, 1, true, double, double>(ctx, P, L64, px, pbv, P->kw64, f.tol, f.max_iter,
                                                 &pr, st, prof, 0, P->amg);
+    }
     if (rc) return rc;
     if (stats) {
       stats->poisson_iters += pr.iters;
@@ -2455,12 +2620,24 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                        pr.relres, pr.iters, pr.status);
     k_sum<double><<<G, kThreads, 0, st>>>(P->px, f.M, P->gr, P->dscal);
     if (MIX) k_split<<<G, kThreads, 0, st>>>(f.M, P->px, P->px2);
-    PresArgs pa{f.M, f.ld_p, k, f.pp_idx, plap, P->px, P->px2, P->dscal, a, s->pt, s->p, P->pt2};
+    PresArgs pa{f.M,   f.ld_p, k,    f.pp_idx, plap,   P->px,  P->px2,
+                P->dscal, a,   s->pt, s->p, P->pt2,   P->proj};
     k_pressure<K, MIX><<<G, kThreads, 0, st>>>(pa);
-    CorrArgs ka{f.N,    f.ld_v, k,      f.vp_idx, gdx,  gdy,  s->pt, P->pt2, P->uss,
-                P->vss, f.v_bc, gu,     gv,       f.dt, f.overwrite_bc, s->u, s->v,
-                P->u2,  P->v2};
-    k_correct<K, MIX><<<G, kThreads, 0, st>>>(ka);
+    // The exact projection corrects with G0 x (x = phi + const) and the wall
+    // flux, with FP64 weights in both precisions (like the divergence), so
+    // that D^(P,V) u_{j+1} vanishes to the solve's accuracy.
+    CorrArgs ka{f.N,      f.ld_v, k,        f.vp_idx,       proj ? f.vp_dx : gdx,
+                proj ? f.vp_dy : gdy,       proj ? P->px : s->pt,   proj ? P->px2 : P->pt2,
+                P->uss,   P->vss, f.v_bc,   gu,             gv,   f.dt,
+                f.overwrite_bc,   s->u,     s->v,           P->u2, P->v2,
+                P->proj,  P->dscal, P->esn, f.v_nx,         f.v_ny};
+    if (proj && MIX) {
+      k_correct<K, false><<<G, kThreads, 0, st>>>(ka);
+      k_split<<<G, kThreads, 0, st>>>(f.N, s->u, P->u2);
+      k_split<<<G, kThreads, 0, st>>>(f.N, s->v, P->v2);
+    } else {
+      k_correct<K, MIX><<<G, kThreads, 0, st>>>(ka);
+    }
     rc = check_cuda(ctx, cudaGetLastError(), "stage 3 kernels");
     if (rc) return rc;
     s->j += 1;
@@ -2468,6 +2645,12 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     if (stats) stats->steps += 1;
   }
   int rc = check_cuda(ctx, cudaStreamSynchronize(st), "step sync");
+  if (stats && proj && n_steps > 0 && !rc) {
+    double sx = 0.0;
+    rc = check_cuda(ctx, cudaMemcpy(&sx, P->dscal, sizeof(double), cudaMemcpyDeviceToHost),
+                    "wall flux");
+    stats->wall_flux = -f.dt * sx / P->esn_h;
+  }
   if (stats) {
     stats->launches = P->launches - launches0;
     stats->spmv_launches = P->spmv_launches;

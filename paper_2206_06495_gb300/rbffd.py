@@ -27,6 +27,8 @@ ERR_OOM = -6
 OP_INTERP, OP_DX, OP_DY, OP_LAP = 1, 2, 4, 8
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+PROJ_PAPER, PROJ_EXACT = 0, 1
+CN_PRINTED, CN_KIM_MOIN = 0, 1
 
 _ERRNAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_SINGULAR_STENCIL: "SINGULAR_STENCIL",
              ERR_NOT_CONVERGED: "NOT_CONVERGED", ERR_NONFINITE: "NONFINITE",
@@ -66,7 +68,7 @@ class FlowC(C.Structure):
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("max_iter", C.c_int32),
                 ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32), ("profile", C.c_int32),
                 ("p_edges", C.c_void_p), ("n_edges", C.c_int64), ("p_x", C.c_void_p),
-                ("p_y", C.c_void_p)]
+                ("p_y", C.c_void_p), ("projection", C.c_int32), ("cn_form", C.c_int32)]
 
 
 class StateC(C.Structure):
@@ -85,7 +87,8 @@ class Stats(C.Structure):
                 ("refinements", C.c_int64), ("helm_relres", C.c_double),
                 ("poisson_relres", C.c_double), ("launches", C.c_int64),
                 ("spmv_launches", C.c_int64), ("spmv_ms", C.c_double),
-                ("spmv_batch_launches", C.c_int64), ("spmv_batch_ms", C.c_double)]
+                ("spmv_batch_launches", C.c_int64), ("spmv_batch_ms", C.c_double),
+                ("wall_flux", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -281,6 +284,8 @@ class Flow:
     overwrite_bc: int = 1
     profile: int = 0
     precond: int = 1
+    projection: int = PROJ_PAPER
+    cn_form: int = CN_PRINTED
     _c: FlowC = field(default=None, repr=False)
 
     def cstruct(self) -> FlowC:
@@ -301,7 +306,8 @@ class Flow:
                      precond=self.precond,
                      p_edges=p("p_edges") if "p_edges" in t else None,
                      n_edges=t["p_edges"].shape[0] if "p_edges" in t else 0,
-                     p_x=p("px") if "px" in t else None, p_y=p("py") if "py" in t else None)
+                     p_x=p("px") if "px" in t else None, p_y=p("py") if "py" in t else None,
+                     projection=self.projection, cn_form=self.cn_form)
 
 
 def flow_from_nodes(ctx: Context, nodes, Re: float, dt: float, device="cuda", **kw) -> Flow:
