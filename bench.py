@@ -528,6 +528,40 @@ def run_ours(args):
                "fp64_peak_gflops": fp64_peak, "fp32_peak_gflops": fp32_peak,
                "frac": nd.N * flops_sys / wsec / 1e9 / fp64_peak if fp64_peak else None,
                "flops_per_system": flops_sys, "note": "k-NN search included in the time"}
+    # The (n, m, q) parameter study (Section 4) on a 200,000-stencil sample of
+    # this node set's V->V family: weights of D_x and the Laplacian plus their
+    # per-node relative errors on the test function, per triple, then the
+    # condition numbers of the chosen triple's local systems.
+    from paper_2206_06495_gb300.sweep import parameter_sweep
+    ns_s = min(200000, nd.N)
+    sx, sy = vx[:ns_s].contiguous(), vy[:ns_s].contiguous()
+    triples = [(28, 3, 3), (28, 5, 3), (28, 7, 3), (28, 9, 3), (28, 7, 1), (28, 7, 2),
+               (28, 7, 4), (21, 7, 3), (35, 7, 3)]
+    parameter_sweep(sx[:4096].contiguous(), sy[:4096].contiguous(), vx, vy, triples[:1])
+    torch.cuda.synchronize()
+    t0 = time.time()
+    rows = parameter_sweep(sx, sy, vx, vy, triples)
+    torch.cuda.synchronize()
+    sweep_s = time.time() - t0
+    cctx = R.Context(28, 7, 3)
+    cidx, _, _ = R.build_weights(cctx, sx, sy, vx, vy, R.OP_DX)
+    R.stencil_condition(cctx, sx[:4096].contiguous(), sy[:4096].contiguous(), vx, vy,
+                        cidx[:, :4096].contiguous())
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    cond = R.stencil_condition(cctx, sx, sy, vx, vy, cidx)
+    b.record(stream)
+    torch.cuda.synchronize()
+    cond_ms = a.elapsed_time(b)
+    sweep = {"stencils_per_triple": ns_s, "triples": len(triples), "seconds": sweep_s,
+             "stencil_triples_per_s": ns_s * len(triples) / sweep_s,
+             "timing": "wall clock around the whole sweep (context creation, k-NN, weights "
+                       "and error kernels per triple), after one warm-up triple",
+             "E": {f"{r['n']},{r['m']},{r['q']}": {"dx": float(r["E_dx"]),
+                                                    "lap": float(r["E_lap"])} for r in rows},
+             "cond_28_7_3": {"ms": cond_ms, "stencils_per_s": ns_s / (cond_ms * 1e-3),
+                             "median": float(cond.median()), "max": float(cond.max())}}
+    cctx.close()
     if rank != 0:
         return None
     if not res:
@@ -602,6 +636,7 @@ def run_ours(args):
                                            "launch inside the profiled step's solves"}},
         "spmv": spmv,
         "weights": weights,
+        "sweep": sweep,
         "clocks": sampler.summary(windows) if sampler else None,
         "failed": failed,
     }

@@ -339,6 +339,66 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
                const double* gv, int32_t n_steps, rbffd_stats* stats, cudaStream_t stream);
 
 /*
+ * rbffd_stencil_condition - condition numbers of the local systems.
+ *
+ * Section 4.2 (the histograms of cond(A_aug) used to choose q): for every
+ * alpha-node, the 1-norm condition number ||A_aug||_1 ||A_aug^-1||_1 of the
+ * augmented matrix [A P; P^T 0] of Eq. rbf_poly_compact that
+ * rbffd_build_weights factors for that node, i.e. in local coordinates
+ * (shifted to the alpha-node, scaled by the largest stencil radius), with
+ * the context's (n, m, q).  The inverse is formed from the same LU with
+ * partial pivoting (one solve per unit vector, FP64).
+ * idx        int32[n * ld]: the stencils (as written by rbffd_build_weights)
+ * cond       out: double[n_alpha]; +inf for a singular system
+ * Errors: INVALID_ARG, CUDA, OOM.  Synchronises `stream`.
+ */
+int rbffd_stencil_condition(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,
+                            const double* bx, const double* by, int64_t n_beta,
+                            const int32_t* idx, int64_t ld, double* cond, cudaStream_t stream);
+
+/*
+ * rbffd_modified_wavenumber - Eq. 2d_mw at every alpha-node.
+ *
+ * Section 4.1: for the plane wave exp(i k.x) with k = (kx, ky) and
+ * k~ = |k|, the radial derivative delta_r = (kx D_x + ky D_y) / k~ gives the
+ * modified wavenumber k* = -i delta_r{exp(i k.x)} exp(-i k.x_0).  Output
+ * k1[i] = k* / k~ (complex, interleaved re, im); when Dlap is given, also
+ * k2[i] = -D_Lap{exp(i k.x)} exp(-i k.x_0) / k~^2 (the second-derivative
+ * counterpart, 1 for an exact operator).  The phase of every stencil node is
+ * taken relative to the alpha-node.  Dx, Dy: FP64 ELL operators of the same
+ * shape (rows = alpha-nodes, columns = beta-nodes); Dlap may be NULL.
+ * ax, ay  alpha-node coordinates; bx, by  beta-node coordinates.
+ * k1, k2  out: double[2 * n_rows] (k2 ignored when Dlap is NULL).
+ * Errors: INVALID_ARG (shapes, dtype, k = 0), CUDA.  Asynchronous.
+ */
+int rbffd_modified_wavenumber(rbffd_ctx* ctx, const rbffd_ell* Dx, const rbffd_ell* Dy,
+                              const rbffd_ell* Dlap, const double* ax, const double* ay,
+                              const double* bx, const double* by, double kx, double ky,
+                              double* k1, double* k2, cudaStream_t stream);
+
+/*
+ * rbffd_stencil_error - per-node relative error of an operator (Section 4,
+ * Eq. test and Eq. relative_error).
+ *
+ * For alpha-node i the test function is g_i(x, y) = cos(x / dr_i) cos(y / dr_i)
+ * with dr_i the local spacing; the error is |(D g_i)_i - L g_i(x_i)| divided
+ * by max |L g_i| (1 for RBFFD_OP_INTERP, 1/dr_i for RBFFD_OP_DX and _DY,
+ * 2/dr_i^2 for RBFFD_OP_LAP).  The paper's E is the mean over the nodes.
+ * D        FP64 ELL operator of the operation `op` (one RBFFD_OP_* bit)
+ * dr       device double[n_rows] or NULL: NULL takes dr_i as the mean distance
+ *          from the alpha-node to stencil slots 1..6, which for a collocated
+ *          operator (slot 0 = the node itself) is the mean distance to its 6
+ *          nearest nodes; needs n >= 7
+ * err      out: double[n_rows]
+ * err_mean out (device double, may be NULL): the mean of err, summed in a
+ *          fixed order
+ * Errors: INVALID_ARG, CUDA, OOM.  Asynchronous.
+ */
+int rbffd_stencil_error(rbffd_ctx* ctx, const rbffd_ell* D, uint32_t op, const double* ax,
+                        const double* ay, const double* bx, const double* by, const double* dr,
+                        double* err, double* err_mean, cudaStream_t stream);
+
+/*
  * rbffd_debug_set_wait_limit - test hook (no counterpart in the paper): the
  * number of polls the step's kernels spend on their first wait for a tile or
  * record staged into shared memory before they give up.  polls = 0 makes

@@ -304,6 +304,62 @@ def modified_wavenumber(w_dx, w_dy, idx, ax, ay, bx, by, kx, ky):
     return (-1j * (d_r * phase_b[idx]).sum(1) * phase_a)
 
 
+def test_function_derivative(x, y, dr, op):
+    """L g at (x, y) for the test function g = cos(x/dr) cos(y/dr) of
+    Section 4 (Eq. test), with max |L g| over the plane (reading R11):
+    returns (L g, max |L g|)."""
+    cx, sx = np.cos(x / dr), np.sin(x / dr)
+    cy, sy = np.cos(y / dr), np.sin(y / dr)
+    if op == OP_DX:
+        return -sx * cy / dr, 1.0 / dr
+    if op == OP_DY:
+        return -cx * sy / dr, 1.0 / dr
+    if op == OP_LAP:
+        return -2.0 * cx * cy / dr ** 2, 2.0 / dr ** 2
+    return cx * cy, 1.0
+
+
+def stencil_error(w, idx, ax, ay, bx, by, op, dr) -> np.ndarray:
+    """Per-node relative error of Eq. relative_error: for alpha-node i and its
+    own test function g_i = cos(x/dr_i) cos(y/dr_i) (Eq. test, dr_i the local
+    spacing), |sum_s w_is g_i(x_j) - L g_i(x_i)| / max |L g_i|.  The paper's E
+    is the mean over the nodes."""
+    dr = np.asarray(dr, np.float64)
+    g = np.cos(bx[idx] / dr[:, None]) * np.cos(by[idx] / dr[:, None])
+    exact, scale = test_function_derivative(ax, ay, dr, op)
+    return np.abs((w * g).sum(1) - exact) / scale
+
+
+def stencil_condition(ax, ay, bx, by, idx, m: int, q: int) -> np.ndarray:
+    """1-norm condition number ||A_aug||_1 ||A_aug^-1||_1 of every stencil's
+    augmented matrix (Eq. rbf_poly_compact) in the local coordinates of R1,
+    the matrix the weight solve factors (Section 4.2 discusses these numbers
+    for the parameter choice).  Exact: numpy's dense inverse per stencil."""
+    ax = np.asarray(ax, np.float64)
+    ay = np.asarray(ay, np.float64)
+    out = np.empty(idx.shape[0])
+    for s0 in range(0, idx.shape[0], 2048):
+        sl = slice(s0, s0 + 2048)
+        X = np.stack([bx[idx[sl]] - ax[sl, None], by[idx[sl]] - ay[sl, None]], -1)
+        sc = np.sqrt((X[..., 0] ** 2 + X[..., 1] ** 2).max(-1))
+        A = augmented_matrix(X / sc[:, None, None], m, q)
+        out[sl] = np.linalg.cond(A, 1)
+    return out
+
+
+def modified_wavenumber_local(w_dx, w_dy, idx, ax, ay, bx, by, kx, ky, w_lap=None):
+    """Normalised modified wavenumbers k*/k~ (Eq. 2d_mw) of the first
+    derivative along the wave direction and, when w_lap is given, k*^2/k~^2
+    of the Laplacian, at every alpha-node; the phase of each stencil node is
+    taken relative to the alpha-node, exp(i k.(x_j - x_0)), which equals
+    exp(i k.x_j) exp(-i k.x_0)."""
+    kt = np.hypot(kx, ky)
+    ph = np.exp(1j * (kx * (bx[idx] - ax[:, None]) + ky * (by[idx] - ay[:, None])))
+    k1 = -1j * ((kx * w_dx + ky * w_dy) / kt * ph).sum(1) / kt
+    k2 = None if w_lap is None else -(w_lap * ph).sum(1) / (kt * kt)
+    return k1, k2
+
+
 # --------------------------------------------------------------------------
 # The fractional-step Navier-Stokes solver (Section 3)
 # --------------------------------------------------------------------------

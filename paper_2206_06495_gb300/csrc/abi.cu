@@ -3,6 +3,8 @@
 #include <new>
 #include <vector>
 
+#include <cmath>
+
 #include "common.cuh"
 
 namespace rbffd {
@@ -230,6 +232,64 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
   if (n_steps == 0) return RBFFD_OK;
   return step_run(ctx, flow, state, gu, gv, n_steps, stats, stream);
+}
+
+int rbffd_stencil_condition(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,
+                            const double* bx, const double* by, int64_t n_beta,
+                            const int32_t* idx, int64_t ld, double* cond, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (n_alpha < 0 || n_beta < ctx->prm.n || ld < n_alpha || ld % 32 || n_alpha > INT32_MAX)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad sizes");
+  if (n_alpha == 0) return RBFFD_OK;
+  if (!ax || !ay || !bx || !by || !idx || !cond)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  return cond_build(ctx, ax, ay, n_alpha, bx, by, idx, ld, cond, stream);
+}
+
+static bool ell_f64_ok(const rbffd_ell* D) {
+  return D && D->n_rows >= 0 && D->n_cols >= 1 && D->n >= 1 && D->n <= kMaxStencil &&
+         D->ld >= D->n_rows && D->ld % 32 == 0 && D->w_dtype == RBFFD_F64 &&
+         (D->n_rows == 0 || (D->idx && D->w));
+}
+
+int rbffd_modified_wavenumber(rbffd_ctx* ctx, const rbffd_ell* Dx, const rbffd_ell* Dy,
+                              const rbffd_ell* Dlap, const double* ax, const double* ay,
+                              const double* bx, const double* by, double kx, double ky,
+                              double* k1, double* k2, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ell_f64_ok(Dx) || !ell_f64_ok(Dy) || (Dlap && !ell_f64_ok(Dlap)))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad operator (FP64 ELL expected)");
+  if (Dy->n_rows != Dx->n_rows || Dy->n != Dx->n || Dy->ld != Dx->ld ||
+      Dy->n_cols != Dx->n_cols || (Dlap && (Dlap->n_rows != Dx->n_rows ||
+                                             Dlap->n_cols != Dx->n_cols)))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "operators of different shapes");
+  if (!(kx * kx + ky * ky > 0.0) || !std::isfinite(kx) || !std::isfinite(ky))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "wave vector must be finite and nonzero");
+  if (Dx->n_rows == 0) return RBFFD_OK;
+  if (!ax || !ay || !bx || !by || !k1 || (Dlap && !k2))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  return analysis_mw(ctx, Dx, Dy, Dlap, ax, ay, bx, by, kx, ky, k1, k2, stream);
+}
+
+int rbffd_stencil_error(rbffd_ctx* ctx, const rbffd_ell* D, uint32_t op, const double* ax,
+                        const double* ay, const double* bx, const double* by, const double* dr,
+                        double* err, double* err_mean, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ell_f64_ok(D)) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad operator (FP64 ELL expected)");
+  int opi = -1;
+  if (op == RBFFD_OP_INTERP) opi = 0;
+  else if (op == RBFFD_OP_DX) opi = 1;
+  else if (op == RBFFD_OP_DY) opi = 2;
+  else if (op == RBFFD_OP_LAP) opi = 3;
+  if (opi < 0) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "op must be one RBFFD_OP_* bit");
+  if (!dr && D->n < 7)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "dr from the stencil needs n >= 7");
+  if (D->n_rows == 0) return RBFFD_OK;
+  if (!ax || !ay || !bx || !by || !err) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  return analysis_error(ctx, D, opi, ax, ay, bx, by, dr, err, err_mean, stream);
 }
 
 int rbffd_debug_set_wait_limit(rbffd_ctx* ctx, int64_t polls) {

@@ -135,6 +135,14 @@ void step_plan_free(struct StepPlan* p);
 int step_set_wait_limit(rbffd_ctx* ctx, long long polls);
 int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* f, const rbffd_state* s, rbffd_adjoint* lam,
                 double* grad_gu, double* grad_gv, rbffd_stats* stats, cudaStream_t st);
+int cond_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
+               const double* by, const int32_t* idx, int64_t ld, double* cond, cudaStream_t st);
+int analysis_mw(rbffd_ctx* ctx, const rbffd_ell* Dx, const rbffd_ell* Dy, const rbffd_ell* Dl,
+                const double* ax, const double* ay, const double* bx, const double* by,
+                double kx, double ky, double* k1, double* k2, cudaStream_t st);
+int analysis_error(rbffd_ctx* ctx, const rbffd_ell* D, int op, const double* ax,
+                   const double* ay, const double* bx, const double* by, const double* dr,
+                   double* err, double* mean, cudaStream_t st);
 // allocation-free variants on caller-provided device scratch (status codes only)
 size_t knn_scratch_bytes(int64_t nb, int64_t max_cells);
 int knn_build_scratch(const double* ax, const double* ay, int64_t na, const double* bx,

@@ -73,6 +73,19 @@ __device__ __forceinline__ double rhs_value(int op, int row, int n, int m, doubl
   }
 }
 
+// Magnitude of a double as an ordered integer key: for non-negative values
+// the IEEE bit pattern orders like the value, so the pivot search compares
+// integers instead of spending FP64 instructions (NaN, with the largest
+// patterns, wins and is then caught as a singular pivot).
+__device__ __forceinline__ unsigned long long mag_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// One warp per stencil.  COND = false: the weights of the requested operators
+// (right-hand sides per rhs_value), written to w.  COND = true: the 1-norm
+// condition number ||A_aug||_1 ||A_aug^-1||_1 of the same local system (the
+// right-hand sides are the S unit vectors, nrhs = S), written to w[i].
+template <bool COND>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
     weights_kernel(const double* __restrict__ ax, const double* __restrict__ ay, int64_t na,
                    const double* __restrict__ bx, const double* __restrict__ by,
@@ -83,13 +96,15 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int np = q < 0 ? 0 : (q + 1) * (q + 2) / 2;
   const int S = n + np, NC = S + nrhs;
-  double* Am = smem + (size_t)wib * (LD * NC + 2 * kMaxStencil);
+  double* Am = smem + (size_t)wib * (LD * NC + 2 * n + S);
   double* xs = Am + LD * NC;
-  double* ys = xs + kMaxStencil;
+  double* ys = xs + n;
+  double* invd = ys + n;  // reciprocals of U's diagonal
   const int op_of[4] = {ops.x, ops.y, ops.z, ops.w};
   const int wpb = blockDim.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * wpb + wib;
   const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  const int npair = n * (n - 1) / 2;
   for (int64_t i = gw; i < na; i += nwarps) {
     const double cx = ax[i], cy = ay[i];
     double r2max = 0.0;
@@ -102,61 +117,86 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
     }
     for (int o = 16; o > 0; o >>= 1) r2max = fmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
     const double sc = sqrt(r2max);
+    const double isc = 1.0 / sc;
     __syncwarp();
     for (int s = lane; s < n; s += 32) {
-      xs[s] = xs[s] / sc;
-      ys[s] = ys[s] / sc;
+      xs[s] = xs[s] * isc;
+      ys[s] = ys[s] * isc;
     }
     __syncwarp();
-    // ---- assemble [A P; P^T 0 | rhs] column-major: element (r, c) at Am[c*LD + r]
+    // ---- assemble [A P; P^T 0 | rhs] column-major: element (r, c) at Am[c*LD + r].
+    // A is symmetric with phi(0) = 0 on its diagonal: each pair (r < c) is
+    // evaluated once and stored twice.
     double amax = 0.0;
-    for (int e = lane; e < S * S; e += 32) {
-      const int c = e / S, r = e - c * S;
-      double v;
-      if (r < n && c < n) {
-        const double dx = xs[r] - xs[c], dy = ys[r] - ys[c];
-        v = phs_from_r2(dx * dx + dy * dy, m);
-      } else if (r < n) {  // P block: row r (node), column c (monomial c - n)
-        int a, b;
-        monomial(c - n, a, b);
-        v = ipow(xs[r], a) * ipow(ys[r], b);
-      } else if (c < n) {  // P^T block
-        int a, b;
-        monomial(r - n, a, b);
-        v = ipow(xs[c], a) * ipow(ys[c], b);
-      } else {
-        v = 0.0;
-      }
+    for (int p = lane; p < npair; p += 32) {
+      int c = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+      while (c * (c - 1) / 2 > p) --c;
+      while (c * (c + 1) / 2 <= p) ++c;
+      const int r = p - c * (c - 1) / 2;
+      const double dx = xs[r] - xs[c], dy = ys[r] - ys[c];
+      const double v = phs_from_r2(dx * dx + dy * dy, m);
       Am[c * LD + r] = v;
+      Am[r * LD + c] = v;
       amax = fmax(amax, fabs(v));
     }
-    for (int e = lane; e < S * nrhs; e += 32) {
-      const int o = e / S, r = e - o * S;
-      const double X = r < n ? xs[r] : 0.0, Y = r < n ? ys[r] : 0.0;
-      Am[(S + o) * LD + r] = rhs_value(op_of[o], r, n, m, X, Y);
+    for (int r = lane; r < n; r += 32) Am[r * LD + r] = 0.0;
+    for (int e = lane; e < n * np; e += 32) {  // P (row r, monomial t) and P^T
+      const int t = e / n, r = e - t * n;
+      int a, b;
+      monomial(t, a, b);
+      const double v = ipow(xs[r], a) * ipow(ys[r], b);
+      Am[(n + t) * LD + r] = v;
+      Am[r * LD + n + t] = v;
+      amax = fmax(amax, fabs(v));
+    }
+    for (int e = lane; e < np * np; e += 32) {
+      const int c = e / np, r = e - c * np;
+      Am[(n + c) * LD + n + r] = 0.0;
+    }
+    if (COND) {
+      for (int e = lane; e < S * S; e += 32) {
+        const int o = e / S, r = e - o * S;
+        Am[(S + o) * LD + r] = r == o ? 1.0 : 0.0;
+      }
+    } else {
+      for (int e = lane; e < S * nrhs; e += 32) {
+        const int o = e / S, r = e - o * S;
+        const double X = r < n ? xs[r] : 0.0, Y = r < n ? ys[r] : 0.0;
+        Am[(S + o) * LD + r] = rhs_value(op_of[o], r, n, m, X, Y);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     __syncwarp();
+    double anorm = 0.0;  // ||A_aug||_1, the largest column sum
+    if (COND) {
+      for (int c = lane; c < S; c += 32) {
+        double cs = 0.0;
+        for (int r = 0; r < S; ++r) cs += fabs(Am[c * LD + r]);
+        anorm = fmax(anorm, cs);
+      }
+      for (int o = 16; o > 0; o >>= 1) anorm = fmax(anorm, __shfl_xor_sync(0xffffffffu, anorm, o));
+    }
     // ---- elimination with partial pivoting
     bool singular = false;
     for (int kk = 0; kk < S; ++kk) {
-      double bv = -1.0;
+      unsigned long long bk = 0ull;
       int br = S;
       for (int r = kk + lane; r < S; r += 32) {
-        const double v = fabs(Am[kk * LD + r]);
-        if (v > bv) {
-          bv = v;
+        const unsigned long long key = mag_key(Am[kk * LD + r]);
+        if (br == S || key > bk) {
+          bk = key;
           br = r;
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
         const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-        if (ov > bv || (ov == bv && orr < br)) {
-          bv = ov;
+        if (ok > bk || (ok == bk && orr < br)) {
+          bk = ok;
           br = orr;
         }
       }
+      const double bv = __longlong_as_double((long long)bk);
       if (!(bv > 1e-14 * amax) || !isfinite(bv)) {
         singular = true;
         break;
@@ -170,6 +210,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
       }
       __syncwarp();
       const double inv = 1.0 / Am[kk * LD + kk];
+      if (lane == 0) invd[kk] = inv;
       for (int r = kk + 1 + lane; r < S; r += 32) Am[kk * LD + r] *= inv;
       __syncwarp();
       const int R = S - 1 - kk, C = NC - 1 - kk;
@@ -181,16 +222,21 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
     }
     if (singular) {
       if (lane == 0) atomicMin(bad, (unsigned long long)i);
-      for (int e = lane; e < nrhs * n; e += 32) {
-        const int o = e / n, s = e - o * n;
-        w[(int64_t)o * n * ld + (int64_t)s * ld + i] = 0.0;
+      if (COND) {
+        if (lane == 0) w[i] = INFINITY;
+      } else {
+        for (int e = lane; e < nrhs * n; e += 32) {
+          const int o = e / n, s = e - o * n;
+          w[(int64_t)o * n * ld + (int64_t)s * ld + i] = 0.0;
+        }
       }
       __syncwarp();
       continue;
     }
     // ---- back substitution on the upper triangle, all right-hand sides
     for (int c = S - 1; c >= 0; --c) {
-      if (lane < nrhs) Am[(S + lane) * LD + c] /= Am[c * LD + c];
+      const double ic = invd[c];
+      for (int o = lane; o < nrhs; o += 32) Am[(S + o) * LD + c] *= ic;
       __syncwarp();
       for (int p = lane; p < c * nrhs; p += 32) {
         const int o = p / c, r = p - o * c;
@@ -198,17 +244,44 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
       }
       __syncwarp();
     }
+    if (COND) {
+      double inorm = 0.0;  // ||A_aug^-1||_1 from the solved unit vectors
+      for (int o = lane; o < S; o += 32) {
+        double cs = 0.0;
+        for (int r = 0; r < S; ++r) cs += fabs(Am[(S + o) * LD + r]);
+        inorm = fmax(inorm, cs);
+      }
+      for (int o = 16; o > 0; o >>= 1) inorm = fmax(inorm, __shfl_xor_sync(0xffffffffu, inorm, o));
+      if (lane == 0) w[i] = anorm * inorm;
+      __syncwarp();
+      continue;
+    }
     // ---- unscale and store w (the first n entries of each solution)
     for (int e = lane; e < nrhs * n; e += 32) {
       const int o = e / n, s = e - o * n;
       const int op = op_of[o];
       double v = Am[(S + o) * LD + s];
-      if (op == 1 || op == 2) v /= sc;
-      else if (op == 3) v /= (sc * sc);
+      if (op == 1 || op == 2) v *= isc;
+      else if (op == 3) v *= isc * isc;
       w[(int64_t)o * n * ld + (int64_t)s * ld + i] = v;
     }
     __syncwarp();
   }
+}
+
+// shared memory of one warp (the system with its right-hand sides, the local
+// coordinates and the pivot reciprocals) and the launch shape
+struct WShape {
+  int LD, wpb;
+  size_t smem;
+};
+inline WShape weights_shape(int n, int S, int nrhs) {
+  WShape sh;
+  sh.LD = (S % 2) ? S : S + 1;
+  const size_t per_warp = sizeof(double) * ((size_t)sh.LD * (S + nrhs) + 2 * n + S);
+  sh.wpb = (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / per_warp));
+  sh.smem = per_warp * sh.wpb;
+  return sh;
 }
 
 }  // namespace
@@ -223,12 +296,11 @@ int weights_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na
   int nrhs = 0;
   for (int b = 0; b < 4; ++b)
     if (op_mask & (1u << b)) opv[nrhs++] = b;
-  const int LD = (S % 2) ? S : S + 1;
-  const size_t per_warp = sizeof(double) * ((size_t)LD * (S + nrhs) + 2 * kMaxStencil);
-  const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / per_warp));
-  const size_t smem = per_warp * wpb;
+  const WShape sh = weights_shape(n, S, nrhs);
+  const int LD = sh.LD, wpb = sh.wpb;
+  const size_t smem = sh.smem;
   int rc = check_cuda(ctx,
-                      cudaFuncSetAttribute(weights_kernel,
+                      cudaFuncSetAttribute(weights_kernel<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                       "weights smem attribute");
   if (rc) return rc;
@@ -241,7 +313,7 @@ int weights_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na
   const int sms = sm_count();
   const int64_t need = (na + wpb - 1) / wpb;
   const int blocks = (int)std::min<int64_t>(need, (int64_t)sms * 16);
-  weights_kernel<<<blocks, wpb * 32, smem, st>>>(
+  weights_kernel<false><<<blocks, wpb * 32, smem, st>>>(
       ax, ay, na, bx, by, idx, ld, n, m, q, nrhs, make_int4(opv[0], opv[1], opv[2], opv[3]), LD,
       w, d_bad);
   rc = check_cuda(ctx, cudaGetLastError(), "weights kernel");
@@ -277,12 +349,10 @@ int weights_build_scratch(int n, int m, int q, const double* ax, const double* a
   int nrhs = 0;
   for (int b = 0; b < 4; ++b)
     if (op_mask & (1u << b)) opv[nrhs++] = b;
-  const int LD = (S % 2) ? S : S + 1;
-  const size_t per_warp = sizeof(double) * ((size_t)LD * (S + nrhs) + 2 * kMaxStencil);
-  const int wpb =
-      (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / per_warp));
-  const size_t smem = per_warp * wpb;
-  if (cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const WShape sh = weights_shape(n, S, nrhs);
+  const int LD = sh.LD, wpb = sh.wpb;
+  const size_t smem = sh.smem;
+  if (cudaFuncSetAttribute(weights_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return RBFFD_ERR_CUDA;
   // the status word keeps the previous call's value: reset it
@@ -291,9 +361,10 @@ int weights_build_scratch(int n, int m, int q, const double* ax, const double* a
   const int sms = sm_count();
   const int64_t need = (na + wpb - 1) / wpb;
   const int blocks = (int)std::min<int64_t>(need, (int64_t)sms * 16);
-  weights_kernel<<<blocks, wpb * 32, smem, st>>>(ax, ay, na, bx, by, idx, ld, n, m, q, nrhs,
-                                                 make_int4(opv[0], opv[1], opv[2], opv[3]), LD,
-                                                 w, d_bad);
+  weights_kernel<false><<<blocks, wpb * 32, smem, st>>>(ax, ay, na, bx, by, idx, ld, n, m, q,
+                                                        nrhs,
+                                                        make_int4(opv[0], opv[1], opv[2], opv[3]),
+                                                        LD, w, d_bad);
   unsigned long long h_bad = 0;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -304,6 +375,40 @@ int weights_build_scratch(int n, int m, int q, const double* ax, const double* a
     return RBFFD_ERR_SINGULAR_STENCIL;
   }
   return RBFFD_OK;
+}
+
+}  // namespace rbffd
+
+namespace rbffd {
+
+// 1-norm condition numbers of the local systems the weight solves factor
+// (rbffd_stencil_condition): the weight kernel in its COND mode.
+int cond_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
+               const double* by, const int32_t* idx, int64_t ld, double* cond,
+               cudaStream_t st) {
+  const int n = ctx->prm.n, m = ctx->prm.m, q = ctx->prm.q;
+  const int np = q < 0 ? 0 : (q + 1) * (q + 2) / 2;
+  const int S = n + np;
+  const WShape sh = weights_shape(n, S, S);
+  int rc = check_cuda(ctx,
+                      cudaFuncSetAttribute(weights_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sh.smem),
+                      "condition smem attribute");
+  if (rc) return rc;
+  void* base = nullptr;
+  rc = ctx_scratch(ctx, 256, &base);
+  if (rc) return rc;
+  unsigned long long* d_bad = (unsigned long long*)base;
+  rc = check_cuda(ctx, cudaMemsetAsync(d_bad, 0xff, sizeof(unsigned long long), st), "memset");
+  if (rc) return rc;
+  const int64_t need = (na + sh.wpb - 1) / sh.wpb;
+  const int blocks = (int)std::min<int64_t>(need, (int64_t)sm_count() * 16);
+  weights_kernel<true><<<blocks, sh.wpb * 32, sh.smem, st>>>(
+      ax, ay, na, bx, by, idx, ld, n, m, q, S, make_int4(0, 0, 0, 0), sh.LD, cond, d_bad);
+  rc = check_cuda(ctx, cudaGetLastError(), "condition kernel");
+  if (rc) return rc;
+  return check_cuda(ctx, cudaStreamSynchronize(st), "condition sync");
 }
 
 }  // namespace rbffd

@@ -117,6 +117,16 @@ PROTOTYPES = {
     "rbffd_probe_fma": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                   C.c_void_p]),
     "rbffd_debug_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "rbffd_stencil_condition": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_int64, C.c_void_p, C.c_void_p]),
+    "rbffd_modified_wavenumber": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.POINTER(Ell),
+                                            C.POINTER(Ell), C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_stencil_error": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_uint32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_apply_op": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "rbffd_apply_op_shape": (C.c_int, [C.c_void_p, C.POINTER(Ell), C.c_int32,
@@ -388,6 +398,53 @@ def step(ctx: Context, flow: Flow, state: State, gu, gv, n_steps: int = 1) -> di
         e.stats = st.as_dict()
         raise
     return st.as_dict()
+
+
+def _ell(idx, w, n_rows: int, n_cols: int) -> Ell:
+    torch = _torch()
+    return Ell(idx=_ptr(idx).value, w=_ptr(w).value, n_rows=n_rows, n_cols=n_cols,
+               ld=idx.shape[1], n=idx.shape[0], w_dtype=F64 if w.dtype == torch.float64 else F32)
+
+
+def stencil_condition(ctx: Context, ax, ay, bx, by, idx):
+    """rbffd_stencil_condition: 1-norm condition number of every stencil's
+    local system (float64 [n_alpha])."""
+    torch = _torch()
+    na = ax.numel()
+    cond = torch.empty(na, dtype=torch.float64, device=ax.device)
+    ctx.check(lib().rbffd_stencil_condition(ctx.handle, _ptr(ax), _ptr(ay), na, _ptr(bx),
+                                            _ptr(by), bx.numel(), _ptr(idx), idx.shape[1],
+                                            _ptr(cond), _stream()))
+    return cond
+
+
+def modified_wavenumber(ctx: Context, idx, wx, wy, ax, ay, bx, by, kx: float, ky: float,
+                        idx_lap=None, w_lap=None):
+    """rbffd_modified_wavenumber: (k*/k~, k*^2/k~^2 or None) as complex128 tensors."""
+    torch = _torch()
+    n = ax.numel()
+    Dx, Dy = _ell(idx, wx, n, bx.numel()), _ell(idx, wy, n, bx.numel())
+    Dl = _ell(idx_lap, w_lap, n, bx.numel()) if w_lap is not None else None
+    k1 = torch.empty(2 * n, dtype=torch.float64, device=ax.device)
+    k2 = torch.empty(2 * n, dtype=torch.float64, device=ax.device) if Dl else None
+    ctx.check(lib().rbffd_modified_wavenumber(
+        ctx.handle, C.byref(Dx), C.byref(Dy), C.byref(Dl) if Dl else None, _ptr(ax), _ptr(ay),
+        _ptr(bx), _ptr(by), kx, ky, _ptr(k1), _ptr(k2), _stream()))
+    as_c = lambda t: torch.view_as_complex(t.view(n, 2))  # noqa: E731
+    return as_c(k1), (as_c(k2) if k2 is not None else None)
+
+
+def stencil_error(ctx: Context, idx, w, op: int, ax, ay, bx, by, dr=None):
+    """rbffd_stencil_error: (per-node relative error, its mean as a 0-d tensor)."""
+    torch = _torch()
+    n = ax.numel()
+    D = _ell(idx, w, n, bx.numel())
+    err = torch.empty(n, dtype=torch.float64, device=ax.device)
+    mean = torch.zeros((), dtype=torch.float64, device=ax.device)
+    ctx.check(lib().rbffd_stencil_error(ctx.handle, C.byref(D), op, _ptr(ax), _ptr(ay),
+                                        _ptr(bx), _ptr(by), _ptr(dr), _ptr(err), _ptr(mean),
+                                        _stream()))
+    return err, mean
 
 
 def debug_set_wait_limit(ctx: Context, polls: int) -> None:

@@ -234,6 +234,87 @@ def test_modified_wavenumber_within_paper_bound():
         assert np.abs(ks[inner] / kt - 1).max() < 1e-5
 
 
+# ------------------------------------------- parameter study (Section 4)
+@pytest.fixture(scope="module")
+def sweep_nodes():
+    nd = ns.jittered_cavity(40, 0)
+    x, y = nd.vx, nd.vy
+    inner = (x > 0.2) & (x < 0.8) & (y > 0.2) & (y < 0.8)
+    return x, y, inner, O.local_spacing(x, y)
+
+
+def _mean_error(sweep_nodes, n, m, q, op):
+    x, y, inner, dr = sweep_nodes
+    idx, W = O.build_weights(x[inner], y[inner], x, y, n, m, q, (op,))
+    return O.stencil_error(W[op], idx, x[inner], y[inner], x, y, op, dr[inner]).mean()
+
+
+def test_test_function_derivatives_against_finite_differences():
+    """The closed forms of L g (Eq. test) against central differences of g."""
+    rng = np.random.default_rng(2)
+    x, y = rng.random(50), rng.random(50)
+    dr, eps = 0.07, 1e-5
+    g = lambda a, b: np.cos(a / dr) * np.cos(b / dr)  # noqa: E731
+    fd = {O.OP_DX: (g(x + eps, y) - g(x - eps, y)) / (2 * eps),
+          O.OP_DY: (g(x, y + eps) - g(x, y - eps)) / (2 * eps),
+          O.OP_LAP: (g(x + eps, y) + g(x - eps, y) + g(x, y + eps) + g(x, y - eps)
+                     - 4 * g(x, y)) / eps ** 2,
+          O.OP_INTERP: g(x, y)}
+    for op, ref in fd.items():
+        val, scale = O.test_function_derivative(x, y, dr, op)
+        assert np.abs(val - ref).max() < 1e-4 * scale, op
+        assert np.abs(val).max() <= scale * (1 + 1e-12)
+
+
+def test_parameter_study_trends(sweep_nodes):
+    """Section 4.1-4.2 on a jittered lattice: the relative error E of D_x
+    falls as the PHS exponent grows from 3 to 7 and as the stencil grows, and
+    for n = 28, m = 7 it falls from q = 1 to q = 3 while q = 4 brings no gain
+    (the paper's reasons for (n, m, q) = (28, 7, 3))."""
+    e = {t: _mean_error(sweep_nodes, *t, O.OP_DX)
+         for t in ((28, 3, 3), (28, 5, 3), (28, 7, 3), (28, 7, 1), (28, 7, 4), (21, 7, 3),
+                   (35, 7, 3))}
+    assert e[(28, 3, 3)] > e[(28, 5, 3)] > e[(28, 7, 3)], e
+    assert e[(21, 7, 3)] > e[(28, 7, 3)] > e[(35, 7, 3)], e
+    assert e[(28, 7, 1)] > 1.2 * e[(28, 7, 3)] and e[(28, 7, 4)] >= e[(28, 7, 3)], e
+
+
+def test_condition_number_definition_and_invariance(sweep_nodes):
+    """The oracle's 1-norm condition number equals the definition written
+    out with a plain Gauss-Jordan inverse on a small stencil, is unchanged by
+    shifting and scaling the nodes (R1), and grows with the PHS exponent m
+    (Section 4.2: m = 11 is numerically unstable)."""
+    x, y, inner, _ = sweep_nodes
+    idx = O.knn(x[:3], y[:3], x, y, 6)
+    c = O.stencil_condition(x[:3], y[:3], x, y, idx, 3, 1)
+    for i in range(3):
+        X = np.stack([x[idx[i]] - x[i], y[idx[i]] - y[i]], -1)
+        X = X / np.sqrt((X ** 2).sum(1).max())
+        A = O.augmented_matrix(X, 3, 1).tolist()
+        S = len(A)
+        aug = [row[:] + [1.0 if r == c2 else 0.0 for c2 in range(S)] for r, row in enumerate(A)]
+        for col in range(S):
+            piv = max(range(col, S), key=lambda r: abs(aug[r][col]))
+            aug[col], aug[piv] = aug[piv], aug[col]
+            pv = aug[col][col]
+            aug[col] = [v / pv for v in aug[col]]
+            for r in range(S):
+                if r != col:
+                    f = aug[r][col]
+                    aug[r] = [a - f * b for a, b in zip(aug[r], aug[col])]
+        inv_norm = max(sum(abs(aug[r][S + c2]) for r in range(S)) for c2 in range(S))
+        a_norm = max(sum(abs(A[r][c2]) for r in range(S)) for c2 in range(S))
+        assert abs(c[i] / (a_norm * inv_norm) - 1) < 1e-9
+    sel = np.nonzero(inner)[0][:200]
+    idx = O.knn(x[sel], y[sel], x, y, 28)
+    c1 = O.stencil_condition(x[sel], y[sel], x, y, idx, 7, 3)
+    c2 = O.stencil_condition(x[sel] * 1e-3 + 5, y[sel] * 1e-3 - 2, x * 1e-3 + 5, y * 1e-3 - 2,
+                             idx, 7, 3)
+    assert np.abs(c1 / c2 - 1).max() < 1e-8
+    med = [np.median(O.stencil_condition(x[sel], y[sel], x, y, idx, m, 3)) for m in (3, 5, 7, 9)]
+    assert med[0] < med[1] < med[2] < med[3], med
+
+
 # ---------------------------------------------------------------- the step
 def _tg(x, y, t, Re):
     e = np.exp(-2 * t / Re)
