@@ -47,8 +47,8 @@ def parse():
                     help="untimed steps from rest before the warm-up steps (a developed "
                          "start; the pressure iteration count of the first steps is not typical)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-variants", action="store_true",
-                    help="skip timing the exactly projecting step beside the paper's")
+    ap.add_argument("--variants", action="store_true",
+                    help="also time the exactly projecting step beside the paper's")
     ap.add_argument("--inner-tol", type=float, default=5e-3,
                     help="relative tolerance of the FP32 inner solves (MIXED)")
     ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both")
@@ -441,7 +441,7 @@ def run_ours(args):
     # same way (spin-up, warm-up, device-resident steps); reported beside the
     # paper's step, not as the headline.
     variants = {}
-    if not args.no_variants and flows:
+    if args.variants and flows:
         b0 = next(iter(flows.values()))
         for name, prec in (("mixed", R.PREC_MIXED), ("fp64", R.PREC_FP64)):
             if args.only not in ("both", name):

@@ -103,6 +103,23 @@ struct Acc<float> {
   using t = float;
 };
 
+// Self-checks of a diagnostic build (-DRBFFD_SELF_CHECK): an index outside
+// its array is reported (first few, with the site, row and index) and the
+// access is skipped instead of made.
+#ifdef RBFFD_SELF_CHECK
+__device__ int g_check_prints = 0;
+__device__ __forceinline__ bool index_ok(long long j, long long n, int site, long long row) {
+  if (j >= 0 && j < n) return true;
+  if (atomicAdd(&g_check_prints, 1) < 20)
+    printf("[rbffd self-check] site %d row %lld index %lld bound %lld\n", site, row, j, n);
+  return false;
+}
+#define RBFFD_CHECK(j, n, site, row) \
+  if (!index_ok((long long)(j), (long long)(n), (site), (long long)(row))) continue
+#else
+#define RBFFD_CHECK(j, n, site, row)
+#endif
+
 // sum_s w[s][i] * x[idx[s][i]] for one or two vectors sharing the stencil,
 // accumulated in the precision of the vectors
 template <int K, int NRHS, typename TW, typename TV>
@@ -115,6 +132,7 @@ __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, co
 #pragma unroll(K > 0 ? K : 1)
   for (int s = 0; s < k; ++s) {
     const int j = op.idx[s * op.ld + i];
+    if (K == 0) RBFFD_CHECK(j, op.n, 1, i);
     const A w = (A)op.w[s * op.ld + i];
 #pragma unroll
     for (int r = 0; r < NRHS; ++r) acc[r] += w * (A)x[r][j];
@@ -1012,7 +1030,10 @@ __global__ void __launch_bounds__(kThreads)
       ZAcc<TW, TV> acc;
       const int kk = K > 0 ? K : op.k;
 #pragma unroll(K > 0 ? K : 1)
-      for (int q = 0; q < kk; ++q) acc.add(op.w[q * op.ld + i], z[op.idx[q * op.ld + i]]);
+      for (int q = 0; q < kk; ++q) {
+        RBFFD_CHECK(op.idx[q * op.ld + i], op.n, 2, i);
+        acc.add(op.w[q * op.ld + i], z[op.idx[q * op.ld + i]]);
+      }
       finish_row(i, (TV)acc.get());
     }
   }
@@ -1555,6 +1576,7 @@ __global__ void __launch_bounds__(128)
     double dw = 0.0;
     for (int s = 0; s < k; ++s) {
       const int32_t v = pv_idx[s * ld_p + i];
+      RBFFD_CHECK(v, ld_v, 3, i);
       const double ax = pv_dx[s * ld_p + i], ay = pv_dy[s * ld_p + i];
       if (v_bc[v]) {
         dw += ax * v_nx[v] + ay * v_ny[v];
@@ -1562,6 +1584,7 @@ __global__ void __launch_bounds__(128)
       }
       for (int t = 0; t < k; ++t) {
         const int32_t c = vp_idx[t * ld_v + v];
+        RBFFD_CHECK(c, M, 4, i);
         const double wt = ax * vp_dx[t * ld_v + v] + ay * vp_dy[t * ld_v + v];
         int q = 0;
         while (q < nc && cols[q] != c) ++q;
