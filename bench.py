@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", action="store_true",
                     help="also time the exactly projecting step beside the paper's")
-    ap.add_argument("--inner-tol", type=float, default=5e-3,
+    ap.add_argument("--inner-tol", type=float, default=1e-2,
                     help="relative tolerance of the FP32 inner solves (MIXED)")
     ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both")
     ap.add_argument("--profile-ops", action="store_true",

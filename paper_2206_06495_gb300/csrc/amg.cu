@@ -451,12 +451,13 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
   if ((rc = upload(ctx, a, hX, &a->Xc, st))) return fail(rc);
   // level-0 scaling: the scaled pressure rows approximate rows of G divided by diag(G)
   // (stored in the level-0 order: entry p belongs to P-node oldi[0][p])
-  std::vector<float> hc(M), hce(M);
+  std::vector<float> hc(M), hce(M), hcn(M);
   double ces = 0.0;
   for (int64_t p = 0; p < M; ++p) {
     const int32_t i = oldi[0][p];
     const double ci = diag_a[i] != 0.0 ? L[0].diag[p] / diag_a[i] : L[0].diag[p];
     hc[p] = (float)ci;
+    hcn[i] = (float)ci;
     hce[p] = (float)(ci * es[i]);
   }
   for (int64_t i = 0; i < M; ++i) {  // in P-node order, like the scalar it normalises
@@ -468,7 +469,8 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
                                                                   "pressure rank-one column is zero"));
   a->inv_ces = 1.0 / ces;
   a->inv_R = 1.0 / (double)M;
-  if ((rc = upload(ctx, a, hc, &a->c, st)) || (rc = upload(ctx, a, hce, &a->ce, st)) ||
+  if ((rc = upload(ctx, a, hc, &a->c, st)) || (rc = upload(ctx, a, hcn, &a->cnode, st)) ||
+      (rc = upload(ctx, a, hce, &a->ce, st)) ||
       (rc = aalloc(ctx, a, &a->zp, M)) || (rc = aalloc(ctx, a, &a->zs, M)) ||
       (rc = aalloc(ctx, a, &a->zpd, M)) || (rc = aalloc(ctx, a, &a->zsd, M)))
     return fail(rc);

@@ -85,7 +85,8 @@ struct Amg {
   int64_t nc = 0;
   // level-0 map of a residual v of the scaled pressure system: r0 = c v - mu ce,
   // mu = (c . v) / (c . es); the result is z + mu / M (see step.cu)
-  float* c = nullptr;   // [M] diag(G) / diag(A)
+  float* c = nullptr;   // [M] diag(G) / diag(A), in the level-0 order
+  float* cnode = nullptr;  // [M] the same in P-node order (for (c . v) of Krylov vectors)
   float* ce = nullptr;  // [M] c * es
   float *zp = nullptr, *zs = nullptr;     // [M] V-cycle results for p and s (B v = z + kap), FP32 solves
   double *zpd = nullptr, *zsd = nullptr;  // the same for FP64 solves

@@ -1928,7 +1928,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     TRY(to32(ctx, p, f.vv_dx, nv, &p->vv_dx32, st));
     TRY(to32(ctx, p, f.vv_dy, nv, &p->vv_dy32, st));
     TRY(to32(ctx, p, f.vv_lap, nv, &p->vv_lap32, st));
-    TRY(to32(ctx, p, f.pp_lap, np, &p->pp_lap32, st));
+    TRY(to32(ctx, p, f.pp_lap, f.ld_p * p->k, &p->pp_lap32, st));  // the caller's width
     TRY(to32(ctx, p, f.vp_dx, nv, &p->vp_dx32, st));
     TRY(to32(ctx, p, f.vp_dy, nv, &p->vp_dy32, st));
     TRY(palloc(ctx, p, &p->u2, f.N));
@@ -2156,7 +2156,9 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   }
   if (pc && (NRHS != 1 || !RANK1 || op.rdot || !op.a1))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "multigrid preconditioner: pressure solves only");
-  const float* pcc = pc ? pc->c : nullptr;
+  // (c . v) of the rank-one completion pairs c with v node by node: the
+  // P-node-ordered copy of c (the V-cycle's input map uses the level-0 one)
+  const float* pcc = pc ? pc->cnode : nullptr;
   const int vc_launches = pc ? 2 * pc->nlev : 0;
   const int G = P->grid;
   double* sigx = P->dscal;

@@ -214,13 +214,15 @@ def test_step_config0_500_steps(R, ctx, precision, tol):
     dv = np.abs(st.v.cpu().numpy() - s.v).max()
     assert du < tol and dv < tol, (du, dv, stats)
     # the other fields of the state, relative to their size: the FP64 path to
-    # 1e-8 throughout; mixed precision to 1e-6 for the convective terms and to
-    # 1e-5 for the pressures (the FP32 weights of the explicit convection leave
-    # about 1.4e-6 in p~, which the pressure solve does not damp)
+    # 1e-8 throughout.  Mixed precision: the convective terms C_{j-1} are
+    # products of FP32-weight derivative stencils, each of the k = 28 weights
+    # rounded by 2^-24, so they are good to about k 2^-24 = 1.7e-6 of their
+    # scale; they and the pressures (which that rounding reaches through the
+    # divergence, undamped by the pressure solve) are held to 1e-5
     ptol = tol if precision == 0 else 1e-5
     for name, got, ref, t in (("pt", st.pt, s.pt, ptol), ("p", st.p, s.p, ptol),
-                              ("cu_prev", st.cu_prev, s.cu_prev, tol),
-                              ("cv_prev", st.cv_prev, s.cv_prev, tol)):
+                              ("cu_prev", st.cu_prev, s.cu_prev, ptol),
+                              ("cv_prev", st.cv_prev, s.cv_prev, ptol)):
         err = np.abs(got.cpu().numpy() - ref).max() / np.abs(ref).max()
         assert err < t, (name, err)
 
