@@ -412,6 +412,30 @@ int rbffd_stencil_error(rbffd_ctx* ctx, const rbffd_ell* D, uint32_t op, const d
 int rbffd_debug_set_wait_limit(rbffd_ctx* ctx, int64_t polls);
 
 /*
+ * rbffd_ensemble_step - advance an ensemble of independent flows that share
+ * one node set and its operators (the batching of many flows at once; the
+ * paper runs one flow at a time).  Member e is the step of rbffd_step
+ * (Section 3, the paper's projection) with Reynolds number Re[e] and its own
+ * wall data, in the MIXED design (FP32 explicit stages and inner Krylov
+ * solves, FP64 refinement of both implicit solves to flow->tol).  Every
+ * operator is read once per row for all members.
+ * flow       the shared flow description (flow->Re and flow->precision are
+ *            not used; projection must be RBFFD_PROJ_PAPER)
+ * n_members  E, a power of two from 1 to 64
+ * Re         HOST double[E]
+ * state      member-contiguous device arrays: u, v, cu_prev, cv_prev hold
+ *            double[N * E] with member e of V-node i at [i * E + e]; pt, p hold
+ *            double[M * E]; j is shared by the members
+ * gu, gv     device double[N * E], wall data of every member (same layout)
+ * Errors: INVALID_ARG, NOT_CONVERGED, NONFINITE, CUDA, OOM.  Synchronises
+ * `stream`; stats (HOST, may be NULL) sums the Krylov iterations over the
+ * batched solves (one iteration advances every member).
+ */
+int rbffd_ensemble_step(rbffd_ctx* ctx, const rbffd_flow* flow, int32_t n_members,
+                        const double* Re, rbffd_state* state, const double* gu, const double* gv,
+                        int32_t n_steps, rbffd_stats* stats, cudaStream_t stream);
+
+/*
  * rbffd_probe_fma - measured FMA throughput of the device (no counterpart in
  * the paper): 8 independent FMA chains per thread, 8 blocks of 256 threads
  * per SM, `iters` FMAs per chain, timed with CUDA events on `stream`.

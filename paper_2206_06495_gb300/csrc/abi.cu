@@ -82,6 +82,7 @@ int rbffd_create(rbffd_ctx** ctx, const rbffd_params* p) {
 int rbffd_destroy(rbffd_ctx* ctx) {
   if (!ctx) return RBFFD_OK;
   if (ctx->plan) step_plan_free(ctx->plan);
+  if (ctx->ens) ens_plan_free(ctx->ens);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   delete ctx;
@@ -232,6 +233,30 @@ int rbffd_step(rbffd_ctx* ctx, const rbffd_flow* flow, rbffd_state* state, const
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
   if (n_steps == 0) return RBFFD_OK;
   return step_run(ctx, flow, state, gu, gv, n_steps, stats, stream);
+}
+
+int rbffd_ensemble_step(rbffd_ctx* ctx, const rbffd_flow* flow, int32_t n_members,
+                        const double* Re, rbffd_state* state, const double* gu, const double* gv,
+                        int32_t n_steps, rbffd_stats* stats, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!flow || !state || !gu || !gv || !Re)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  if (n_members < 1 || n_members > 64 || (n_members & (n_members - 1)))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "n_members must be a power of two, 1..64");
+  for (int e = 0; e < n_members; ++e)
+    if (!(Re[e] > 0.0) || !std::isfinite(Re[e]))
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "Re[%d] must be finite and positive", e);
+  if (n_steps < 0) return set_error(ctx, RBFFD_ERR_INVALID_ARG, "negative n_steps");
+  int rc = check_flow(ctx, flow);
+  if (rc) return rc;
+  if (flow->projection != RBFFD_PROJ_PAPER)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "ensembles run the paper's projection only");
+  if (!state->u || !state->v || !state->cu_prev || !state->cv_prev || !state->pt || !state->p)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
+  if (n_steps == 0) return RBFFD_OK;
+  return ensemble_run(ctx, flow, n_members, Re, state, gu, gv, n_steps, stats, stream);
 }
 
 int rbffd_stencil_condition(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t n_alpha,

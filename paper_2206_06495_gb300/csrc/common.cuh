@@ -95,6 +95,7 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], GridReduce gr, doub
 // ------------------------------------------------------------------ context
 namespace rbffd {
 struct StepPlan;
+struct EnsPlan;
 }
 
 struct rbffd_ctx {
@@ -105,6 +106,7 @@ struct rbffd_ctx {
   size_t scratch_bytes = 0;
   void* host_pinned = nullptr;  // small pinned buffer for status words
   rbffd::StepPlan* plan = nullptr;
+  rbffd::EnsPlan* ens = nullptr;  // ensemble step plan (rbffd_ensemble_step)
   // launch shapes the SpMV autotuner picked, per operator shape key
   std::vector<std::pair<uint64_t, int>> spmv_shapes;
 };
@@ -135,6 +137,10 @@ void step_plan_free(struct StepPlan* p);
 int step_set_wait_limit(rbffd_ctx* ctx, long long polls);
 int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* f, const rbffd_state* s, rbffd_adjoint* lam,
                 double* grad_gu, double* grad_gv, rbffd_stats* stats, cudaStream_t st);
+int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* f, int E, const double* Re, rbffd_state* s,
+                 const double* gu, const double* gv, int32_t n_steps, rbffd_stats* stats,
+                 cudaStream_t st);
+void ens_plan_free(struct EnsPlan* p);
 int cond_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, const double* bx,
                const double* by, const int32_t* idx, int64_t ld, double* cond, cudaStream_t st);
 int analysis_mw(rbffd_ctx* ctx, const rbffd_ell* Dx, const rbffd_ell* Dy, const rbffd_ell* Dl,

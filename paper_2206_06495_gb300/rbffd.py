@@ -117,6 +117,9 @@ PROTOTYPES = {
     "rbffd_probe_fma": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                   C.c_void_p]),
     "rbffd_debug_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "rbffd_ensemble_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.c_int32,
+                                      C.POINTER(C.c_double), C.POINTER(StateC), C.c_void_p,
+                                      C.c_void_p, C.c_int32, C.POINTER(Stats), C.c_void_p]),
     "rbffd_stencil_condition": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                           C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                           C.c_int64, C.c_void_p, C.c_void_p]),
@@ -445,6 +448,32 @@ def stencil_error(ctx: Context, idx, w, op: int, ax, ay, bx, by, dr=None):
                                         _ptr(bx), _ptr(by), _ptr(dr), _ptr(err), _ptr(mean),
                                         _stream()))
     return err, mean
+
+
+def ensemble_zeros(flow: Flow, n_members: int, device="cuda") -> State:
+    """A member-contiguous ensemble state at rest ([N * E] and [M * E] arrays)."""
+    torch = _torch()
+    z = lambda n: torch.zeros(n * n_members, dtype=torch.float64, device=device)  # noqa: E731
+    return State(z(flow.N), z(flow.N), z(flow.N), z(flow.N), z(flow.M), z(flow.M), 0)
+
+
+def ensemble_step(ctx: Context, flow: Flow, Re, state: State, gu, gv, n_steps: int = 1) -> dict:
+    """rbffd_ensemble_step: E = len(Re) members, member-contiguous state and
+    wall data (entry (i, e) at [i * E + e]); advances state in place."""
+    E = len(Re)
+    re = (C.c_double * E)(*[float(r) for r in Re])
+    fc = flow.cstruct()
+    sc = _state_c(state)
+    st = Stats()
+    rc = lib().rbffd_ensemble_step(ctx.handle, C.byref(fc), E, re, C.byref(sc), _ptr(gu),
+                                   _ptr(gv), n_steps, C.byref(st), _stream())
+    state.j = sc.j
+    try:
+        ctx.check(rc)
+    except RbffdError as e:
+        e.stats = st.as_dict()
+        raise
+    return st.as_dict()
 
 
 def debug_set_wait_limit(ctx: Context, polls: int) -> None:
