@@ -907,12 +907,11 @@ int ens_build(rbffd_ctx* ctx, const rbffd_flow& f, int E, EnsPlan** out, cudaStr
   TRY(ealloc(ctx, p, &p->rd.counter, 1));
   TRY(check_cuda(ctx, cudaMemsetAsync(p->rd.counter, 0, sizeof(unsigned int), st), "memset"));
   if (const Amg* a = p->amg) {
+    // level l (0 <= l < nlev; the coarsest is lev[nlev - 1], nc rows)
     for (int l = 0; l < a->nlev; ++l) {
       TRY(ealloc(ctx, p, &p->lr[l], a->lev[l].n * E));
       TRY(ealloc(ctx, p, &p->lx[l], a->lev[l].n * E));
     }
-    TRY(ealloc(ctx, p, &p->lr[a->nlev], a->nc * E));
-    TRY(ealloc(ctx, p, &p->lx[a->nlev], a->nc * E));
   }
   TRY(check_cuda(ctx, cudaStreamSynchronize(st), "ensemble plan"));
 #undef TRY
@@ -922,25 +921,29 @@ int ens_build(rbffd_ctx* ctx, const rbffd_flow& f, int E, EnsPlan** out, cudaStr
 
 // B v for the C pressure columns of v (v: kw[3] = p or kw[5] = s): batched V-cycle
 void ens_vcycle(EnsPlan* P, const float* v, int which, float* zout, cudaStream_t st) {
+  // The hierarchy's nlev levels include the coarsest, lev[nlev - 1] (nc rows,
+  // dense inverse Xc); only the levels above it restrict (their cptr maps the
+  // next level's rows to their own).
   const Amg* a = P->amg;
-  const int C = P->E, G = P->grid;
+  const int C = P->E, G = P->grid, L = a->nlev;
   e_pc_in<<<G, kT, 0, st>>>(P->M, C, v, a->c, a->ce, a->perm0, which, a->inv_ces, P->sc,
                             P->lr[0]);
-  for (int l = 0; l < a->nlev; ++l)
-    e_pc_restrict<<<G, kT, 0, st>>>(a->lev[l], l + 1 < a->nlev ? a->lev[l + 1].n : a->nc, C,
-                                    P->lr[l], P->lx[l], P->lr[l + 1], P->sc);
+  for (int l = 0; l + 1 < L; ++l)
+    e_pc_restrict<<<G, kT, 0, st>>>(a->lev[l], a->lev[l + 1].n, C, P->lr[l], P->lx[l],
+                                    P->lr[l + 1], P->sc);
   const AmgLevel none{};
-  e_pc_coarse<<<G, kT, 0, st>>>(a->nc, C, a->Xc, P->lr[a->nlev], a->nlev ? nullptr : P->lx[0],
-                                a->nlev ? a->lev[a->nlev - 1] : none,
-                                a->nlev ? P->lx[a->nlev - 1] : nullptr, a->nlev ? 1 : 0, P->sc);
-  if (a->nlev == 0)  // the coarsest level is level 0: its z (in lx[0]) is the result
+  const bool fine = L >= 2;
+  e_pc_coarse<<<G, kT, 0, st>>>(a->nc, C, a->Xc, P->lr[L - 1], fine ? nullptr : P->lx[0],
+                                fine ? a->lev[L - 2] : none, fine ? P->lx[L - 2] : nullptr,
+                                fine ? 1 : 0, P->sc);
+  if (!fine)  // the coarsest level is level 0: its z (in lx[0]) is the result
     e_pc_fin<<<G, kT, 0, st>>>(P->M, C, P->lx[0], a->perm0, zout, which, a->inv_ces, a->inv_R,
                                P->sc, P->rd);
-  for (int l = a->nlev - 1; l >= 0; --l)
+  for (int l = L - 2; l >= 0; --l)
     e_pc_up<<<G, kT, 0, st>>>(a->lev[l], C, P->lr[l], P->lx[l], l ? a->lev[l - 1] : none,
                               l ? P->lx[l - 1] : nullptr, l == 0 ? 1 : 0, a->perm0, zout, which,
                               a->inv_ces, a->inv_R, P->sc, P->rd);
-  P->launches += 2 + 2 * a->nlev + (a->nlev == 0 ? 1 : 0);
+  P->launches += 2 + 2 * (L - 1) + (fine ? 0 : 1);
 }
 
 struct ESolve {

@@ -7,8 +7,6 @@
 // synchronisation they can imply.  The k-NN buckets and the status word live
 // in one file-scope device array of fixed size, reserved when the library is
 // loaded and held by every GPU that loads it until the process exits.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace rbffd {
@@ -16,27 +14,20 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 2u << 20;  // 2 MiB per device
 constexpr int64_t kNoAllocMaxBeta = 65536;          // largest n_beta accepted
-constexpr int kMaxDevices = 64;
 
 // Device scratch shared by every call of the entry point below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_addr_mutex;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch in the current context.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up on
+// every call: the lookup allocates nothing and does not synchronise, and a
+// cached address would outlive the context it belongs to (cudaDeviceReset
+// destroys the context and the module; the next context loads the module
+// afresh, possibly at another address).
 int scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RBFFD_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RBFFD_ERR_CUDA;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RBFFD_ERR_CUDA;
+  *out = p;
   return RBFFD_OK;
 }
 
