@@ -32,6 +32,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <type_traits>
 #include <vector>
 
 #include "amg.cuh"
@@ -983,8 +984,8 @@ struct ZAcc<float, float> {  // FP32 inner solves: plain FP32 sums
 //   y = A z + kap (A 1) + es mu,   mu = rank-one sum of B v (sc->sum_p / sum_s)
 // WHICH = 0: v = A p^, reduce (rh, v) -> alpha;  WHICH = 1: t = A s^, reduce
 // (t, s), (t, t) -> omega.
-template <int K, typename TW, typename TV, int WHICH>
-__global__ void __launch_bounds__(kThreads)
+template <int K, typename TW, typename TV, int WHICH, int DIRECT = 0>
+__global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
     k_spmv_pc(KOp<TW, TV> op, const TV* __restrict__ z, TV* __restrict__ y,
               const TV* __restrict__ dotv, KScal* sc, GridReduce gr, int* worked) {
   if (sc->done) return;
@@ -1002,7 +1003,7 @@ __global__ void __launch_bounds__(kThreads)
     d0 += di * yi;
     if (WHICH) d1 += yi * yi;
   };
-  if constexpr (kStage<K, TW>) {
+  if constexpr (kStage<K, TW> && DIRECT == 0) {
     extern __shared__ __align__(128) unsigned char dsm[];
     auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
     __shared__ uint64_t bar;
@@ -2200,6 +2201,23 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     }
     if (rc0) return rc0;
   }
+  // TEMPORARY measurement switch: direct-load pressure SpMV at full occupancy
+  static const int direct_pc = getenv("RBFFD_PC_DIRECT") ? atoi(getenv("RBFFD_PC_DIRECT")) : 0;
+  const int Gd = (int)std::max<int64_t>(
+      1, std::min<int64_t>((op.n + kThreads - 1) / kThreads,
+                           (int64_t)sm_count() * (direct_pc > 0 ? direct_pc : 1)));
+  auto spmv_pc = [&](auto W, cudaStream_t s, const TV* z, TV* y, const TV* dv, KScal* scp,
+                     int* wf) {
+    constexpr int WH = decltype(W)::value;
+    if (direct_pc == 8)
+      k_spmv_pc<K, TW, TV, WH, 8><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
+    else if (direct_pc == 6)
+      k_spmv_pc<K, TW, TV, WH, 6><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
+    else if (direct_pc == 4)
+      k_spmv_pc<K, TW, TV, WH, 4><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
+    else
+      k_spmv_pc<K, TW, TV, WH><<<Gs, kThreads, smem, s>>>(op, z, y, dv, scp, P->gr, wf);
+  };
   for (int q = 0; q < NRHS; ++q) {
     int rc = check_cuda(ctx, cudaMemcpyAsync(work[6][q], x[q], sizeof(TV) * op.n,
                                              cudaMemcpyDeviceToDevice, st),
@@ -2266,15 +2284,15 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
           if (pc) {  // right-preconditioned: the SpMVs act on B p = zp + kap, B s = zs + kap
             if constexpr (NRHS == 1 && RANK1) {
               if (prof) record_ev(s);
-              k_spmv_pc<K, TW, TV, 0><<<Gs, kThreads, smem, s>>>(op, zbuf<TV>(pc, 0), V.v[0], RH.v[0],
-                                                                   P->sc, P->gr, work_flag());
+              spmv_pc(std::integral_constant<int, 0>{}, s, zbuf<TV>(pc, 0), V.v[0], RH.v[0],
+                      P->sc, work_flag());
               if (prof) record_ev(s);
               k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
                                                              pcc);
               vcycle<TV>(P, pc, S.v[0], 1, zbuf<TV>(pc, 1), s);
               if (prof) record_ev(s);
-              k_spmv_pc<K, TW, TV, 1><<<Gs, kThreads, smem, s>>>(op, zbuf<TV>(pc, 1), T.v[0], S.v[0],
-                                                                   P->sc, P->gr, work_flag());
+              spmv_pc(std::integral_constant<int, 1>{}, s, zbuf<TV>(pc, 1), T.v[0], S.v[0],
+                      P->sc, work_flag());
               if (prof) record_ev(s);
               k_update_xr_pc<TV><<<G, kThreads, 0, s>>>(op.n, X.v[0], R.v[0], RH.v[0],
                                                         zbuf<TV>(pc, 0), zbuf<TV>(pc, 1), S.v[0],
@@ -2391,8 +2409,8 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       if (rc) return rc;
       cudaEventRecord(P->ev[0], st);
       for (int r = 0; r < kReps; ++r)
-        k_spmv_pc<K, TW, TV, 0><<<Gs, kThreads, smem, st>>>(op, zbuf<TV>(pc, 0), T.v[0], RH.v[0],
-                                                             P->sc_timing, P->gr, nullptr);
+        spmv_pc(std::integral_constant<int, 0>{}, st, zbuf<TV>(pc, 0), T.v[0], RH.v[0],
+                P->sc_timing, nullptr);
       cudaEventRecord(P->ev[1], st);
       float ms = 0.f;
       if (cudaEventSynchronize(P->ev[1]) == cudaSuccess &&
