@@ -91,17 +91,29 @@ __device__ __forceinline__ void col_reduce(double (&v)[NV], int C, EReduce rd, F
   if (t == 0) *rd.counter = 0u;
 }
 
-#define EFOR(n, C)                                                                           \
-  for (int64_t f = blockIdx.x * (int64_t)kT + threadIdx.x; f < (int64_t)(n) * (C);          \
-       f += (int64_t)gridDim.x * kT)
+// Items f = i C + c (row i, column c) of a contiguous share of the rows per
+// block: thread t takes the items r0 C + t + q kT, so its column is t mod C
+// (C divides kT) for the whole loop, and the block walks its rows in order,
+// so the gathers of nearby (Morton-ordered) rows find their lines in L1.
+#define EFOR(n, C, I)                                                                     \
+  const int64_t ef_share = ((int64_t)(n) + gridDim.x - 1) / gridDim.x;                   \
+  const int64_t ef_r1 = min((int64_t)(n), ef_share * (blockIdx.x + 1));                  \
+  const int ef_c = (int)threadIdx.x % (C), ef_step = kT / (C);                           \
+  for (int64_t I = min((int64_t)(n), ef_share * blockIdx.x) + (int)threadIdx.x / (C),     \
+               f = I * (C) + ef_c;                                                       \
+       I < ef_r1; I += ef_step, f += kT)
 
 // ------------------------------------------------------------ explicit stages
 // sum_s w[s][i] (x2[j][c] - x2[ref][c]) over split FP32 copies
+// (K > 0: the stencil size at compile time, every gather issued at once)
+template <int K>
 __device__ __forceinline__ float gsplit(const int32_t* idx, const float* w, int64_t ld, int k,
                                         int64_t i, const float2* x2, int C, int c) {
   const float2 ref = x2[(int64_t)idx[i] * C + c];
   float acc = 0.f;
-  for (int s = 0; s < k; ++s) {
+  const int kk = K > 0 ? K : k;
+#pragma unroll(K > 0 ? K : 1)
+  for (int s = 0; s < kk; ++s) {
     const float2 xj = x2[(int64_t)idx[s * ld + i] * C + c];
     acc += w[s * ld + i] * ((xj.x - ref.x) + (xj.y - ref.y));
   }
@@ -109,6 +121,7 @@ __device__ __forceinline__ float gsplit(const int32_t* idx, const float* w, int6
 }
 
 // Stage 1 (AB2 convection) for every member.
+template <int K>
 __global__ void __launch_bounds__(kT)
     e_convect(int64_t N, int64_t ld, int k, int E, const int32_t* __restrict__ idx,
               const float* __restrict__ wdx, const float* __restrict__ wdy,
@@ -117,11 +130,10 @@ __global__ void __launch_bounds__(kT)
               double* __restrict__ cu_prev, double* __restrict__ cv_prev, double* __restrict__ us,
               double* __restrict__ vs, float2* __restrict__ us2, float2* __restrict__ vs2,
               double dt, int first) {
-  EFOR(N, E) {
-    const int64_t i = f / E;
-    const int c = (int)(f - i * E);
-    const double ux = gsplit(idx, wdx, ld, k, i, u2, E, c), uy = gsplit(idx, wdy, ld, k, i, u2, E, c);
-    const double vx = gsplit(idx, wdx, ld, k, i, v2, E, c), vy = gsplit(idx, wdy, ld, k, i, v2, E, c);
+  EFOR(N, E, i) {
+    const int c = ef_c;
+    const double ux = gsplit<K>(idx, wdx, ld, k, i, u2, E, c), uy = gsplit<K>(idx, wdy, ld, k, i, u2, E, c);
+    const double vx = gsplit<K>(idx, wdx, ld, k, i, v2, E, c), vy = gsplit<K>(idx, wdy, ld, k, i, v2, E, c);
     const double ui = u[f], vi = v[f];
     const double cu = -(ui * ux + vi * uy), cv = -(ui * vx + vi * vy);
     const double cup = first ? cu : cu_prev[f], cvp = first ? cv : cv_prev[f];
@@ -137,7 +149,8 @@ __global__ void __launch_bounds__(kT)
 
 // Stage 2 right side into the viscous layout (column e: u of member e, E + e:
 // v): inside u* + a_e D_Lap (u* or u_j); walls: wall data (+ Kim & Moin term).
-__global__ void __launch_bounds__(kT)
+template <int K>
+__global__ void __launch_bounds__(kT, 2)
     e_helm_rhs(int64_t N, int64_t ldv, int k, int E, const int32_t* __restrict__ vv_idx,
                const float* __restrict__ lap, const double* __restrict__ us,
                const double* __restrict__ vs, const float2* __restrict__ q2u,
@@ -149,20 +162,19 @@ __global__ void __launch_bounds__(kT)
                const double* __restrict__ a_col, double dt, int km,
                double* __restrict__ rhs, double* __restrict__ x0) {
   const int C = 2 * E;
-  EFOR(N, E) {
-    const int64_t i = f / E;
-    const int e = (int)(f - i * E);
+  EFOR(N, E, i) {
+    const int e = ef_c;
     double bu, bv;
     if (!v_bc[i]) {
       const double a = a_col[e];
-      bu = us[f] + a * gsplit(vv_idx, lap, ldv, k, i, q2u, E, e);
-      bv = vs[f] + a * gsplit(vv_idx, lap, ldv, k, i, q2v, E, e);
+      bu = us[f] + a * gsplit<K>(vv_idx, lap, ldv, k, i, q2u, E, e);
+      bv = vs[f] + a * gsplit<K>(vv_idx, lap, ldv, k, i, q2v, E, e);
     } else {
       bu = gu[f];
       bv = gv[f];
       if (km) {
-        const double gx = gsplit(vp_idx, gdx, ldv, k, i, pt2, E, e);
-        const double gy = gsplit(vp_idx, gdy, ldv, k, i, pt2, E, e);
+        const double gx = gsplit<K>(vp_idx, gdx, ldv, k, i, pt2, E, e);
+        const double gy = gsplit<K>(vp_idx, gdy, ldv, k, i, pt2, E, e);
         if (km == 1) {
           const double tx = -v_ny[i], ty = v_nx[i], gt = tx * gx + ty * gy;
           bu += dt * gt * tx;
@@ -182,17 +194,19 @@ __global__ void __launch_bounds__(kT)
 
 // Stage 3a: F = D^(P,V) u** (FP64 weights), scaled right side of the pressure
 // solve (0 on the Neumann rows)
+template <int K>
 __global__ void __launch_bounds__(kT)
     e_divergence(int64_t M, int64_t ldp, int k, int E, const int32_t* __restrict__ idx,
                  const double* __restrict__ wdx, const double* __restrict__ wdy,
                  const double* __restrict__ xv, const uint8_t* __restrict__ p_bc,
                  const double* __restrict__ scale, double inv_dt, double* __restrict__ b) {
   const int C = 2 * E;
-  EFOR(M, E) {
-    const int64_t i = f / E;
-    const int e = (int)(f - i * E);
+  EFOR(M, E, i) {
+    const int e = ef_c;
     double acc = 0.0;
-    for (int s = 0; s < k; ++s) {
+    const int kk = K > 0 ? K : k;
+#pragma unroll(K > 0 ? K : 1)
+    for (int s = 0; s < kk; ++s) {
       const int64_t j = idx[s * ldp + i];
       acc += wdx[s * ldp + i] * xv[j * C + e] + wdy[s * ldp + i] * xv[j * C + E + e];
     }
@@ -201,23 +215,24 @@ __global__ void __launch_bounds__(kT)
 }
 
 // Stage 3c: p~ = x - mean(x) per member; p = p~ - a_e D^(P,P)_Lap p~
+template <int K>
 __global__ void __launch_bounds__(kT)
     e_pressure(int64_t M, int64_t ldp, int k, int E, const int32_t* __restrict__ idx,
                const float* __restrict__ lap, const double* __restrict__ x,
                const float2* __restrict__ x2, const double* __restrict__ mean,
                const double* __restrict__ a_col, double* __restrict__ pt, double* __restrict__ p,
                float2* __restrict__ pt2) {
-  EFOR(M, E) {
-    const int64_t i = f / E;
-    const int e = (int)(f - i * E);
+  EFOR(M, E, i) {
+    const int e = ef_c;
     const double v = x[f] - mean[e];
     pt[f] = v;
-    p[f] = v - a_col[e] * gsplit(idx, lap, ldp, k, i, x2, E, e);
+    p[f] = v - a_col[e] * gsplit<K>(idx, lap, ldp, k, i, x2, E, e);
     pt2[f] = split2e(v);
   }
 }
 
 // Stage 3d: u = u** - dt D^(V,P) p~; wall nodes set to the wall data
+template <int K>
 __global__ void __launch_bounds__(kT)
     e_correct(int64_t N, int64_t ldv, int k, int E, const int32_t* __restrict__ idx,
               const float* __restrict__ gdx, const float* __restrict__ gdy,
@@ -226,11 +241,10 @@ __global__ void __launch_bounds__(kT)
               const double* __restrict__ gv, double dt, int overwrite, double* __restrict__ u,
               double* __restrict__ v, float2* __restrict__ u2, float2* __restrict__ v2) {
   const int C = 2 * E;
-  EFOR(N, E) {
-    const int64_t i = f / E;
-    const int e = (int)(f - i * E);
-    double un = xv[i * C + e] - dt * gsplit(idx, gdx, ldv, k, i, pt2, E, e);
-    double vn = xv[i * C + E + e] - dt * gsplit(idx, gdy, ldv, k, i, pt2, E, e);
+  EFOR(N, E, i) {
+    const int e = ef_c;
+    double un = xv[i * C + e] - dt * gsplit<K>(idx, gdx, ldv, k, i, pt2, E, e);
+    double vn = xv[i * C + E + e] - dt * gsplit<K>(idx, gdy, ldv, k, i, pt2, E, e);
     if (overwrite && v_bc[i]) {
       un = gu[f];
       vn = gv[f];
@@ -251,7 +265,7 @@ __global__ void e_split(int64_t n, const double* __restrict__ x, float2* __restr
 __global__ void __launch_bounds__(kT)
     e_colmean(int64_t n, int C, const double* __restrict__ x, EReduce rd, double* out) {
   double v[1] = {0.0};
-  EFOR(n, C) v[0] += x[f];
+  EFOR(n, C, row) v[0] += x[f];
   col_reduce<1>(v, C, rd, [&](int c, double* t) { out[c] = t[0] / (double)n; });
 }
 
@@ -268,12 +282,13 @@ struct EOp {
   const float* a1;      // pressure: row sums
 };
 
-template <typename TW>
-__device__ __forceinline__ float erow32(const EOp& op, const TW* w, int64_t i, const float* x,
+template <int K>
+__device__ __forceinline__ float erow32(const EOp& op, const float* w, int64_t i, const float* x,
                                       int C, int c) {
   float acc = 0.f;
-  for (int s = 0; s < op.k; ++s)
-    acc += (float)w[s * op.ld + i] * x[(int64_t)op.idx[s * op.ld + i] * C + c];
+  const int kk = K > 0 ? K : op.k;
+#pragma unroll(K > 0 ? K : 1)
+  for (int s = 0; s < kk; ++s) acc += w[s * op.ld + i] * x[(int64_t)op.idx[s * op.ld + i] * C + c];
   return acc;
 }
 
@@ -284,8 +299,7 @@ __global__ void __launch_bounds__(kT)
            float* __restrict__ rh, float* __restrict__ p, float* __restrict__ x,
            const float* __restrict__ cnode, EScal* sc, EReduce rd, double tol2, int maxit) {
   double v[3] = {0.0, 0.0, 0.0};
-  EFOR(n, C) {
-    const int64_t i = f / C;
+  EFOR(n, C, i) {
     const float bi = b[f];
     r[f] = bi;
     rh[f] = bi;
@@ -314,24 +328,29 @@ __global__ void __launch_bounds__(kT)
 }
 
 // v = A zp (+ rank-one terms); reduce (rh, v) -> alpha
-template <typename TW>
+template <int K>
 __global__ void __launch_bounds__(kT)
-    e_spmv_v(EOp op, const TW* __restrict__ w, const float* __restrict__ zp,
+    e_spmv_v(EOp op, const float* __restrict__ w, const float* __restrict__ zp,
              float* __restrict__ v, const float* __restrict__ rh, EScal* sc, EReduce rd) {
   if (sc->done) return;
   const int C = sc->C;
+  // this thread's column is fixed: its scalars are read once
+  const int c0 = (int)threadIdx.x % C;
+  const bool act = sc->active[c0] != 0;
+  const float ac = op.visc ? op.a[c0] : 0.f;
+  const float kap = op.visc ? 0.f : (float)sc->kap[0][c0];
+  const float sig = op.visc ? 0.f : (float)sc->sum_p[c0];
   double acc[1] = {0.0};
-  EFOR(op.n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
-    if (!sc->active[c]) continue;
-    float y = erow32(op, w, i, zp, C, c);
-    if (op.visc)
-      y = zp[f] - op.a[c] * y;
-    else
-      y += (float)sc->kap[0][c] * op.a1[i] + op.es[i] * (float)sc->sum_p[c];
-    v[f] = y;
-    acc[0] += (double)rh[f] * y;
+  if (act) {
+    EFOR(op.n, C, i) {
+      float y = erow32<K>(op, w, i, zp, C, ef_c);
+      if (op.visc)
+        y = zp[f] - ac * y;
+      else
+        y += kap * op.a1[i] + op.es[i] * sig;
+      v[f] = y;
+      acc[0] += (double)rh[f] * y;
+    }
   }
   col_reduce<1>(acc, C, rd, [&](int c, double* t) {
     if (!sc->active[c]) return;
@@ -350,38 +369,44 @@ __global__ void __launch_bounds__(kT)
                float* __restrict__ s, const float* __restrict__ cnode, EScal* sc, EReduce rd) {
   if (sc->done) return;
   const int C = sc->C;
+  const int c0 = (int)threadIdx.x % C;
+  const bool act = sc->active[c0] != 0;
+  const float al = (float)sc->alpha[c0];
   double acc[1] = {0.0};
-  EFOR(n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
-    if (!sc->active[c]) continue;
-    const float si = r[f] - (float)sc->alpha[c] * v[f];
-    s[f] = si;
-    if (cnode) acc[0] += (double)cnode[i] * si;
+  if (act) {
+    EFOR(n, C, i) {
+      const float si = r[f] - al * v[f];
+      s[f] = si;
+      if (cnode) acc[0] += (double)cnode[i] * si;
+    }
   }
   col_reduce<1>(acc, C, rd, [&](int c, double* t) { sc->cs[c] = t[0]; });
 }
 
 // t = A zs; reduce (t, s), (t, t) -> omega
-template <typename TW>
+template <int K>
 __global__ void __launch_bounds__(kT)
-    e_spmv_t(EOp op, const TW* __restrict__ w, const float* __restrict__ zs,
+    e_spmv_t(EOp op, const float* __restrict__ w, const float* __restrict__ zs,
              float* __restrict__ tv, const float* __restrict__ s, EScal* sc, EReduce rd) {
   if (sc->done) return;
   const int C = sc->C;
+  const int c0 = (int)threadIdx.x % C;
+  const bool act = sc->active[c0] != 0;
+  const float ac = op.visc ? op.a[c0] : 0.f;
+  const float kap = op.visc ? 0.f : (float)sc->kap[1][c0];
+  const float sig = op.visc ? 0.f : (float)sc->sum_s[c0];
   double acc[2] = {0.0, 0.0};
-  EFOR(op.n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
-    if (!sc->active[c]) continue;
-    float y = erow32(op, w, i, zs, C, c);
-    if (op.visc)
-      y = zs[f] - op.a[c] * y;
-    else
-      y += (float)sc->kap[1][c] * op.a1[i] + op.es[i] * (float)sc->sum_s[c];
-    tv[f] = y;
-    acc[0] += (double)y * s[f];
-    acc[1] += (double)y * y;
+  if (act) {
+    EFOR(op.n, C, i) {
+      float y = erow32<K>(op, w, i, zs, C, ef_c);
+      if (op.visc)
+        y = zs[f] - ac * y;
+      else
+        y += kap * op.a1[i] + op.es[i] * sig;
+      tv[f] = y;
+      acc[0] += (double)y * s[f];
+      acc[1] += (double)y * y;
+    }
   }
   col_reduce<2>(acc, C, rd, [&](int c, double* t) {
     if (!sc->active[c]) return;
@@ -402,18 +427,19 @@ __global__ void __launch_bounds__(kT)
                 const float* __restrict__ tv, int pc, EScal* sc, EReduce rd) {
   if (sc->done) return;
   const int C = sc->C;
+  const int c0 = (int)threadIdx.x % C;
+  const bool act = sc->active[c0] != 0;
+  const float al = (float)sc->alpha[c0], om = (float)sc->omega[c0];
+  const float kp = pc ? (float)sc->kap[0][c0] : 0.f, ks = pc ? (float)sc->kap[1][c0] : 0.f;
   double acc[2] = {0.0, 0.0};
-  EFOR(n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
-    if (!sc->active[c]) continue;
-    const float al = (float)sc->alpha[c], om = (float)sc->omega[c];
-    const float kp = pc ? (float)sc->kap[0][c] : 0.f, ks = pc ? (float)sc->kap[1][c] : 0.f;
-    x[f] += al * (zp[f] + kp) + om * (zs[f] + ks);
-    const float ri = s[f] - om * tv[f];
-    r[f] = ri;
-    acc[0] += (double)rh[f] * ri;
-    acc[1] += (double)ri * ri;
+  if (act) {
+    EFOR(n, C, i) {
+      x[f] += al * (zp[f] + kp) + om * (zs[f] + ks);
+      const float ri = s[f] - om * tv[f];
+      r[f] = ri;
+      acc[0] += (double)rh[f] * ri;
+      acc[1] += (double)ri * ri;
+    }
   }
   col_reduce<2>(acc, C, rd, [&](int c, double* t) {
     if (sc->active[c]) {
@@ -443,15 +469,16 @@ __global__ void __launch_bounds__(kT)
                EReduce rd) {
   if (sc->done) return;
   const int C = sc->C;
+  const int c0 = (int)threadIdx.x % C;
+  const bool act = sc->active[c0] != 0;
+  const float be = (float)sc->alpha[c0], om = (float)sc->omega[c0];
   double acc[1] = {0.0};
-  EFOR(n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
-    if (!sc->active[c]) continue;
-    const float be = (float)sc->alpha[c], om = (float)sc->omega[c];
-    const float pi = r[f] + be * (p[f] - om * v[f]);
-    p[f] = pi;
-    if (cnode) acc[0] += (double)cnode[i] * pi;
+  if (act) {
+    EFOR(n, C, i) {
+      const float pi = r[f] + be * (p[f] - om * v[f]);
+      p[f] = pi;
+      if (cnode) acc[0] += (double)cnode[i] * pi;
+    }
   }
   col_reduce<1>(acc, C, rd, [&](int c, double* t) {
     if (sc->active[c]) sc->cp[c] = t[0];
@@ -470,12 +497,9 @@ __global__ void __launch_bounds__(kT)
             const float* __restrict__ ce, const int32_t* __restrict__ perm0, int which,
             double inv_ces, const EScal* sc, float* __restrict__ r0) {
   if (sc->done) return;
-  EFOR(M, C) {
-    const int64_t p = f / C;
-    const int c = (int)(f - p * C);
-    const float mu = (float)((which ? sc->cs[c] : sc->cp[c]) * inv_ces);
-    r0[f] = cl[p] * v[(int64_t)perm0[p] * C + c] - mu * ce[p];
-  }
+  const int c0 = (int)threadIdx.x % C;
+  const float mu = (float)((which ? sc->cs[c0] : sc->cp[c0]) * inv_ces);
+  EFOR(M, C, p) r0[f] = cl[p] * v[(int64_t)perm0[p] * C + ef_c] - mu * ce[p];
 }
 
 // Pre-smoothing from zero (x = omega D^-1 r) and restriction of its residual
@@ -484,9 +508,8 @@ __global__ void __launch_bounds__(kT)
     e_pc_restrict(AmgLevel F, int64_t nagg, int C, const float* __restrict__ r,
                   float* __restrict__ x, float* __restrict__ rc, const EScal* sc) {
   if (sc->done) return;
-  EFOR(nagg, C) {
-    const int64_t I = f / C;
-    const int c = (int)(f - I * C);
+  EFOR(nagg, C, I) {
+    const int c = ef_c;
     float acc = 0.f;
     for (int32_t i = F.cptr[I]; i < F.cptr[I + 1]; ++i) {
       const float ri = r[(int64_t)i * C + c];
@@ -503,23 +526,58 @@ __global__ void __launch_bounds__(kT)
   }
 }
 
-// Coarsest level: z = X r (dense inverse); then the correction of the next
-// finer level's rows of aggregate `row` (has_fine), or z itself
+// Coarsest level: z = X r for the C columns (X: nc x nc, the dense inverse)
+// as a tiled product.  A block takes TR rows of z and every column; thread t
+// keeps column t mod C and the rows g, g + G, ... of the tile (G = kT / C
+// groups); X and r move through shared memory in slabs of kCJ columns of X
+// (rows of r), and every output sums its products in j order, as the plain
+// dot product does.  Then the correction of the next finer level's rows of
+// aggregate `row` (has_fine), or z itself.
+constexpr int kCJ = 32;
+constexpr int kCoarseRows = 16;  // TR for C >= 16 (fewer columns: one row per thread)
+
 __global__ void __launch_bounds__(kT)
     e_pc_coarse(int64_t nc, int C, const float* __restrict__ X, const float* __restrict__ r,
                 float* __restrict__ z, AmgLevel Fine, float* __restrict__ xfine, int has_fine,
                 const EScal* sc) {
   if (sc->done) return;
-  EFOR(nc, C) {
-    const int64_t row = f / C;
-    const int c = (int)(f - row * C);
-    float acc = 0.f;
-    for (int64_t j = 0; j < nc; ++j) acc += X[row * nc + j] * r[j * C + c];
+  __shared__ float xs[kT * (kCJ + 1)];  // TR x kCJ slab of X (TR <= kT), padded rows
+  __shared__ float rs[kCJ * 64];        // kCJ x C slab of r (C <= 64)
+  const int G = kT / C;
+  const int TR = G > kCoarseRows ? G : kCoarseRows;
+  const int RPT = TR / G;  // rows per thread, <= kCoarseRows / 4
+  const int t = (int)threadIdx.x, c = t % C, g = t / C;
+  const int64_t row0 = (int64_t)blockIdx.x * TR;
+  float acc[kCoarseRows / 4] = {};
+  for (int64_t j0 = 0; j0 < nc; j0 += kCJ) {
+    for (int e = t; e < TR * kCJ; e += kT) {
+      const int rr = e / kCJ, jj = e % kCJ;
+      const int64_t row = row0 + rr, col = j0 + jj;
+      xs[rr * (kCJ + 1) + jj] = (row < nc && col < nc) ? X[row * nc + col] : 0.f;
+    }
+    for (int e = t; e < kCJ * C; e += kT) {
+      const int jj = e / C, cc = e % C;
+      rs[jj * C + cc] = (j0 + jj < nc) ? r[(j0 + jj) * C + cc] : 0.f;
+    }
+    __syncthreads();
+    const int jn = (int)(nc - j0 < kCJ ? nc - j0 : kCJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      const float rv = rs[jj * C + c];
+#pragma unroll
+      for (int q = 0; q < kCoarseRows / 4; ++q)
+        if (q < RPT) acc[q] += xs[(g + q * G) * (kCJ + 1) + jj] * rv;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kCoarseRows / 4; ++q) {
+    const int64_t row = row0 + g + q * G;
+    if (q >= RPT || row >= nc) continue;
     if (has_fine) {
-      const float v = kAmgCoarseScale * acc;
+      const float v = kAmgCoarseScale * acc[q];
       for (int32_t i = Fine.cptr[row]; i < Fine.cptr[row + 1]; ++i) xfine[(int64_t)i * C + c] += v;
     } else {
-      z[f] = acc;
+      z[row * C + c] = acc[q];
     }
   }
 }
@@ -535,9 +593,8 @@ __global__ void __launch_bounds__(kT)
             double inv_ces, double inv_R, EScal* sc, EReduce rd) {
   if (sc->done) return;
   double acc[1] = {0.0};
-  EFOR(F.n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
+  EFOR(F.n, C, i) {
+    const int c = ef_c;
     const float xi = x[f];
     float ax = F.diag[i] * xi;
     for (int s = 0; s < F.width; ++s) {
@@ -572,9 +629,8 @@ __global__ void __launch_bounds__(kT)
              EReduce rd) {
   if (sc->done) return;
   double acc[1] = {0.0};
-  EFOR(M, C) {
-    const int64_t q = f / C;
-    const int c = (int)(f - q * C);
+  EFOR(M, C, q) {
+    const int c = ef_c;
     zout[(int64_t)perm0[q] * C + c] = z0[f];
     acc[0] += z0[f];
   }
@@ -590,17 +646,19 @@ __global__ void __launch_bounds__(kT)
 
 // ------------------------------------------------------------- refinement
 // r = b - A x in FP64 (FP64 weights); per-column (r, r), (b, b)
+template <int K>
 __global__ void __launch_bounds__(kT)
     e_residual64(EOp op, const double* __restrict__ w, const double* __restrict__ ad,
                  const double* __restrict__ esd, const double* __restrict__ x,
                  const double* __restrict__ b, double* __restrict__ r,
                  const double* __restrict__ xsum, int C, EReduce rd, double* out) {
   double acc[2] = {0.0, 0.0};
-  EFOR(op.n, C) {
-    const int64_t i = f / C;
-    const int c = (int)(f - i * C);
+  EFOR(op.n, C, i) {
+    const int c = ef_c;
     double y = 0.0;
-    for (int s = 0; s < op.k; ++s) y += w[s * op.ld + i] * x[(int64_t)op.idx[s * op.ld + i] * C + c];
+    const int kk = K > 0 ? K : op.k;
+#pragma unroll(K > 0 ? K : 1)
+    for (int s = 0; s < kk; ++s) y += w[s * op.ld + i] * x[(int64_t)op.idx[s * op.ld + i] * C + c];
     if (op.visc)
       y = x[f] - ad[c] * y;
     else
@@ -620,22 +678,22 @@ __global__ void __launch_bounds__(kT)
 __global__ void __launch_bounds__(kT)
     e_colsum(int64_t n, int C, const double* __restrict__ x, EReduce rd, double* out) {
   double v[1] = {0.0};
-  EFOR(n, C) v[0] += x[f];
+  EFOR(n, C, row) v[0] += x[f];
   col_reduce<1>(v, C, rd, [&](int c, double* t) { out[c] = t[0]; });
 }
 
 __global__ void e_to32(int64_t n, int C, const double* __restrict__ r, const double* __restrict__ sc,
                        float* __restrict__ r32) {
-  EFOR(n, C) {
-    const int c = (int)(f % C);
+  EFOR(n, C, row) {
+    const int c = ef_c;
     r32[f] = (float)(r[f] * sc[c]);
   }
 }
 
 __global__ void e_addcorr(int64_t n, int C, double* __restrict__ x, const float* __restrict__ e32,
                           const double* __restrict__ nrm) {
-  EFOR(n, C) {
-    const int c = (int)(f % C);
+  EFOR(n, C, row) {
+    const int c = ef_c;
     x[f] += nrm[c] * (double)e32[f];
   }
 }
@@ -700,6 +758,16 @@ int ealloc(rbffd_ctx* ctx, EnsPlan* p, T** out, size_t count) {
   *out = (T*)ptr;
   return RBFFD_OK;
 }
+
+// kern<28> when the stencil size k is 28 (every gather of a row unrolled and
+// issued at once), kern<0> (runtime size) otherwise
+#define EK(kern, grid, ...)                                      \
+  do {                                                           \
+    if (k == 28)                                                 \
+      kern<28><<<grid, kT, 0, st>>>(__VA_ARGS__);                \
+    else                                                         \
+      kern<0><<<grid, kT, 0, st>>>(__VA_ARGS__);                 \
+  } while (0)
 
 int ens_to32(rbffd_ctx* ctx, EnsPlan* p, const double* src, int64_t n, float** dst,
              cudaStream_t st) {
@@ -933,7 +1001,9 @@ void ens_vcycle(EnsPlan* P, const float* v, int which, float* zout, cudaStream_t
                                     P->lr[l + 1], P->sc);
   const AmgLevel none{};
   const bool fine = L >= 2;
-  e_pc_coarse<<<G, kT, 0, st>>>(a->nc, C, a->Xc, P->lr[L - 1], fine ? nullptr : P->lx[0],
+  const int TRc = kT / C > kCoarseRows ? kT / C : kCoarseRows;
+  const int Gc = (int)((a->nc + TRc - 1) / TRc);
+  e_pc_coarse<<<Gc, kT, 0, st>>>(a->nc, C, a->Xc, P->lr[L - 1], fine ? nullptr : P->lx[0],
                                 fine ? a->lev[L - 2] : none, fine ? P->lx[L - 2] : nullptr,
                                 fine ? 1 : 0, P->sc);
   if (!fine)  // the coarsest level is level 0: its z (in lx[0]) is the result
@@ -948,6 +1018,7 @@ void ens_vcycle(EnsPlan* P, const float* v, int which, float* zout, cudaStream_t
 
 struct ESolve {
   int iters = 0;
+  int sweeps = 0;  // refinement sweeps (inner solves)
   bool converged = true;
   bool nonfinite = false;
   double relres = 0.0;
@@ -956,7 +1027,7 @@ struct ESolve {
 // One batched FP32 BiCGSTAB on C columns: op32 e = r32 (x0 = 0) to inner_tol.
 int ens_bicgstab(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const float* w32, int C, bool pc,
                  double inner_tol, int maxit, ESolve* res, cudaStream_t st) {
-  const int G = P->grid;
+  const int G = P->grid, k = op.k;
   float *x = P->kw[0], *r = P->kw[1], *rh = P->kw[2], *pp = P->kw[3], *v = P->kw[4],
         *s = P->kw[5], *t = P->kw[6], *zp = P->kw[7], *zs = P->kw[8];
   const float* cnode = pc ? P->amg->cnode : nullptr;
@@ -974,13 +1045,13 @@ int ens_bicgstab(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const float* w32, in
         ens_vcycle(P, pp, 0, zp, st);
         zpp = zp;
       }
-      e_spmv_v<float><<<G, kT, 0, st>>>(op, w32, zpp, v, rh, P->sc, P->rd);
+      EK(e_spmv_v, G, op, w32, zpp, v, rh, P->sc, P->rd);
       e_update_s<<<G, kT, 0, st>>>(n, r, v, s, cnode, P->sc, P->rd);
       if (pc) {
         ens_vcycle(P, s, 1, zs, st);
         zss = zs;
       }
-      e_spmv_t<float><<<G, kT, 0, st>>>(op, w32, zss, t, s, P->sc, P->rd);
+      EK(e_spmv_t, G, op, w32, zss, t, s, P->sc, P->rd);
       e_update_xr<<<G, kT, 0, st>>>(n, x, r, rh, zpp, zss, s, t, pc ? 1 : 0, P->sc, P->rd);
       e_update_p<<<G, kT, 0, st>>>(n, pp, r, v, cnode, P->sc, P->rd);
       P->launches += 5;
@@ -1005,7 +1076,7 @@ int ens_bicgstab(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const float* w32, in
 int ens_refine(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const double* w64, const float* w32,
                int C, bool pc, double* x, const double* b, double tol, double inner_tol,
                int maxit, ESolve* res, cudaStream_t st) {
-  const int G = P->grid;
+  const int G = P->grid, k = op.k;
   // [2C] norms, staged after the EScal that the inner solves copy to offset 0
   double* h = (double*)ctx->host_pinned + 4096;
   double hn[kCMax], hi[kCMax];
@@ -1014,7 +1085,7 @@ int ens_refine(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const double* w64, con
   int used = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (!op.visc) e_colsum<<<G, kT, 0, st>>>(op.n, C, x, P->rd, P->xsum);
-    e_residual64<<<G, kT, 0, st>>>(op, w64, P->aV, P->es, x, b, P->r64, P->xsum, C, P->rd, P->h2);
+    EK(e_residual64, G, op, w64, P->aV, P->es, x, b, P->r64, P->xsum, C, P->rd, P->h2);
     P->launches += op.visc ? 1 : 2;
     int rc = check_cuda(ctx, cudaGetLastError(), "ensemble residual");
     if (!rc)
@@ -1053,6 +1124,7 @@ int ens_refine(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const double* w64, con
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
+    res->sweeps += 1;
     e_addcorr<<<G, kT, 0, st>>>(op.n, C, x, P->kw[0], P->nrm);
     P->launches += 2;
   }
@@ -1100,10 +1172,10 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
   EOp H{f.vv_idx, f.ld_v, f.N, k, 1, P->aV32, nullptr, nullptr};
   EOp L{P->Lidx, f.ld_p, f.M, k, 0, nullptr, P->es32, P->a1_32};
   for (int32_t step = 0; step < n_steps; ++step) {
-    e_convect<<<G, kT, 0, st>>>(f.N, f.ld_v, k, E, f.vv_idx, P->vv_dx32, P->vv_dy32, s->u, s->v,
+    EK(e_convect, G, f.N, f.ld_v, k, E, f.vv_idx, P->vv_dx32, P->vv_dy32, s->u, s->v,
                                 P->u2, P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2,
                                 P->vs2, f.dt, s->j == 0 ? 1 : 0);
-    e_helm_rhs<<<G, kT, 0, st>>>(f.N, f.ld_v, k, E, f.vv_idx, P->vv_lap32, P->us, P->vs,
+    EK(e_helm_rhs, G, f.N, f.ld_v, k, E, f.vv_idx, P->vv_lap32, P->us, P->vs,
                                  f.cn_form ? P->u2 : P->us2, f.cn_form ? P->v2 : P->vs2,
                                  f.vp_idx, P->vp_dx32, P->vp_dy32, P->pt2, f.v_bc, f.v_nx,
                                  f.v_ny, gu, gv, P->aE, f.dt, f.km_mode, P->rhs, P->xv);
@@ -1122,7 +1194,7 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
     if (!hr.converged)
       return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
                        "ensemble viscous solve: relative residual %.3e", hr.relres);
-    e_divergence<<<G, kT, 0, st>>>(f.M, f.ld_p, k, E, f.pv_idx, f.pv_dx, f.pv_dy, P->xv, f.p_bc,
+    EK(e_divergence, G, f.M, f.ld_p, k, E, f.pv_idx, f.pv_dx, f.pv_dy, P->xv, f.p_bc,
                                    P->scale, 1.0 / f.dt, P->pb);
     rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * nP,
                                          cudaMemcpyDeviceToDevice, st), "warm start");
@@ -1133,6 +1205,7 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
     if (rc) return rc;
     if (stats) {
       stats->poisson_iters += pr.iters;
+      stats->refinements += pr.sweeps;
       stats->poisson_relres = pr.relres;
     }
     if (pr.nonfinite) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite ensemble pressure solve");
@@ -1141,9 +1214,9 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
                        "ensemble pressure solve: relative residual %.3e", pr.relres);
     e_colmean<<<G, kT, 0, st>>>(f.M, E, P->px, P->rd, P->mean);
     e_split<<<G, kT, 0, st>>>(nP, P->px, P->px2);
-    e_pressure<<<G, kT, 0, st>>>(f.M, f.ld_p, k, E, f.pp_idx, P->pp_lap32, P->px, P->px2, P->mean,
+    EK(e_pressure, G, f.M, f.ld_p, k, E, f.pp_idx, P->pp_lap32, P->px, P->px2, P->mean,
                                  P->aE, s->pt, s->p, P->pt2);
-    e_correct<<<G, kT, 0, st>>>(f.N, f.ld_v, k, E, f.vp_idx, P->vp_dx32, P->vp_dy32, P->pt2, P->xv,
+    EK(e_correct, G, f.N, f.ld_v, k, E, f.vp_idx, P->vp_dx32, P->vp_dy32, P->pt2, P->xv,
                                 f.v_bc, gu, gv, f.dt, f.overwrite_bc, s->u, s->v, P->u2, P->v2);
     P->launches += 6;
     rc = check_cuda(ctx, cudaGetLastError(), "ensemble stage 3");

@@ -2201,20 +2201,18 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     }
     if (rc0) return rc0;
   }
-  // TEMPORARY measurement switch: direct-load pressure SpMV at full occupancy
-  static const int direct_pc = getenv("RBFFD_PC_DIRECT") ? atoi(getenv("RBFFD_PC_DIRECT")) : 0;
+  // Pressure SpMVs of the preconditioned solve: FP32 operators stage 256-row
+  // tiles (48 us per launch at 1M rows, against 50-61 us with direct loads at
+  // 4-8 blocks per SM); FP64 operators load directly at 6 blocks per SM
+  // (91.5 against 97 us: an FP64 tile leaves room for two blocks per SM).
+  constexpr int kPcDirect = std::is_same<TW, double>::value ? 6 : 0;
   const int Gd = (int)std::max<int64_t>(
-      1, std::min<int64_t>((op.n + kThreads - 1) / kThreads,
-                           (int64_t)sm_count() * (direct_pc > 0 ? direct_pc : 1)));
+      1, std::min<int64_t>((op.n + kThreads - 1) / kThreads, (int64_t)sm_count() * 6));
   auto spmv_pc = [&](auto W, cudaStream_t s, const TV* z, TV* y, const TV* dv, KScal* scp,
                      int* wf) {
     constexpr int WH = decltype(W)::value;
-    if (direct_pc == 8)
-      k_spmv_pc<K, TW, TV, WH, 8><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
-    else if (direct_pc == 6)
-      k_spmv_pc<K, TW, TV, WH, 6><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
-    else if (direct_pc == 4)
-      k_spmv_pc<K, TW, TV, WH, 4><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
+    if constexpr (kPcDirect > 0)
+      k_spmv_pc<K, TW, TV, WH, kPcDirect><<<Gd, kThreads, 0, s>>>(op, z, y, dv, scp, P->gr, wf);
     else
       k_spmv_pc<K, TW, TV, WH><<<Gs, kThreads, smem, s>>>(op, z, y, dv, scp, P->gr, wf);
   };
