@@ -31,6 +31,7 @@ namespace {
 constexpr int kT = 256;        // threads per block
 constexpr int kCMax = 128;     // columns of a batched solve (2 x 64 members)
 constexpr int kRV = 3;         // values reduced per column
+constexpr int kInnerRestart = 50;  // iterations of one inner solve, at most
 
 __device__ __forceinline__ float2 split2e(double x) {
   const float hi = (float)x;
@@ -53,22 +54,33 @@ struct EReduce {
 };
 
 // Per-column reduction of NV values (column = thread index mod C, fixed under
-// the grid stride): block sums in thread order, then the last block sums the
-// block partials in block order and runs fin(column, totals) for every column.
+// the loops; thread t is in group g = t / C of the kT / C groups).  In a block,
+// the groups are summed by a fixed tree into group 0, which stores the block
+// partials; the last block then has every thread sum the partials of blocks
+// g, g + G, ... for its column in block order, reduces the groups by the same
+// tree and runs fin(column, totals) for every column.  The order of every sum
+// is fixed, so the result does not depend on timing.
 template <int NV, typename Fin>
 __device__ __forceinline__ void col_reduce(double (&v)[NV], int C, EReduce rd, Fin fin) {
   __shared__ double sh[NV][kT];
   __shared__ bool last;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, G = kT / C, g = t / C;
+  auto tree = [&]() {  // sh[j][c] = sum over the groups of sh[j][g C + c]
+    for (int h = G / 2; h >= 1; h /= 2) {
+      if (g < h) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[j][t] += sh[j][t + h * C];
+      }
+      __syncthreads();
+    }
+  };
 #pragma unroll
   for (int j = 0; j < NV; ++j) sh[j][t] = v[j];
   __syncthreads();
+  tree();
   if (t < C) {
-    for (int j = 0; j < NV; ++j) {
-      double a = 0.0;
-      for (int q = t; q < kT; q += C) a += sh[j][q];
-      rd.partials[((size_t)blockIdx.x * kRV + j) * C + t] = a;
-    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) rd.partials[((size_t)blockIdx.x * kRV + j) * C + t] = sh[j][t];
   }
   __syncthreads();
   if (t == 0) {
@@ -78,15 +90,21 @@ __device__ __forceinline__ void col_reduce(double (&v)[NV], int C, EReduce rd, F
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int c = t; c < C; c += kT) {
+  const int c = t % C;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double a = 0.0;
+    for (int b = g; b < (int)gridDim.x; b += G)
+      a += ((volatile double*)rd.partials)[((size_t)b * kRV + j) * C + c];
+    sh[j][t] = a;
+  }
+  __syncthreads();
+  tree();
+  if (t < C) {
     double tot[NV];
-    for (int j = 0; j < NV; ++j) {
-      double a = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b)
-        a += ((volatile double*)rd.partials)[((size_t)b * kRV + j) * C + c];
-      tot[j] = a;
-    }
-    fin(c, tot);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = sh[j][t];
+    fin(t, tot);
   }
   if (t == 0) *rd.counter = 0u;
 }
@@ -1120,7 +1138,10 @@ int ens_refine(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const double* w64, con
     if (rc) return rc;
     e_to32<<<G, kT, 0, st>>>(op.n, C, P->r64, P->isc, P->r32);
     ESolve inner;
-    rc = ens_bicgstab(ctx, P, op, w32, C, pc, inner_tol, maxit - used, &inner, st);
+    // at most kInnerRestart iterations per inner solve: a column whose
+    // recurrences stagnate restarts from its true residual in the next sweep
+    rc = ens_bicgstab(ctx, P, op, w32, C, pc, inner_tol,
+                      maxit - used < kInnerRestart ? maxit - used : kInnerRestart, &inner, st);
     if (rc) return rc;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
