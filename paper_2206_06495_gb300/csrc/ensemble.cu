@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(kT)
 
 // Pre-smoothing from zero (x = omega D^-1 r) and restriction of its residual
 // to the aggregates: thread (aggregate I, column c) takes I's rows in order.
+template <int W>
 __global__ void __launch_bounds__(kT)
     e_pc_restrict(AmgLevel F, int64_t nagg, int C, const float* __restrict__ r,
                   float* __restrict__ x, float* __restrict__ rc, const EScal* sc) {
@@ -534,9 +535,19 @@ __global__ void __launch_bounds__(kT)
       const float xi = F.wd[i] * ri;
       x[(int64_t)i * C + c] = xi;
       float ax = F.diag[i] * xi;
-      for (int s = 0; s < F.width; ++s) {
-        const int32_t j = F.idx[s * F.ld + i];
-        ax += F.val[s * F.ld + i] * (F.wd[j] * r[(int64_t)j * C + c]);
+      if constexpr (W > 0) {  // every load of the row in flight at once
+#pragma unroll
+        for (int s = 0; s < W; ++s) {
+          if (s < F.width) {
+            const int32_t j = F.idx[s * F.ld + i];
+            ax += F.val[s * F.ld + i] * (F.wd[j] * r[(int64_t)j * C + c]);
+          }
+        }
+      } else {
+        for (int s = 0; s < F.width; ++s) {
+          const int32_t j = F.idx[s * F.ld + i];
+          ax += F.val[s * F.ld + i] * (F.wd[j] * r[(int64_t)j * C + c]);
+        }
       }
       acc += ri - ax;
     }
@@ -547,43 +558,64 @@ __global__ void __launch_bounds__(kT)
 // Coarsest level: z = X r for the C columns (X: nc x nc, the dense inverse)
 // as a tiled product.  A block takes TR rows of z and every column; thread t
 // keeps column t mod C and the rows g, g + G, ... of the tile (G = kT / C
-// groups); X and r move through shared memory in slabs of kCJ columns of X
-// (rows of r), and every output sums its products in j order, as the plain
-// dot product does.  Then the correction of the next finer level's rows of
-// aggregate `row` (has_fine), or z itself.
+// groups).  X and r move through shared memory in slabs of kcj columns of X
+// (rows of r); the next slab's loads are issued into registers before the
+// current slab's products, so the loads overlap the arithmetic.  Every output
+// sums its products in j order, as the plain dot product does.  Then the
+// correction of the next finer level's rows of aggregate `row` (has_fine), or
+// z itself.
 constexpr int kCJ = 32;
 constexpr int kCoarseRows = 16;  // TR for C >= 16 (fewer columns: one row per thread)
+constexpr int kPre = 8;          // slab values a thread prefetches, per operand
 
 __global__ void __launch_bounds__(kT)
     e_pc_coarse(int64_t nc, int C, const float* __restrict__ X, const float* __restrict__ r,
                 float* __restrict__ z, AmgLevel Fine, float* __restrict__ xfine, int has_fine,
                 const EScal* sc) {
   if (sc->done) return;
-  __shared__ float xs[kT * (kCJ + 1)];  // TR x kCJ slab of X (TR <= kT), padded rows
-  __shared__ float rs[kCJ * 64];        // kCJ x C slab of r (C <= 64)
+  __shared__ float xs[kT * kPre + kT];  // TR x kcj slab of X, rows padded by one
+  __shared__ float rs[kCJ * 64];        // kcj x C slab of r (C <= 64)
   const int G = kT / C;
   const int TR = G > kCoarseRows ? G : kCoarseRows;
+  const int kcj = kT * kPre / TR < kCJ ? kT * kPre / TR : kCJ;  // TR kcj <= kT kPre
   const int RPT = TR / G;  // rows per thread, <= kCoarseRows / 4
   const int t = (int)threadIdx.x, c = t % C, g = t / C;
   const int64_t row0 = (int64_t)blockIdx.x * TR;
   float acc[kCoarseRows / 4] = {};
-  for (int64_t j0 = 0; j0 < nc; j0 += kCJ) {
-    for (int e = t; e < TR * kCJ; e += kT) {
-      const int rr = e / kCJ, jj = e % kCJ;
-      const int64_t row = row0 + rr, col = j0 + jj;
-      xs[rr * (kCJ + 1) + jj] = (row < nc && col < nc) ? X[row * nc + col] : 0.f;
+  float px[kPre], pr[kPre];
+  auto load = [&](int64_t j0) {
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int e = t + k * kT;
+      if (e < TR * kcj) {
+        const int rr = e / kcj, jj = e % kcj;
+        px[k] = (row0 + rr < nc && j0 + jj < nc) ? X[(row0 + rr) * nc + j0 + jj] : 0.f;
+      }
+      if (e < kcj * C) {
+        const int jj = e / C, cc = e % C;
+        pr[k] = (j0 + jj < nc) ? r[(j0 + jj) * C + cc] : 0.f;
+      }
     }
-    for (int e = t; e < kCJ * C; e += kT) {
-      const int jj = e / C, cc = e % C;
-      rs[jj * C + cc] = (j0 + jj < nc) ? r[(j0 + jj) * C + cc] : 0.f;
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int e = t + k * kT;
+      if (e < TR * kcj) xs[(e / kcj) * (kcj + 1) + e % kcj] = px[k];
+      if (e < kcj * C) rs[e] = pr[k];
     }
+  };
+  load(0);
+  for (int64_t j0 = 0; j0 < nc; j0 += kcj) {
+    store();
     __syncthreads();
-    const int jn = (int)(nc - j0 < kCJ ? nc - j0 : kCJ);
+    if (j0 + kcj < nc) load(j0 + kcj);
+    const int jn = (int)(nc - j0 < kcj ? nc - j0 : kcj);
     for (int jj = 0; jj < jn; ++jj) {
       const float rv = rs[jj * C + c];
 #pragma unroll
       for (int q = 0; q < kCoarseRows / 4; ++q)
-        if (q < RPT) acc[q] += xs[(g + q * G) * (kCJ + 1) + jj] * rv;
+        if (q < RPT) acc[q] += xs[(g + q * G) * (kcj + 1) + jj] * rv;
     }
     __syncthreads();
   }
@@ -604,6 +636,7 @@ __global__ void __launch_bounds__(kT)
 // coarse correction; above level 0 it corrects the finer level's rows of each
 // aggregate (x_fine += scale z), on level 0 it writes z in P-node order and
 // reduces its per-column sum (for B v = z - mean(z) + mu / M)
+template <int W>
 __global__ void __launch_bounds__(kT)
     e_pc_up(AmgLevel F, int C, const float* __restrict__ r, const float* __restrict__ x,
             AmgLevel Fine, float* __restrict__ xfine, int level0,
@@ -615,9 +648,19 @@ __global__ void __launch_bounds__(kT)
     const int c = ef_c;
     const float xi = x[f];
     float ax = F.diag[i] * xi;
-    for (int s = 0; s < F.width; ++s) {
-      const int32_t j = F.idx[s * F.ld + i];
-      ax += F.val[s * F.ld + i] * x[(int64_t)j * C + c];
+    if constexpr (W > 0) {
+#pragma unroll
+      for (int s = 0; s < W; ++s) {
+        if (s < F.width) {
+          const int32_t j = F.idx[s * F.ld + i];
+          ax += F.val[s * F.ld + i] * x[(int64_t)j * C + c];
+        }
+      }
+    } else {
+      for (int s = 0; s < F.width; ++s) {
+        const int32_t j = F.idx[s * F.ld + i];
+        ax += F.val[s * F.ld + i] * x[(int64_t)j * C + c];
+      }
     }
     const float zi = xi + F.wd[i] * (r[f] - ax);
     if (level0) {
@@ -754,6 +797,7 @@ struct EnsPlan {
   float* lr[kAmgMaxLevels + 1] = {};
   float* lx[kAmgMaxLevels + 1] = {};
   EScal* sc = nullptr;
+  EScal* sc_t = nullptr;  // scalars of the timed SpMV launches (profile)
   EReduce rd{};
   int64_t launches = 0;
 };
@@ -785,6 +829,18 @@ int ealloc(rbffd_ctx* ctx, EnsPlan* p, T** out, size_t count) {
       kern<28><<<grid, kT, 0, st>>>(__VA_ARGS__);                \
     else                                                         \
       kern<0><<<grid, kT, 0, st>>>(__VA_ARGS__);                 \
+  } while (0)
+
+// kern<8> / kern<16> for graph rows of at most that width (slots unrolled
+// and predicated), kern<0> (plain loop) for wider ones
+#define EW(kern, width, ...)                                     \
+  do {                                                           \
+    if ((width) <= 8)                                            \
+      kern<8><<<G, kT, 0, st>>>(__VA_ARGS__);                    \
+    else if ((width) <= 16)                                      \
+      kern<16><<<G, kT, 0, st>>>(__VA_ARGS__);                   \
+    else                                                         \
+      kern<0><<<G, kT, 0, st>>>(__VA_ARGS__);                    \
   } while (0)
 
 int ens_to32(rbffd_ctx* ctx, EnsPlan* p, const double* src, int64_t n, float** dst,
@@ -901,7 +957,7 @@ int ens_build(rbffd_ctx* ctx, const rbffd_flow& f, int E, EnsPlan** out, cudaStr
   p->k = ctx->prm.n;
   p->N = f.N;
   p->M = f.M;
-  p->grid = sm_count() * 4;
+  p->grid = sm_count() * 8;  // 8 blocks of 256 per SM
   const int C = 2 * E, k = p->k;
   const int64_t nv = f.ld_v * k, np = f.ld_p * k;
   int rc = 0;
@@ -989,6 +1045,7 @@ int ens_build(rbffd_ctx* ctx, const rbffd_flow& f, int E, EnsPlan** out, cudaStr
   TRY(ealloc(ctx, p, &p->xsum, kCMax));
   TRY(ealloc(ctx, p, &p->mean, kCMax));
   TRY(ealloc(ctx, p, &p->sc, 1));
+  TRY(ealloc(ctx, p, &p->sc_t, 1));
   TRY(ealloc(ctx, p, &p->rd.partials, (size_t)p->grid * kRV * kCMax));
   TRY(ealloc(ctx, p, &p->rd.counter, 1));
   TRY(check_cuda(ctx, cudaMemsetAsync(p->rd.counter, 0, sizeof(unsigned int), st), "memset"));
@@ -1015,8 +1072,8 @@ void ens_vcycle(EnsPlan* P, const float* v, int which, float* zout, cudaStream_t
   e_pc_in<<<G, kT, 0, st>>>(P->M, C, v, a->c, a->ce, a->perm0, which, a->inv_ces, P->sc,
                             P->lr[0]);
   for (int l = 0; l + 1 < L; ++l)
-    e_pc_restrict<<<G, kT, 0, st>>>(a->lev[l], a->lev[l + 1].n, C, P->lr[l], P->lx[l],
-                                    P->lr[l + 1], P->sc);
+    EW(e_pc_restrict, a->lev[l].width, a->lev[l], a->lev[l + 1].n, C, P->lr[l], P->lx[l],
+       P->lr[l + 1], P->sc);
   const AmgLevel none{};
   const bool fine = L >= 2;
   const int TRc = kT / C > kCoarseRows ? kT / C : kCoarseRows;
@@ -1028,9 +1085,9 @@ void ens_vcycle(EnsPlan* P, const float* v, int which, float* zout, cudaStream_t
     e_pc_fin<<<G, kT, 0, st>>>(P->M, C, P->lx[0], a->perm0, zout, which, a->inv_ces, a->inv_R,
                                P->sc, P->rd);
   for (int l = L - 2; l >= 0; --l)
-    e_pc_up<<<G, kT, 0, st>>>(a->lev[l], C, P->lr[l], P->lx[l], l ? a->lev[l - 1] : none,
-                              l ? P->lx[l - 1] : nullptr, l == 0 ? 1 : 0, a->perm0, zout, which,
-                              a->inv_ces, a->inv_R, P->sc, P->rd);
+    EW(e_pc_up, a->lev[l].width, a->lev[l], C, P->lr[l], P->lx[l], l ? a->lev[l - 1] : none,
+       l ? P->lx[l - 1] : nullptr, l == 0 ? 1 : 0, a->perm0, zout, which, a->inv_ces,
+       a->inv_R, P->sc, P->rd);
   P->launches += 2 + 2 * (L - 1) + (fine ? 0 : 1);
 }
 
@@ -1247,6 +1304,35 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
   }
   rc = check_cuda(ctx, cudaStreamSynchronize(st), "ensemble sync");
   if (stats) stats->launches = P->launches - l0;
+  if (!rc && stats && f.profile) {
+    // the batched pressure SpMV timed alone: 20 back-to-back launches on this
+    // plan's operator and work vectors (every column active), CUDA events on
+    // the caller's stream
+    EScal* hs = (EScal*)ctx->host_pinned;
+    memset(hs, 0, sizeof(EScal));
+    hs->C = E;
+    for (int c = 0; c < E; ++c) hs->active[c] = 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = check_cuda(ctx, cudaMemcpyAsync(P->sc_t, hs, sizeof(EScal), cudaMemcpyHostToDevice, st),
+                    "timing scalars");
+    if (!rc) rc = check_cuda(ctx, cudaEventCreate(&e0), "event");
+    if (!rc) rc = check_cuda(ctx, cudaEventCreate(&e1), "event");
+    if (!rc) {
+      constexpr int kReps = 20;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < kReps; ++r)
+        EK(e_spmv_v, G, L, P->Lw32, P->kw[7], P->kw[4], P->kw[2], P->sc_t, P->rd);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      rc = check_cuda(ctx, cudaEventSynchronize(e1), "timing sync");
+      if (!rc && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        stats->spmv_batch_ms += ms;
+        stats->spmv_batch_launches += kReps;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
   return rc;
 }
 

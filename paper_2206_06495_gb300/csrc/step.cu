@@ -961,17 +961,23 @@ __global__ void __launch_bounds__(kThreads)
 // ---------------------------------------------- cluster tail of the V-cycle
 // The levels from l0 (at most kTailRows rows) down to the coarsest run in ONE
 // launch of a thread-block cluster instead of two launches per level and one
-// for the coarse solve.  Each tail level's r and x are split over the CTAs'
-// shared memory in power-of-two chunks (row j lives in CTA j >> shift, at
-// j & (chunk - 1)); neighbours' values are read through distributed shared
-// memory, and cluster barriers separate the phases: the restriction of each
-// level, the dense coarse solve, the post-smoothing of each level.  A row and
-// an aggregate take the arithmetic of k_pc_restrict, k_pc_coarse and k_pc_up
-// in the same order.  Input: the restricted residual of level l0 (global
-// lev[l0].r); output: the coarse-grid correction added to lev[l0 - 1].x.
+// for the coarse solve.  Each tail level's r and x (and the residual of the
+// restriction) are split over the CTAs' shared memory in power-of-two chunks
+// (row j lives in CTA j >> shift, at j & (chunk - 1)); neighbours' values are
+// read through distributed shared memory, and cluster barriers separate the
+// phases.  Restriction of level l: one thread per row forms the residual of
+// the pre-smoothed iterate, then one thread per aggregate sums its rows in
+// order; the dense coarse solve takes one warp per row; the post-smoothing of
+// level l takes one thread per row and corrects the next finer level.  Rows
+// and aggregates do the arithmetic of k_pc_restrict, k_pc_coarse and k_pc_up
+// in the same order, with the slot loops unrolled to kTailWidth (the tail is
+// used only where every tail level is at most that wide).  Input: the
+// restricted residual of level l0 (global lev[l0].r); output: the coarse-grid
+// correction added to lev[l0 - 1].x.
 namespace cg = cooperative_groups;
 constexpr int kTailThreads = 1024;
-constexpr int64_t kTailRows = 65536;      // largest first tail level
+constexpr int64_t kTailRows = 16384;      // largest first tail level
+constexpr int kTailWidth = 16;            // widest tail level
 constexpr size_t kTailSmem = 160 * 1024;  // dynamic shared memory per CTA, at most
 
 struct TailLevels {
@@ -980,11 +986,12 @@ struct TailLevels {
 struct TailArgs {
   int l0 = 0, nlev = 0;
   int shift[kAmgMaxLevels] = {};  // log2 of the rows per CTA of each tail level
-  int off_r[kAmgMaxLevels] = {}, off_x[kAmgMaxLevels] = {};  // float offsets in shared memory
+  // float offsets in shared memory: r, x and the restriction's residual
+  int off_r[kAmgMaxLevels] = {}, off_x[kAmgMaxLevels] = {}, off_q[kAmgMaxLevels] = {};
   int off_rc = 0;  // the whole coarse right side, gathered by every CTA
 };
 
-__global__ void __launch_bounds__(kTailThreads)
+__global__ void __launch_bounds__(kTailThreads, 1)
     k_pc_tail(TailLevels T, TailArgs A, int64_t nc, const float* __restrict__ X,
               const KScal* sc) {
   if (sc->done) return;  // the same verdict in every CTA of the cluster
@@ -1011,23 +1018,37 @@ __global__ void __launch_bounds__(kTailThreads)
   // pre-smoothing from zero and restriction, level l -> l + 1
   for (int l = A.l0; l + 1 < A.nlev; ++l) {
     const AmgLevel& F = T.lev[l];
-    int64_t a0, a1;
-    span(l + 1, a0, a1);
-    float* rc = tsm + A.off_r[l + 1];
-    for (int64_t I = a0 + t; I < a1; I += kTailThreads) {
-      float acc = 0.f;
-      for (int32_t i = F.cptr[I]; i < F.cptr[I + 1]; ++i) {
-        const float ri = *at(A.off_r[l], l, i);
+    {
+      int64_t r0, r1;
+      span(l, r0, r1);
+      const float* rs = tsm + A.off_r[l];
+      float* xs = tsm + A.off_x[l];
+      float* qs = tsm + A.off_q[l];
+      for (int64_t i = r0 + t; i < r1; i += kTailThreads) {
+        const float ri = rs[i - r0];
         const float xi = F.wd[i] * ri;
-        *at(A.off_x[l], l, i) = xi;
+        xs[i - r0] = xi;
         float off = 0.f;
-        for (int s = 0; s < F.width; ++s) {
-          const int32_t j = F.idx[s * F.ld + i];
-          off += F.val[s * F.ld + i] * (F.wd[j] * *at(A.off_r[l], l, j));
+#pragma unroll
+        for (int s = 0; s < kTailWidth; ++s) {
+          if (s < F.width) {
+            const int32_t j = F.idx[s * F.ld + i];
+            off += F.val[s * F.ld + i] * (F.wd[j] * *at(A.off_r[l], l, j));
+          }
         }
-        acc += ri - (F.diag[i] * xi + off);
+        qs[i - r0] = ri - (F.diag[i] * xi + off);
       }
-      rc[I - a0] = acc;
+    }
+    cl.sync();
+    {
+      int64_t a0, a1;
+      span(l + 1, a0, a1);
+      float* rc = tsm + A.off_r[l + 1];
+      for (int64_t I = a0 + t; I < a1; I += kTailThreads) {
+        float acc = 0.f;
+        for (int32_t i = F.cptr[I]; i < F.cptr[I + 1]; ++i) acc += *at(A.off_q[l], l, i);
+        rc[I - a0] = acc;
+      }
     }
     cl.sync();
   }
@@ -1064,8 +1085,9 @@ __global__ void __launch_bounds__(kTailThreads)
     for (int64_t i = r0 + t; i < r1; i += kTailThreads) {
       const float xi = xs[i - r0];
       float off = 0.f;
-      for (int s = 0; s < F.width; ++s)
-        off += F.val[s * F.ld + i] * *at(A.off_x[l], l, F.idx[s * F.ld + i]);
+#pragma unroll
+      for (int s = 0; s < kTailWidth; ++s)
+        if (s < F.width) off += F.val[s * F.ld + i] * *at(A.off_x[l], l, F.idx[s * F.ld + i]);
       const float zi = xi + F.wd[i] * (rs[i - r0] - (F.diag[i] * xi + off));
       const float v = kAmgCoarseScale * zi;
       for (int32_t c = Fn.cptr[i]; c < Fn.cptr[i + 1]; ++c) {
@@ -1930,6 +1952,7 @@ int tail_setup(rbffd_ctx* ctx, StepPlan* p) {
   const Amg* a = p->amg;
   p->tail_cs = 0;
   if (!a || a->nlev < 3) return RBFFD_OK;
+  if (getenv("RBFFD_NO_TAIL")) return RBFFD_OK;  // TEMPORARY A/B switch
   int rc = check_cuda(ctx,
                       cudaFuncSetAttribute(k_pc_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)kTailSmem),
@@ -1942,6 +1965,9 @@ int tail_setup(rbffd_ctx* ctx, StepPlan* p) {
   for (int cs = wide ? 16 : 8; cs >= 8; cs /= 2) {
     for (int l0 = 1; l0 + 2 <= a->nlev; ++l0) {
       if (a->lev[l0].n > kTailRows) continue;
+      bool narrow = true;
+      for (int l = l0; l + 1 < a->nlev; ++l) narrow = narrow && a->lev[l].width <= kTailWidth;
+      if (!narrow) break;
       TailArgs A;
       A.l0 = l0;
       A.nlev = a->nlev;
@@ -1953,6 +1979,8 @@ int tail_setup(rbffd_ctx* ctx, StepPlan* p) {
         A.off_r[l] = (int)off;
         off += (size_t)1 << sh;
         A.off_x[l] = (int)off;
+        off += (size_t)1 << sh;
+        A.off_q[l] = (int)off;
         off += (size_t)1 << sh;
       }
       A.off_rc = (int)off;
