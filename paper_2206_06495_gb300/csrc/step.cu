@@ -27,8 +27,6 @@
 // corrections come from FP32 solves on FP32 copies of the scaled operators.
 // Pressure solves are right-preconditioned by the multigrid V-cycle of
 // amg.cuh (one application per search direction).
-#include <cooperative_groups.h>
-
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -958,149 +956,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// ---------------------------------------------- cluster tail of the V-cycle
-// The levels from l0 (at most kTailRows rows) down to the coarsest run in ONE
-// launch of a thread-block cluster instead of two launches per level and one
-// for the coarse solve.  Each tail level's r and x (and the residual of the
-// restriction) are split over the CTAs' shared memory in power-of-two chunks
-// (row j lives in CTA j >> shift, at j & (chunk - 1)); neighbours' values are
-// read through distributed shared memory, and cluster barriers separate the
-// phases.  Restriction of level l: one thread per row forms the residual of
-// the pre-smoothed iterate, then one thread per aggregate sums its rows in
-// order; the dense coarse solve takes one warp per row; the post-smoothing of
-// level l takes one thread per row and corrects the next finer level.  Rows
-// and aggregates do the arithmetic of k_pc_restrict, k_pc_coarse and k_pc_up
-// in the same order, with the slot loops unrolled to kTailWidth (the tail is
-// used only where every tail level is at most that wide).  Input: the
-// restricted residual of level l0 (global lev[l0].r); output: the coarse-grid
-// correction added to lev[l0 - 1].x.
-namespace cg = cooperative_groups;
-constexpr int kTailThreads = 1024;
-constexpr int64_t kTailRows = 16384;      // largest first tail level
-constexpr int kTailWidth = 16;            // widest tail level
-constexpr size_t kTailSmem = 160 * 1024;  // dynamic shared memory per CTA, at most
-
-struct TailLevels {
-  AmgLevel lev[kAmgMaxLevels];
-};
-struct TailArgs {
-  int l0 = 0, nlev = 0;
-  int shift[kAmgMaxLevels] = {};  // log2 of the rows per CTA of each tail level
-  // float offsets in shared memory: r, x and the restriction's residual
-  int off_r[kAmgMaxLevels] = {}, off_x[kAmgMaxLevels] = {}, off_q[kAmgMaxLevels] = {};
-  int off_rc = 0;  // the whole coarse right side, gathered by every CTA
-};
-
-__global__ void __launch_bounds__(kTailThreads, 1)
-    k_pc_tail(TailLevels T, TailArgs A, int64_t nc, const float* __restrict__ X,
-              const KScal* sc) {
-  if (sc->done) return;  // the same verdict in every CTA of the cluster
-  extern __shared__ __align__(16) float tsm[];
-  cg::cluster_group cl = cg::this_cluster();
-  const int q = (int)cl.block_rank();
-  const int t = threadIdx.x;
-  auto at = [&](int off, int l, int64_t j) -> float* {  // row j of a level vector, any CTA
-    const unsigned o = (unsigned)(j >> A.shift[l]);
-    return cl.map_shared_rank(tsm + off, o) + (j & ((1ll << A.shift[l]) - 1));
-  };
-  auto span = [&](int l, int64_t& r0, int64_t& r1) {  // rows of level l held here
-    const int64_t ch = 1ll << A.shift[l], n = T.lev[l].n;
-    r0 = (int64_t)q * ch < n ? (int64_t)q * ch : n;
-    r1 = r0 + ch < n ? r0 + ch : n;
-  };
-  {
-    int64_t r0, r1;
-    span(A.l0, r0, r1);
-    float* rs = tsm + A.off_r[A.l0];
-    for (int64_t i = r0 + t; i < r1; i += kTailThreads) rs[i - r0] = T.lev[A.l0].r[i];
-  }
-  cl.sync();
-  // pre-smoothing from zero and restriction, level l -> l + 1
-  for (int l = A.l0; l + 1 < A.nlev; ++l) {
-    const AmgLevel& F = T.lev[l];
-    {
-      int64_t r0, r1;
-      span(l, r0, r1);
-      const float* rs = tsm + A.off_r[l];
-      float* xs = tsm + A.off_x[l];
-      float* qs = tsm + A.off_q[l];
-      for (int64_t i = r0 + t; i < r1; i += kTailThreads) {
-        const float ri = rs[i - r0];
-        const float xi = F.wd[i] * ri;
-        xs[i - r0] = xi;
-        float off = 0.f;
-#pragma unroll
-        for (int s = 0; s < kTailWidth; ++s) {
-          if (s < F.width) {
-            const int32_t j = F.idx[s * F.ld + i];
-            off += F.val[s * F.ld + i] * (F.wd[j] * *at(A.off_r[l], l, j));
-          }
-        }
-        qs[i - r0] = ri - (F.diag[i] * xi + off);
-      }
-    }
-    cl.sync();
-    {
-      int64_t a0, a1;
-      span(l + 1, a0, a1);
-      float* rc = tsm + A.off_r[l + 1];
-      for (int64_t I = a0 + t; I < a1; I += kTailThreads) {
-        float acc = 0.f;
-        for (int32_t i = F.cptr[I]; i < F.cptr[I + 1]; ++i) acc += *at(A.off_q[l], l, i);
-        rc[I - a0] = acc;
-      }
-    }
-    cl.sync();
-  }
-  // coarsest level: z = X r (one warp per row over the cluster's warps), then
-  // the correction of the next finer level's rows of each aggregate
-  {
-    const int lc = A.nlev - 1;
-    float* rcf = tsm + A.off_rc;
-    for (int64_t j = t; j < nc; j += kTailThreads) rcf[j] = *at(A.off_r[lc], lc, j);
-    __syncthreads();
-    const AmgLevel& Fn = T.lev[lc - 1];
-    const int lane = t & 31;
-    const int64_t nw = (int64_t)cl.num_blocks() * (kTailThreads / 32);
-    for (int64_t row = (int64_t)q * (kTailThreads / 32) + (t >> 5); row < nc; row += nw) {
-      float acc = 0.f;
-#pragma unroll 8
-      for (int64_t j = lane; j < nc; j += 32) acc += X[row * nc + j] * rcf[j];
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        const float v = kAmgCoarseScale * acc;
-        for (int32_t c = Fn.cptr[row]; c < Fn.cptr[row + 1]; ++c) *at(A.off_x[lc - 1], lc - 1, c) += v;
-      }
-    }
-    cl.sync();
-  }
-  // post-smoothing of each level, and its correction of the next finer level
-  for (int l = A.nlev - 2; l >= A.l0; --l) {
-    const AmgLevel& F = T.lev[l];
-    const AmgLevel& Fn = T.lev[l - 1];
-    int64_t r0, r1;
-    span(l, r0, r1);
-    const float* xs = tsm + A.off_x[l];
-    const float* rs = tsm + A.off_r[l];
-    for (int64_t i = r0 + t; i < r1; i += kTailThreads) {
-      const float xi = xs[i - r0];
-      float off = 0.f;
-#pragma unroll
-      for (int s = 0; s < kTailWidth; ++s)
-        if (s < F.width) off += F.val[s * F.ld + i] * *at(A.off_x[l], l, F.idx[s * F.ld + i]);
-      const float zi = xi + F.wd[i] * (rs[i - r0] - (F.diag[i] * xi + off));
-      const float v = kAmgCoarseScale * zi;
-      for (int32_t c = Fn.cptr[i]; c < Fn.cptr[i + 1]; ++c) {
-        if (l - 1 >= A.l0)
-          *at(A.off_x[l - 1], l - 1, c) += v;
-        else
-          Fn.x[c] += v;
-      }
-    }
-    cl.sync();  // also keeps every CTA's shared memory alive until the last reader is done
-  }
-}
-
 // one-level hierarchy: the lifted coarse solve is already mean-free
 __global__ void k_pc_fin1(KScal* sc, int which, double inv_ces, double inv_R) {
   if (sc->done) return;
@@ -1865,11 +1720,6 @@ struct StepPlan {
   double* dscal = nullptr;  // [0]: sum, [1..6]: residual norms
   struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
   Amg* amg = nullptr;                 // pressure preconditioner (precond = 1)
-  // cluster tail of the V-cycle (tail_cs CTAs per cluster; 0: none)
-  int tail_cs = 0;
-  size_t tail_smem = 0;
-  TailLevels tail_lev;
-  TailArgs tail_args;
   double* a1 = nullptr;    // row sums of the FP64 pressure operator
   float* a1_32 = nullptr;  // row sums of its FP32 copy
   // tile records of the pressure and viscous operators the Krylov solves
@@ -1941,77 +1791,6 @@ rbffd_flow plan_key(const rbffd_flow& f) {
   k.tol = k.inner_tol = 0.0;
   k.max_iter = k.km_mode = k.overwrite_bc = k.profile = k.cn_form = 0;
   return k;
-}
-
-// The cluster tail for the plan's hierarchy: the first level l0 >= 1 with at
-// most kTailRows rows whose tail fits kTailSmem per CTA, with a level between
-// it and the coarsest (l0 <= nlev - 2); clusters of 16 CTAs where the device
-// can hold one with that shared memory, else 8; none if neither fits (the
-// V-cycle then launches every level).
-int tail_setup(rbffd_ctx* ctx, StepPlan* p) {
-  const Amg* a = p->amg;
-  p->tail_cs = 0;
-  if (!a || a->nlev < 3) return RBFFD_OK;
-  if (getenv("RBFFD_NO_TAIL")) return RBFFD_OK;  // TEMPORARY A/B switch
-  int rc = check_cuda(ctx,
-                      cudaFuncSetAttribute(k_pc_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kTailSmem),
-                      "tail shared memory");
-  if (rc) return rc;
-  const bool wide =
-      cudaFuncSetAttribute(k_pc_tail, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-      cudaSuccess;
-  cudaGetLastError();
-  for (int cs = wide ? 16 : 8; cs >= 8; cs /= 2) {
-    for (int l0 = 1; l0 + 2 <= a->nlev; ++l0) {
-      if (a->lev[l0].n > kTailRows) continue;
-      bool narrow = true;
-      for (int l = l0; l + 1 < a->nlev; ++l) narrow = narrow && a->lev[l].width <= kTailWidth;
-      if (!narrow) break;
-      TailArgs A;
-      A.l0 = l0;
-      A.nlev = a->nlev;
-      size_t off = 0;
-      for (int l = l0; l < a->nlev; ++l) {
-        int sh = 0;
-        while (((int64_t)cs << sh) < a->lev[l].n) ++sh;
-        A.shift[l] = sh;
-        A.off_r[l] = (int)off;
-        off += (size_t)1 << sh;
-        A.off_x[l] = (int)off;
-        off += (size_t)1 << sh;
-        A.off_q[l] = (int)off;
-        off += (size_t)1 << sh;
-      }
-      A.off_rc = (int)off;
-      off += (size_t)a->nc;
-      const size_t bytes = off * sizeof(float);
-      if (bytes > kTailSmem) continue;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)cs);
-      cfg.blockDim = dim3(kTailThreads);
-      cfg.dynamicSmemBytes = bytes;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = (unsigned)cs;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, k_pc_tail, &cfg) != cudaSuccess ||
-          nclusters < 1) {
-        cudaGetLastError();
-        break;  // not with this cluster size: try the smaller one
-      }
-      p->tail_cs = cs;
-      p->tail_smem = bytes;
-      p->tail_args = A;
-      for (int l = 0; l < a->nlev; ++l) p->tail_lev.lev[l] = a->lev[l];
-      return RBFFD_OK;
-    }
-  }
-  return RBFFD_OK;
 }
 
 int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t st) {
@@ -2134,7 +1913,6 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
                    "rank-one column copy"));
     TRY(check_cuda(ctx, cudaStreamSynchronize(st), "diagonal sync"));
     TRY(amg_build(ctx, f, hd.data(), hes.data(), &p->amg, st));
-    TRY(tail_setup(ctx, p));
     TRY(palloc(ctx, p, &p->a1, f.M));
     k_rowsum<double><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->kL, p->Lw, p->a1);
     TRY(check_cuda(ctx, cudaGetLastError(), "row sums"));
@@ -2246,11 +2024,7 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
   const int64_t n = a->lev[0].n;
   k_pc_in<TV><<<G, kThreads, 0, st>>>(n, v, a->c, a->ce, a->perm0, which, a->inv_ces, P->sc,
                                        a->lev[0].r);
-  // with a cluster tail, levels 0 .. l0 - 1 restrict here and the tail takes
-  // the levels from l0 down
-  const bool tail = P->tail_cs > 0 && a == P->amg;
-  const int lt = tail ? P->tail_args.l0 : a->nlev - 1;  // restrictions: levels 0 .. lt - 1
-  for (int l = 0; l < lt; ++l) {
+  for (int l = 0; l + 1 < a->nlev; ++l) {
     const AmgLevel& F = a->lev[l];
     const int gb = (int)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)G * 2, (a->lev[l + 1].n + kRB - 1) / kRB));
@@ -2270,28 +2044,11 @@ void vcycle(StepPlan* P, const Amg* a, const TV* v, int which, TV* zout, cudaStr
       default: k_pc_restrict<0><<<gb, kThreads, 0, st>>>(F, a->lev[l + 1].n, a->lev[l + 1].r, P->sc);
     }
   }
-  if (tail) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)P->tail_cs);
-    cfg.blockDim = dim3(kTailThreads);
-    cfg.dynamicSmemBytes = P->tail_smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)P->tail_cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_pc_tail, P->tail_lev, P->tail_args, a->nc,
-                       (const float*)a->Xc, (const KScal*)P->sc);
-  } else {
-    const AmgLevel& C = a->lev[a->nlev - 1];
-    const AmgLevel& Cf = a->lev[a->nlev >= 2 ? a->nlev - 2 : 0];
-    k_pc_coarse<TV><<<grid_for(a->nc * 32), kThreads, 0, st>>>(a->nc, a->Xc, C.r, zout, Cf,
-                                                               a->nlev >= 2 ? 1 : 0, P->sc);
-  }
-  for (int l = tail ? P->tail_args.l0 - 1 : a->nlev - 2; l >= 1; --l) {
+  const AmgLevel& C = a->lev[a->nlev - 1];
+  const AmgLevel& Cf = a->lev[a->nlev >= 2 ? a->nlev - 2 : 0];
+  k_pc_coarse<TV><<<grid_for(a->nc * 32), kThreads, 0, st>>>(a->nc, a->Xc, C.r, zout, Cf,
+                                                             a->nlev >= 2 ? 1 : 0, P->sc);
+  for (int l = a->nlev - 2; l >= 1; --l) {
     const AmgLevel& F = a->lev[l];
     if (a->rec[l]) {
       const int gbr = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)G * 2, a->rec_n[l]));
@@ -2403,10 +2160,7 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   // (c . v) of the rank-one completion pairs c with v node by node: the
   // P-node-ordered copy of c (the V-cycle's input map uses the level-0 one)
   const float* pcc = pc ? pc->cnode : nullptr;
-  // V-cycle launches: input map, restrictions, coarse solve (or the cluster
-  // tail), post-smoothing sweeps, level 0
-  const int vc_launches =
-      !pc ? 0 : (P->tail_cs > 0 && pc == P->amg) ? 2 * P->tail_args.l0 + 2 : 2 * pc->nlev;
+  const int vc_launches = pc ? 2 * pc->nlev : 0;
   const int G = P->grid;
   double* sigx = P->dscal;
   KScal* h = (KScal*)ctx->host_pinned;
