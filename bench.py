@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--ens-dt", type=float, default=2.5e-4,
                     help="time step of the ensemble (stable for Re 100 to 5000 at 316^2)")
     ap.add_argument("--ens-steps", type=int, default=10)
+    ap.add_argument("--profile-ensemble", action="store_true",
+                    help="profiler capture: the batched ensemble (--ensemble members on an "
+                         "--ens-n cavity) after --warmup steps, then one ensemble step between "
+                         "cudaProfilerStart/Stop; prints its statistics")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiler capture: set up, take --warmup steps, then one step between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off); prints its "
@@ -838,6 +842,40 @@ def profile_step(args):
             "stats": s}
 
 
+def profile_ensemble(args):
+    """One batched ensemble step between cudaProfilerStart and cudaProfilerStop
+    (for ncu --profile-from-start off), after --warmup steps: the members,
+    Reynolds numbers, wall data and time step of bench.py's ensemble record."""
+    import numpy as np
+    import torch
+
+    from paper_2206_06495_gb300 import build
+    from paper_2206_06495_gb300 import nodesets as ns
+    build.build()
+    from paper_2206_06495_gb300 import rbffd as R
+
+    E = args.ensemble
+    nd = ns.jittered_cavity(args.ens_n, 4)
+    rng = np.random.default_rng(4)
+    Re = [float(r) for r in rng.uniform(100.0, 5000.0, E)]
+    lid = 1.0 + 0.05 * rng.standard_normal(E)
+    ctx = R.Context(28, 7, 3)
+    flow = R.flow_from_nodes(ctx, nd, Re=1.0, dt=args.ens_dt, precision=R.PREC_MIXED,
+                             tol=args.tol, inner_tol=args.inner_tol, max_iter=args.max_iter)
+    gu_h = np.zeros((nd.N, E))
+    gu_h[nd.v_wall == ns.WALL_TOP, :] = lid[None, :]
+    gu = torch.as_tensor(gu_h.ravel(), device="cuda")
+    gv = torch.zeros_like(gu)
+    st = R.ensemble_zeros(flow, E)
+    R.ensemble_step(ctx, flow, Re, st, gu, gv, max(args.warmup, 1))
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    s = R.ensemble_step(ctx, flow, Re, st, gu, gv, 1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return {"profile_ensemble": E, "M": nd.M, "N": nd.N, "dt": args.ens_dt, "stats": s}
+
+
 def profile_ops(args):
     """Operator kernels of the benchmark's node family between
     cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
@@ -885,6 +923,9 @@ def main():
         return
     if args.profile_step:
         print(json.dumps(profile_step(args)))
+        return
+    if args.profile_ensemble:
+        print(json.dumps(profile_ensemble(args)))
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
