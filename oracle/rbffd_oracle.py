@@ -49,6 +49,20 @@ Readings of points the paper leaves open:
      g_{j+1} (switchable).
   R7 AB2 at the first step uses C_{-1} = C_0; the flow starts from rest with
      p~_0 = 0.
+  R17 open flows (Section 5.2, flow past a cylinder): each boundary V-node
+     carries a Dirichlet or a homogeneous Neumann condition per velocity
+     component, each boundary P-node a homogeneous Neumann or a Dirichlet
+     (p~ = 0) condition.  The stress-free outlet is read as du/dn = dv/dn = 0
+     for the intermediate velocity and p~ = 0 for the pressure correction
+     (the outlet rows of the pressure system make it nonsingular: no
+     bordering); the outlet's two corner P-nodes keep the side walls'
+     Neumann row.  (With p~ = 0 there too, a mode localised at the corner,
+     where the slip side meets the outlet, grew by 1.66 per step at dt 0.01
+     on a uniform channel flow, an exact solution; with the Neumann corner
+     rows the flow stays at rounding level.)  Neumann V-rows are n_x D_x + n_y D_y on a one-sided stencil,
+     the node itself followed by its n-1 nearest interior V-nodes (as R4).
+     Dirichlet V-rows take the Kim & Moin value of R5; after the correction
+     only Dirichlet components are overwritten with the data.
 """
 from __future__ import annotations
 
@@ -725,3 +739,215 @@ def lid_bc(nodes, lid_u=1.0):
     gu[from_top] = (np.broadcast_to(lid_u, (nodes.N,)))[from_top]
     gv = np.zeros(nodes.N)
     return gu, gv
+
+
+# --------------------------------------------------------------------------
+# Open flows: the cylinder wake of Section 5.2
+BC_INTERIOR = 0
+BC_DIRICHLET = 1
+BC_NEUMANN = 2
+
+
+def wake_conditions(nodes, u_inf: float = 1.0):
+    """Boundary conditions of the cylinder wake (Section 5.2) on a
+    nodesets.cylinder_wake node set: uniform inflow u = u_inf, v = 0;
+    symmetry sides v = 0, du/dn = 0; no slip on the cylinder; the stress-free
+    outlet as du/dn = dv/dn = 0 and p~ = 0 (R17).  Returns bc_u, bc_v (per
+    V-node), bc_p (per P-node) and the Dirichlet data gu, gv."""
+    from paper_2206_06495_gb300.nodesets import (WALL_CYLINDER, WALL_INFLOW, WALL_OUTFLOW,
+                                                 WALL_SIDE)
+    vw, pw = nodes.v_wall, nodes.p_wall
+    bc_u = np.zeros(nodes.N, np.int8)
+    bc_v = np.zeros(nodes.N, np.int8)
+    bc_p = np.zeros(nodes.M, np.int8)
+    bc_u[(vw == WALL_INFLOW) | (vw == WALL_CYLINDER)] = BC_DIRICHLET
+    bc_u[(vw == WALL_SIDE) | (vw == WALL_OUTFLOW)] = BC_NEUMANN
+    bc_v[(vw == WALL_INFLOW) | (vw == WALL_CYLINDER) | (vw == WALL_SIDE)] = BC_DIRICHLET
+    bc_v[vw == WALL_OUTFLOW] = BC_NEUMANN
+    bc_p[(pw == WALL_INFLOW) | (pw == WALL_SIDE) | (pw == WALL_CYLINDER)] = BC_NEUMANN
+    bc_p[pw == WALL_OUTFLOW] = BC_DIRICHLET
+    # the outlet's two corner nodes take the side walls' Neumann row (R17)
+    y0, y1 = nodes.meta["domain"][2], nodes.meta["domain"][3]
+    bc_p[(pw == WALL_OUTFLOW) & ((nodes.py == y0) | (nodes.py == y1))] = BC_NEUMANN
+    gu = np.where(vw == WALL_INFLOW, u_inf, 0.0)
+    gv = np.zeros(nodes.N)
+    return bc_u, bc_v, bc_p, gu, gv
+
+
+def neumann_rows(nodes, rows, k: int = 28, m: int = 7, q: int = 3) -> sp.csr_matrix:
+    """n_x D_x + n_y D_y at the boundary V-nodes `rows` on one-sided stencils
+    (the node itself, then its k-1 nearest interior V-nodes; R17), as an
+    N x N matrix with those rows only."""
+    N = nodes.N
+    rows = np.asarray(rows, np.int64)
+    if rows.size == 0:
+        return sp.csr_matrix((N, N))
+    vx, vy = nodes.vx, nodes.vy
+    idx = knn(vx[rows], vy[rows], vx, vy, k, beta_mask=~nodes.v_boundary, alpha_self=rows)
+    _, w = build_weights(vx[rows], vy[rows], vx, vy, k, m, q, (OP_DX, OP_DY), idx=idx)
+    vals = nodes.v_nx[rows, None] * w[OP_DX] + nodes.v_ny[rows, None] * w[OP_DY]
+    return sp.csr_matrix((vals.ravel(), (np.repeat(rows, k), idx.ravel())), shape=(N, N))
+
+
+class OpenFlowStep:
+    """Section 3's fractional step with per-component boundary conditions
+    (R17), for open flows such as the cylinder wake of Section 5.2.
+
+    Viscous step, for each component c in (u, v): interior rows
+    (I - a D_Lap) c** = RHS (printed Crank-Nicolson form, or Kim & Moin's
+    with cn_form="kim_moin"); Dirichlet rows c** = g_{j+1} + dt D^(V,P)_c p~_j
+    (Kim & Moin, R5; km_mode 0 drops the pressure term); Neumann rows
+    n.grad c** = 0.  Pressure: interior rows D^(P,P)_Lap p~ = F/dt, Neumann
+    rows n.grad p~ = 0 (R4's one-sided rows), Dirichlet rows p~ = 0; the
+    system is nonsingular when any Dirichlet row is present.  Then
+    p = p~ - a D^(P,P)_Lap p~ and c_{j+1} = c** - dt D^(V,P)_c p~, with
+    Dirichlet components overwritten by g_{j+1}."""
+
+    def __init__(self, nodes, Re: float, dt: float, bc_u, bc_v, bc_p, k: int = 28,
+                 m: int = 7, q: int = 3, ops: Operators | None = None, km_mode: int = 2,
+                 cn_form: str = "printed", convective=None, u_conv: float = 1.0):
+        if km_mode not in (0, 2):
+            raise ValueError("km_mode is 0 or 2 for open flows")
+        if cn_form not in ("printed", "kim_moin"):
+            raise ValueError("cn_form is 'printed' or 'kim_moin'")
+        self.nodes = nodes
+        self.Re, self.dt = float(Re), float(dt)
+        self.a = self.dt / (2.0 * self.Re)
+        self.km_mode, self.cn_form = km_mode, cn_form
+        self.bc_u = np.asarray(bc_u, np.int8)
+        self.bc_v = np.asarray(bc_v, np.int8)
+        self.bc_p = np.asarray(bc_p, np.int8)
+        # convective outflow nodes: Dirichlet rows whose data follow
+        # dc/dt + u_conv dc/dn = 0 (explicit, one-sided normal derivative)
+        self.conv = (np.zeros(nodes.N, bool) if convective is None
+                     else np.asarray(convective, bool))
+        self.u_conv = float(u_conv)
+        if (self.conv & ((self.bc_u != BC_DIRICHLET) | (self.bc_v != BC_DIRICHLET))).any():
+            raise ValueError("convective outflow nodes carry Dirichlet rows")
+        if not (nodes.v_boundary[self.bc_u != BC_INTERIOR].all()
+                and nodes.v_boundary[self.bc_v != BC_INTERIOR].all()
+                and nodes.p_boundary[self.bc_p != BC_INTERIOR].all()):
+            raise ValueError("boundary conditions on interior nodes")
+        if (nodes.v_boundary & ((self.bc_u == BC_INTERIOR) | (self.bc_v == BC_INTERIOR))).any():
+            raise ValueError("a boundary V-node without a condition")
+        self.ops = ops if ops is not None else build_operators(nodes, k, m, q)
+        o, N, M = self.ops, nodes.N, nodes.M
+        nrows = np.nonzero((self.bc_u == BC_NEUMANN) | (self.bc_v == BC_NEUMANN)
+                           | self.conv)[0]
+        self.VN = neumann_rows(nodes, nrows, k, m, q)
+        self.H_u = self._viscous_matrix(self.bc_u)
+        self.H_v = self._viscous_matrix(self.bc_v)
+        inn = sp.diags((self.bc_p == BC_INTERIOR).astype(float))
+        neu = sp.diags((self.bc_p == BC_NEUMANN).astype(float))
+        dirichlet = sp.diags((self.bc_p == BC_DIRICHLET).astype(float))
+        self.L = (inn @ o.pp_lap
+                  + neu @ (sp.diags(nodes.p_nx) @ o.pn_x + sp.diags(nodes.p_ny) @ o.pn_y)
+                  + dirichlet).tocsc()
+        self.Hu_lu = spla.splu(self.H_u)
+        self.Hv_lu = spla.splu(self.H_v)
+        self.L_lu = spla.splu(self.L)
+
+    def _viscous_matrix(self, bc):
+        N = self.nodes.N
+        inn = sp.diags((bc == BC_INTERIOR).astype(float))
+        dirichlet = sp.diags((bc == BC_DIRICHLET).astype(float))
+        neu = sp.diags((bc == BC_NEUMANN).astype(float))
+        return (inn @ (sp.identity(N) - self.a * self.ops.vv_lap) + dirichlet
+                + neu @ self.VN).tocsc()
+
+    def initial_state(self, u0=None, v0=None) -> FlowState:
+        N, M = self.nodes.N, self.nodes.M
+        u = np.zeros(N) if u0 is None else np.array(u0, np.float64)
+        v = np.zeros(N) if v0 is None else np.array(v0, np.float64)
+        return FlowState(u=u, v=v, cu_prev=np.zeros(N), cv_prev=np.zeros(N),
+                         pt=np.zeros(M), p=np.zeros(M))
+
+    def step(self, st: FlowState, gu, gv) -> FlowState:
+        o, dt, a = self.ops, self.dt, self.a
+        cu = -(st.u * (o.vv_x @ st.u) + st.v * (o.vv_y @ st.u))
+        cv = -(st.u * (o.vv_x @ st.v) + st.v * (o.vv_y @ st.v))
+        cu_prev = cu if st.j == 0 else st.cu_prev
+        cv_prev = cv if st.j == 0 else st.cv_prev
+        us = st.u + dt * (1.5 * cu - 0.5 * cu_prev)
+        vs = st.v + dt * (1.5 * cv - 0.5 * cv_prev)
+        if self.cn_form == "printed":
+            ru = us + a * (o.vv_lap @ us)
+            rv = vs + a * (o.vv_lap @ vs)
+        else:
+            ru = us + a * (o.vv_lap @ st.u)
+            rv = vs + a * (o.vv_lap @ st.v)
+        kp = 0.0 if self.km_mode == 0 else 1.0
+        gpx = kp * (o.vp_x @ st.pt)
+        gpy = kp * (o.vp_y @ st.pt)
+        du, dv = self.bc_u == BC_DIRICHLET, self.bc_v == BC_DIRICHLET
+        if self.conv.any():  # outflow data from the convective condition
+            cvn = self.conv
+            gu = np.where(cvn, st.u - dt * self.u_conv * (self.VN @ st.u), gu)
+            gv = np.where(cvn, st.v - dt * self.u_conv * (self.VN @ st.v), gv)
+        ru[du] = gu[du] + dt * gpx[du]
+        rv[dv] = gv[dv] + dt * gpy[dv]
+        ru[self.bc_u == BC_NEUMANN] = 0.0
+        rv[self.bc_v == BC_NEUMANN] = 0.0
+        uss = self.Hu_lu.solve(ru)
+        vss = self.Hv_lu.solve(rv)
+        F = o.pv_x @ uss + o.pv_y @ vss
+        b = np.where(self.bc_p == BC_INTERIOR, F / dt, 0.0)
+        pt = self.L_lu.solve(b)
+        p = pt - a * (o.pp_lap @ pt)
+        un = uss - dt * (o.vp_x @ pt)
+        vn = vss - dt * (o.vp_y @ pt)
+        un[du] = gu[du]
+        vn[dv] = gv[dv]
+        return FlowState(u=un, v=vn, cu_prev=cu, cv_prev=cv, pt=pt, p=p, lam=0.0, j=st.j + 1)
+
+
+def simpson_periodic(f, period: float) -> float:
+    """Composite Simpson's rule for a periodic function sampled at an even
+    number n of equally spaced points f_0 .. f_{n-1} over one period (f_n =
+    f_0): h/3 (2 f_0 + 4 f_1 + 2 f_2 + ... + 4 f_{n-1})."""
+    f = np.asarray(f, np.float64)
+    n = f.size
+    if n < 2 or n % 2:
+        raise ValueError("Simpson's rule needs an even number of intervals")
+    w = np.where(np.arange(n) % 2 == 1, 4.0, 2.0)
+    return float((period / n) / 3.0 * (w @ f))
+
+
+def cylinder_forces(nodes, ops: Operators, u, v, p, Re: float):
+    """Drag and lift coefficients (Section 5.2): the force of the fluid on
+    the cylinder, F = integral over the surface of sigma n, with
+    sigma = -p I + (grad U + grad U^T) / Re and n the unit normal pointing
+    from the cylinder into the fluid, by Simpson's rule in the angle over the
+    cylinder's P-nodes (equally spaced in angle, an even count), with the
+    velocity gradient taken there by D^(P,V); C = F / (1/2 rho U^2 D) with
+    rho = U = 1 and D = 2 radius.  Returns (C_D, C_L)."""
+    from paper_2206_06495_gb300.nodesets import WALL_CYLINDER
+    cyl = np.nonzero(nodes.p_wall == WALL_CYLINDER)[0]
+    x, y = nodes.px[cyl], nodes.py[cyl]
+    th = np.mod(np.arctan2(y, x), 2.0 * np.pi)
+    order = np.argsort(th)
+    cyl, x, y, th = cyl[order], x[order], y[order], th[order]
+    radius = float(np.mean(np.hypot(x, y)))
+    nx, ny = np.cos(th), np.sin(th)
+    ux, uy = (ops.pv_x @ u)[cyl], (ops.pv_y @ u)[cyl]
+    vx, vy = (ops.pv_x @ v)[cyl], (ops.pv_y @ v)[cyl]
+    pc = np.asarray(p)[cyl]
+    tx = -pc * nx + (2.0 * ux * nx + (uy + vx) * ny) / Re
+    ty = -pc * ny + ((uy + vx) * nx + 2.0 * vy * ny) / Re
+    fx = simpson_periodic(tx * radius, 2.0 * np.pi)
+    fy = simpson_periodic(ty * radius, 2.0 * np.pi)
+    d = 2.0 * radius
+    return 2.0 * fx / d, 2.0 * fy / d
+
+
+def strouhal(t, cl, diameter: float = 1.0, u_inf: float = 1.0) -> float:
+    """St = f D / U of a lift signal: f from the mean spacing of the upward
+    zero crossings of cl - mean(cl), located by linear interpolation."""
+    t = np.asarray(t, np.float64)
+    c = np.asarray(cl, np.float64) - np.mean(cl)
+    up = np.nonzero((c[:-1] < 0.0) & (c[1:] >= 0.0))[0]
+    if up.size < 2:
+        raise ValueError("fewer than two upward zero crossings")
+    tc = t[up] - c[up] * (t[up + 1] - t[up]) / (c[up + 1] - c[up])
+    period = (tc[-1] - tc[0]) / (tc.size - 1)
+    return diameter / (period * u_inf)

@@ -27,6 +27,11 @@ WALL_RIGHT = 2
 WALL_TOP = 3  # the moving lid (Section 5.1)
 WALL_LEFT = 4
 WALL_CORNER = 5
+# Boundary tags of the open cylinder-wake domain (Section 5.2).
+WALL_INFLOW = 6    # x = x0: uniform inflow
+WALL_OUTFLOW = 7   # x = x1: stress-free outlet
+WALL_SIDE = 8      # y = y0 and y = y1: symmetry (slip) walls
+WALL_CYLINDER = 9  # the cylinder surface
 
 
 def morton_order(x: np.ndarray, y: np.ndarray, bits: int = 20) -> np.ndarray:
@@ -210,6 +215,234 @@ def jittered_cavity(n: int, seed: int = 0, jitter: float = 0.25,
                           edges=edges, h=h,
                           meta={"kind": "jittered_cavity", "n": n, "seed": seed,
                                 "jitter": jitter, "length": length})
+
+
+def wake_spacing(x, y, h_wall: float, h_wake: float, h_far: float, radius: float,
+                 growth: float):
+    """Target node spacing of the cylinder-wake layout: h_wall on the cylinder,
+    growing by `growth` per unit distance from it; h_wake on the wake
+    centreline (x > 0), growing by `growth` per unit |y| and by 3 % per unit x;
+    never above h_far."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    r = np.hypot(x, y)
+    h_c = h_wall + growth * np.maximum(r - radius, 0.0)
+    h_w = np.where(x > 0.0, h_wake * (1.0 + 0.03 * x) + growth * np.abs(y), np.inf)
+    return np.minimum(np.minimum(h_c, h_w), h_far)
+
+
+def _edge_nodes(a, b, hfun):
+    """Points from a to b (both included) spaced by the local target spacing,
+    stretched uniformly so that the last one lands on b."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    length = float(np.hypot(*(b - a)))
+    s = [0.0]
+    while s[-1] < length:
+        q = a + (b - a) * (s[-1] / length)
+        s.append(s[-1] + float(hfun(q[0:1], q[1:2])[0]))
+    s = np.array(s)
+    if s.size > 2 and s[-1] - length > 0.5 * (s[-1] - s[-2]):
+        s = s[:-1]  # the last step overshoots by more than half: drop it
+    t = s / s[-1]  # graded positions, stretched so the last lands on b
+    t[-1] = 1.0
+    return a[0] + (b[0] - a[0]) * t, a[1] + (b[1] - a[1]) * t
+
+
+def cylinder_wake(h_wall: float = 0.03, h_wake: float = 0.04, h_far: float = 0.5,
+                  x0: float = -8.0, x1: float = 24.0, y0: float = -8.0, y1: float = 8.0,
+                  radius: float = 0.5, growth: float = 0.12, seed: int = 3,
+                  jitter: float = 0.25) -> StaggeredNodes:
+    """Staggered nodes for flow past a cylinder (Section 5.2): the rectangle
+    [x0, x1] x [y0, y1] outside the circle of `radius` about the origin
+    (radius 0: no cylinder, a plain channel), graded by wake_spacing.
+
+    P-nodes: boundary nodes on the circle (an even count, uniform in angle,
+    the first at angle 0) and on the four sides (spaced by the local target
+    spacing, corners included once); interior nodes one per leaf of a
+    quadtree refined until each leaf is no larger than the target spacing at
+    its centre, placed at the leaf centre jittered by U(+-jitter * leaf
+    side), and dropped where they come closer than 0.6 of the local spacing
+    to a boundary.  The P-nodes are triangulated (Delaunay, with a ring of
+    ghost points outside the rectangle so that the sides stay straight;
+    triangles inside the cylinder, touching a ghost, or joining two
+    non-adjacent circle nodes are dropped).  V-nodes: the midpoints of the
+    triangle edges.  A node on x = x0 is an inflow node (corners too), on
+    x = x1 an outflow node (corners too), on y = y0 or y1 a side node, on the
+    circle a cylinder node; a V-node is a boundary node when both endpoints of
+    its edge lie on the same boundary.  Normals point out of the fluid (into
+    the cylinder on its surface)."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+
+    def hfun(x, y):
+        return wake_spacing(x, y, h_wall, h_wake, h_far, radius, growth)
+
+    # boundary P-nodes
+    bx, by, btag = [], [], []
+    nc = 0
+    if radius > 0.0:
+        nc = max(8, 4 * int(round(2.0 * np.pi * radius / h_wall / 4.0)))
+        th = 2.0 * np.pi * np.arange(nc) / nc
+        bx.append(radius * np.cos(th))
+        by.append(radius * np.sin(th))
+        btag.append(np.full(nc, WALL_CYLINDER, np.int8))
+    corners = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+    for c in range(4):
+        a, b = corners[c], corners[(c + 1) % 4]
+        ex, ey = _edge_nodes(a, b, hfun)
+        ex, ey = ex[:-1], ey[:-1]  # each corner once, as the start of its side
+        tag = np.full(ex.size, WALL_SIDE, np.int8)
+        tag[ex == x0] = WALL_INFLOW
+        tag[ex == x1] = WALL_OUTFLOW
+        bx.append(ex)
+        by.append(ey)
+        btag.append(tag)
+    bx = np.concatenate(bx)
+    by = np.concatenate(by)
+    btag = np.concatenate(btag)
+
+    # interior P-nodes: quadtree leaves no larger than the local spacing
+    n0x = int(np.ceil((x1 - x0) / h_far))
+    n0y = int(np.ceil((y1 - y0) / h_far))
+    sx0, sy0 = (x1 - x0) / n0x, (y1 - y0) / n0y
+    gx, gy = np.meshgrid(np.arange(n0x), np.arange(n0y), indexing="ij")
+    cx = x0 + (gx.ravel() + 0.5) * sx0
+    cy = y0 + (gy.ravel() + 0.5) * sy0
+    sx = np.full(cx.size, sx0)
+    sy = np.full(cy.size, sy0)
+    leaves_x, leaves_y, leaves_sx, leaves_sy = [], [], [], []
+    while cx.size:
+        split = np.maximum(sx, sy) > hfun(cx, cy)
+        leaves_x.append(cx[~split])
+        leaves_y.append(cy[~split])
+        leaves_sx.append(sx[~split])
+        leaves_sy.append(sy[~split])
+        cx, cy, sx, sy = cx[split], cy[split], sx[split] / 2, sy[split] / 2
+        cx = np.concatenate([cx - sx / 2, cx + sx / 2, cx - sx / 2, cx + sx / 2])
+        cy = np.concatenate([cy - sy / 2, cy - sy / 2, cy + sy / 2, cy + sy / 2])
+        sx = np.tile(sx, 4)
+        sy = np.tile(sy, 4)
+    lx = np.concatenate(leaves_x)
+    ly = np.concatenate(leaves_y)
+    lsx = np.concatenate(leaves_sx)
+    lsy = np.concatenate(leaves_sy)
+    ix = lx + rng.uniform(-jitter, jitter, lx.size) * lsx
+    iy = ly + rng.uniform(-jitter, jitter, ly.size) * lsy
+    hloc = hfun(ix, iy)
+    # the margin takes the larger of the node's own spacing and the boundary
+    # spacing at its projection, so no node enters the diametral circle of a
+    # boundary segment (which would cut that segment out of the mesh)
+    keep = (ix - x0 > 0.6 * np.maximum(hloc, hfun(np.full_like(iy, x0), iy))) & \
+        (x1 - ix > 0.6 * np.maximum(hloc, hfun(np.full_like(iy, x1), iy))) & \
+        (iy - y0 > 0.6 * np.maximum(hloc, hfun(ix, np.full_like(ix, y0)))) & \
+        (y1 - iy > 0.6 * np.maximum(hloc, hfun(ix, np.full_like(ix, y1))))
+    if radius > 0.0:
+        r_i = np.maximum(np.hypot(ix, iy), 1e-300)
+        h_proj = hfun(radius * ix / r_i, radius * iy / r_i)
+        keep &= r_i - radius > 0.6 * np.maximum(hloc, h_proj)
+    ix, iy = ix[keep], iy[keep]
+
+    x = np.concatenate([bx, ix])
+    y = np.concatenate([by, iy])
+    wall = np.concatenate([btag, np.zeros(ix.size, np.int8)])
+    nb = bx.size
+
+    # ghost ring outside the rectangle, then Delaunay
+    side = btag != WALL_CYLINDER
+    hb = hfun(bx[side], by[side])
+    gxs = np.clip(bx[side], x0, x1) + np.where(bx[side] == x0, -hb, np.where(bx[side] == x1, hb, 0))
+    gys = np.clip(by[side], y0, y1) + np.where(by[side] == y0, -hb, np.where(by[side] == y1, hb, 0))
+    ghost_x = np.concatenate([gxs, [x0 - h_far, x1 + h_far, x1 + h_far, x0 - h_far]])
+    ghost_y = np.concatenate([gys, [y0 - h_far, y0 - h_far, y1 + h_far, y1 + h_far]])
+    allx = np.concatenate([x, ghost_x])
+    ally = np.concatenate([y, ghost_y])
+    tri = Delaunay(np.stack([allx, ally], 1)).simplices
+    n_real = x.size
+    ok = (tri < n_real).all(1)
+    tri = tri[ok]
+    if radius > 0.0:
+        cxm = x[tri].mean(1)
+        cym = y[tri].mean(1)
+        ok = np.hypot(cxm, cym) >= radius
+        for e0, e1 in ((0, 1), (1, 2), (2, 0)):
+            a_, b_ = tri[:, e0], tri[:, e1]
+            both = (a_ < nc) & (b_ < nc)
+            gap = np.abs(a_ - b_)
+            ok &= ~(both & (gap != 1) & (gap != nc - 1))
+        tri = tri[ok]
+    used = np.zeros(n_real, bool)
+    used[tri.ravel()] = True
+    if not used[:nb].all():
+        raise ValueError("a boundary node was left out of the triangulation")
+    remap = -np.ones(n_real, np.int64)
+    remap[used] = np.arange(used.sum())
+    x, y, wall = x[used], y[used], wall[used]
+    tri = remap[tri]
+    edges = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]], 0)
+    edges.sort(axis=1)
+    edges = np.unique(edges, axis=0)
+
+    nx = np.zeros(x.size)
+    ny = np.zeros(x.size)
+    nx[wall == WALL_INFLOW] = -1.0
+    nx[wall == WALL_OUTFLOW] = 1.0
+    sd = wall == WALL_SIDE
+    ny[sd] = np.where(y[sd] == y0, -1.0, 1.0)
+    cyl = wall == WALL_CYLINDER
+    if radius > 0.0:
+        nx[cyl] = -x[cyl] / radius
+        ny[cyl] = -y[cyl] / radius
+
+    perm = morton_order(x, y)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    x, y, wall, nx, ny = x[perm], y[perm], wall[perm], nx[perm], ny[perm]
+    edges = inv[edges]
+    edges.sort(axis=1)
+
+    a, b = edges[:, 0], edges[:, 1]
+    vx = 0.5 * (x[a] + x[b])
+    vy = 0.5 * (y[a] + y[b])
+    wa, wb = wall[a], wall[b]
+    v_wall = np.zeros(edges.shape[0], np.int8)
+    on_in = (x[a] == x0) & (x[b] == x0)
+    on_out = (x[a] == x1) & (x[b] == x1)
+    on_side = ((y[a] == y0) & (y[b] == y0)) | ((y[a] == y1) & (y[b] == y1))
+    on_cyl = (wa == WALL_CYLINDER) & (wb == WALL_CYLINDER)
+    v_wall[on_side] = WALL_SIDE
+    v_wall[on_in] = WALL_INFLOW
+    v_wall[on_out] = WALL_OUTFLOW
+    v_wall[on_cyl] = WALL_CYLINDER
+    v_nx = np.zeros(edges.shape[0])
+    v_ny = np.zeros(edges.shape[0])
+    v_nx[on_in] = -1.0
+    v_nx[on_out] = 1.0
+    v_ny[on_side] = np.where(vy[on_side] == y0, -1.0, 1.0)
+    if radius > 0.0:
+        rv = np.hypot(vx[on_cyl], vy[on_cyl])
+        v_nx[on_cyl] = -vx[on_cyl] / rv
+        v_ny[on_cyl] = -vy[on_cyl] / rv
+
+    # every boundary segment is an edge: a closed boundary of k nodes has k
+    # segments, each open side of k nodes k - 1
+    n_bseg = int((v_wall != WALL_NONE).sum())
+    n_side = [int(((x == x0)).sum()), int(((x == x1)).sum()), int(((y == y0)).sum()),
+              int(((y == y1)).sum())]
+    if n_bseg != sum(n_side) - 4 + nc:
+        raise ValueError("a boundary segment is missing from the triangulation")
+
+    vperm = morton_order(vx, vy)
+    vx, vy, v_wall, edges = vx[vperm], vy[vperm], v_wall[vperm], edges[vperm]
+    v_nx, v_ny = v_nx[vperm], v_ny[vperm]
+    return StaggeredNodes(px=x, py=y, p_wall=wall, p_nx=nx, p_ny=ny,
+                          vx=vx, vy=vy, v_wall=v_wall, v_nx=v_nx, v_ny=v_ny,
+                          edges=edges, h=h_wall,
+                          meta={"kind": "cylinder_wake", "radius": radius,
+                                "domain": (x0, x1, y0, y1), "h_wall": h_wall,
+                                "h_wake": h_wake, "h_far": h_far, "growth": growth,
+                                "seed": seed, "n_cylinder": nc})
 
 
 def poisson_disk(count: int, seed: int = 1, rounds: int = 24) -> tuple[np.ndarray, np.ndarray]:
