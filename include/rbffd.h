@@ -66,6 +66,11 @@ extern "C" {
 #define RBFFD_CN_PRINTED 0  /* Eq. u_ss: (I + a D_Lap) u*                    */
 #define RBFFD_CN_KIM_MOIN 1 /* Kim & Moin: u* + a D_Lap u_j                   */
 
+/* Boundary conditions of open flows (rbffd_flow.v_bcu, v_bcv, p_bc). */
+#define RBFFD_BC_DIRICHLET 1 /* velocity: the wall data (Kim & Moin value for u**) */
+#define RBFFD_BC_NEUMANN 2   /* velocity: n.grad = 0 on a one-sided stencil         */
+#define RBFFD_PBC_DIRICHLET 2 /* p_bc value of a Dirichlet pressure row (p~ = 0)    */
+
 typedef struct rbffd_ctx rbffd_ctx;
 
 /* Stencil parameters (n, m, q) of Section 4; the paper selects (28, 7, 3). */
@@ -256,6 +261,29 @@ int rbffd_apply_op_shape(rbffd_ctx* ctx, const rbffd_ell* D, int32_t xy_dtype, i
  * cn_form         RBFFD_CN_PRINTED (Eq. u_ss, the default) or RBFFD_CN_KIM_MOIN
  *                 (right side u* + a D^(V,V)_Lap u_j, Kim & Moin's
  *                 Crank-Nicolson form; the printed one adds an O(dt) term)
+ *
+ * Open flows (Section 5.2, flow past a cylinder).  With v_bcu and v_bcv null
+ * every boundary V-node (v_bc != 0) is a Dirichlet node for both components
+ * and every boundary P-node a Neumann node, as in the cavity.  Otherwise:
+ * v_bcu, v_bcv    uint8 [N]: per V-node and component 0 (interior; exactly
+ *                 where v_bc is 0), RBFFD_BC_DIRICHLET (row u** = g_{j+1} +
+ *                 dt D^(V,P) p~_j per km_mode 2/0, overwritten by g_{j+1} after
+ *                 the correction) or RBFFD_BC_NEUMANN (row n.grad u** = 0,
+ *                 corrected like an interior node)
+ * nb_v, ld_vb     number of Neumann V-rows and their leading dimension
+ *                 (a multiple of 32, >= nb_v)
+ * vn_rows         int32 [nb_v]: the V-nodes with a Neumann row (every V-node
+ *                 with a Neumann component, each once)
+ * vn_idx          int32 [n][ld_vb]: their one-sided stencils, the node itself in
+ *                 slot 0, then n-1 interior V-nodes (rbffd_build_weights_masked)
+ * vn_dx, vn_dy    float64 [n][ld_vb]: D_x, D_y weights of those stencils; the row
+ *                 is v_nx D_x + v_ny D_y
+ * p_bc            RBFFD_PBC_DIRICHLET marks a Dirichlet pressure row (p~ = 0);
+ *                 with any such row the pressure system is nonsingular: no
+ *                 bordering, and p~ is not shifted to mean zero.  Such nodes
+ *                 need no Neumann row in pn_rows.
+ * Open flows run the paper's projection (projection = RBFFD_PROJ_PAPER) with
+ * km_mode 0 or 2; rbffd_adjoint_step and rbffd_ensemble_step refuse them.
  */
 typedef struct rbffd_flow {
   int64_t N, M, ld_v, ld_p;
@@ -288,6 +316,11 @@ typedef struct rbffd_flow {
   const double *p_x, *p_y;
   int32_t projection;
   int32_t cn_form;
+  const uint8_t *v_bcu, *v_bcv;
+  int64_t nb_v, ld_vb;
+  const int32_t* vn_rows;
+  const int32_t* vn_idx;
+  const double *vn_dx, *vn_dy;
 } rbffd_flow;
 
 /* Solver state at step j (all FP64 device arrays owned by the caller). */
@@ -473,6 +506,28 @@ typedef struct rbffd_adjoint {
 int rbffd_adjoint_step(rbffd_ctx* ctx, const rbffd_flow* flow, const rbffd_state* fwd,
                        rbffd_adjoint* lam, double* grad_gu, double* grad_gv, rbffd_stats* stats,
                        cudaStream_t stream);
+
+/*
+ * rbffd_cylinder_forces - drag and lift coefficients of a circular body
+ * (Section 5.2): C = F / (1/2 rho U^2 D) with rho = U = 1 and D = 2 radius,
+ * F the force of the fluid on the body, the integral over its surface of
+ * (-p I + (grad U + grad U^T) / Re) n with n the unit normal from the body
+ * into the fluid, by composite Simpson's rule in the angle.
+ *   flow    the flow description (its D^(P,V) operators and P-node
+ *           coordinates p_x, p_y are used; p_x, p_y must be set)
+ *   u, v    velocity at the V-nodes, float64 [N], device
+ *   p       pressure at the P-nodes, float64 [M], device
+ *   rows    int32 [n_c], device: the body's surface P-nodes, equally spaced in
+ *           angle about (cx, cy), in increasing angle; n_c even, at least 4
+ *   radius  the body's radius; Re the Reynolds number of the viscous stress
+ *   cd_cl   double[2], HOST: C_D (along +x) and C_L (along +y)
+ * Synchronous.  Errors: INVALID_ARG (null pointers, odd or small n_c, a row
+ * outside [0, M), missing coordinates), CUDA.
+ */
+int rbffd_cylinder_forces(rbffd_ctx* ctx, const rbffd_flow* flow, const double* u,
+                          const double* v, const double* p, const int32_t* rows, int32_t n_c,
+                          double cx, double cy, double radius, double Re, double* cd_cl,
+                          cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -806,8 +806,8 @@ class OpenFlowStep:
     def __init__(self, nodes, Re: float, dt: float, bc_u, bc_v, bc_p, k: int = 28,
                  m: int = 7, q: int = 3, ops: Operators | None = None, km_mode: int = 2,
                  cn_form: str = "printed", convective=None, u_conv: float = 1.0):
-        if km_mode not in (0, 2):
-            raise ValueError("km_mode is 0 or 2 for open flows")
+        if km_mode not in (0, 1, 2):
+            raise ValueError("km_mode is 0, 1 or 2")
         if cn_form not in ("printed", "kim_moin"):
             raise ValueError("cn_form is 'printed' or 'kim_moin'")
         self.nodes = nodes
@@ -879,6 +879,10 @@ class OpenFlowStep:
         kp = 0.0 if self.km_mode == 0 else 1.0
         gpx = kp * (o.vp_x @ st.pt)
         gpy = kp * (o.vp_y @ st.pt)
+        if self.km_mode == 1:  # the component along the wall tangent only (R5)
+            tx, ty = -self.nodes.v_ny, self.nodes.v_nx
+            gt = tx * gpx + ty * gpy
+            gpx, gpy = gt * tx, gt * ty
         du, dv = self.bc_u == BC_DIRICHLET, self.bc_v == BC_DIRICHLET
         if self.conv.any():  # outflow data from the convective condition
             cvn = self.conv

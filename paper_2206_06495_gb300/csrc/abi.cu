@@ -216,6 +216,18 @@ static int check_flow(rbffd_ctx* ctx, const rbffd_flow* flow) {
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "projection and cn_form must be 0 or 1");
   if (f.precond && (!f.p_edges || f.n_edges < 1 || f.n_edges > INT32_MAX || !f.p_x || !f.p_y))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "precond = 1 needs p_edges, n_edges, p_x, p_y");
+  // open flows: per-component velocity conditions with their Neumann rows
+  if ((f.v_bcu == nullptr) != (f.v_bcv == nullptr))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "v_bcu and v_bcv are both set or both null");
+  if (f.v_bcu) {
+    if (f.nb_v < 0 || f.nb_v > f.N ||
+        (f.nb_v > 0 && (f.ld_vb < f.nb_v || f.ld_vb % 32 || !f.vn_rows || !f.vn_idx ||
+                        !f.vn_dx || !f.vn_dy)))
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "bad Neumann V-rows (nb_v, ld_vb, vn_*)");
+    if (f.projection != RBFFD_PROJ_PAPER || (f.km_mode != 0 && f.km_mode != 2))
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                       "open flows run the paper's projection with km_mode 0 or 2");
+  }
   return RBFFD_OK;
 }
 
@@ -253,6 +265,8 @@ int rbffd_ensemble_step(rbffd_ctx* ctx, const rbffd_flow* flow, int32_t n_member
   if (rc) return rc;
   if (flow->projection != RBFFD_PROJ_PAPER)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "ensembles run the paper's projection only");
+  if (flow->v_bcu)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "ensembles run the cavity's walls only");
   if (!state->u || !state->v || !state->cu_prev || !state->cv_prev || !state->pt || !state->p)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null state array");
   if (n_steps == 0) return RBFFD_OK;
@@ -340,7 +354,35 @@ int rbffd_adjoint_step(rbffd_ctx* ctx, const rbffd_flow* flow, const rbffd_state
   if (flow->projection != RBFFD_PROJ_PAPER || flow->cn_form != RBFFD_CN_PRINTED)
     return set_error(ctx, RBFFD_ERR_INVALID_ARG,
                      "the adjoint exists for the paper's step only (projection 0, cn_form 0)");
+  if (flow->v_bcu)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "the adjoint exists for the cavity's walls only");
   return adjoint_run(ctx, flow, fwd, lam, grad_gu, grad_gv, stats, stream);
 }
 
 }  // extern "C"
+
+extern "C" int rbffd_cylinder_forces(rbffd_ctx* ctx, const rbffd_flow* flow, const double* u,
+                                     const double* v, const double* p, const int32_t* rows,
+                                     int32_t n_c, double cx, double cy, double radius, double Re,
+                                     double* cd_cl, cudaStream_t stream) {
+  if (!ctx) return RBFFD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!flow || !u || !v || !p || !rows || !cd_cl)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "null pointer");
+  int rc = check_flow(ctx, flow);
+  if (rc) return rc;
+  if (!flow->p_x || !flow->p_y)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG, "forces need the P-node coordinates p_x, p_y");
+  if (n_c < 4 || n_c % 2 || !(radius > 0.0) || !(Re > 0.0))
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                     "n_c must be even and at least 4, radius and Re positive");
+  std::vector<int32_t> h(n_c);
+  rc = check_cuda(ctx, cudaMemcpyAsync(h.data(), rows, sizeof(int32_t) * n_c,
+                                       cudaMemcpyDeviceToHost, stream), "rows copy");
+  if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(stream), "rows sync");
+  if (rc) return rc;
+  for (int32_t q = 0; q < n_c; ++q)
+    if (h[q] < 0 || h[q] >= flow->M)
+      return set_error(ctx, RBFFD_ERR_INVALID_ARG, "surface row %d out of range", q);
+  return analysis_forces(ctx, *flow, u, v, p, rows, n_c, cx, cy, radius, Re, cd_cl, stream);
+}

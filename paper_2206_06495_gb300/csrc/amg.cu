@@ -27,16 +27,30 @@ struct HostCsr {
 std::string edge_graph(int64_t M, int64_t ne, const std::vector<int32_t>& e,
                        const std::vector<double>& x, const std::vector<double>& y,
                        const std::vector<uint8_t>& bc, HostCsr* G) {
+  // A Dirichlet P-node (bc == RBFFD_PBC_DIRICHLET, open flows) is eliminated:
+  // its edges add their weight to the diagonals of both ends but enter no
+  // row as off-diagonal entries, so its own row is diagonal only and its
+  // neighbours' rows are strictly diagonally dominant (the graph matrix is
+  // then nonsingular, like the pressure system with Dirichlet rows).
+  auto dir = [&](int32_t i) { return bc[i] == RBFFD_PBC_DIRICHLET; };
   std::vector<uint8_t> inner(ne), has_in(M, 0);
+  std::vector<double> dsum(M, 0.0);
   for (int64_t k = 0; k < ne; ++k) {
     const int32_t a = e[2 * k], b = e[2 * k + 1];
     if (a < 0 || a >= M || b < 0 || b >= M) return "an edge end is not a P-node";
     if (a == b) return "an edge joins a P-node to itself";
     inner[k] = !(bc[a] && bc[b]);
     if (inner[k]) has_in[a] = has_in[b] = 1;
+    if (dir(a) || dir(b)) {
+      const double dx = x[a] - x[b], dy = y[a] - y[b], d2 = dx * dx + dy * dy;
+      if (!(d2 > 0.0)) return "an edge has coincident endpoints";
+      dsum[a] += 1.0 / d2;
+      dsum[b] += 1.0 / d2;
+    }
   }
   std::vector<int64_t> cnt(M + 1, 0);
   auto kept = [&](int64_t k) {
+    if (dir(e[2 * k]) || dir(e[2 * k + 1])) return false;
     return inner[k] || !has_in[e[2 * k]] || !has_in[e[2 * k + 1]];
   };
   for (int64_t k = 0; k < ne; ++k)
@@ -70,8 +84,8 @@ std::string edge_graph(int64_t M, int64_t ne, const std::vector<int32_t>& e,
     for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) row.emplace_back(col[p], w[p]);
     std::sort(row.begin(), row.end(),
               [](const auto& u, const auto& v) { return u.first < v.first; });
-    if (row.empty()) return "a P-node has no edge";
-    double s = 0.0;
+    if (row.empty() && !(dsum[i] > 0.0)) return "a P-node has no edge";
+    double s = dsum[i];
     for (size_t q = 0; q < row.size(); ++q) {
       if (q > 0 && row[q].first == row[q - 1].first) {
         G->val.back() -= row[q].second;
@@ -196,13 +210,16 @@ void permute(const HostCsr& A, const std::vector<int32_t>& old, const std::vecto
 // Dense inverse of (A + sigma 1 1^T + eps diag(A)) by Cholesky, row-major.
 // sigma lifts the constant null vector of the Laplacian to the mean diagonal;
 // eps = 1e-10 keeps the factorisation defined if the graph falls apart.
-bool coarse_inverse(const HostCsr& A, std::vector<double>* X) {
+bool coarse_inverse(const HostCsr& A, std::vector<double>* X, bool singular) {
   const int64_t n = A.n;
   std::vector<double> B(n * n, 0.0);
   double dm = 0.0;
   for (int64_t i = 0; i < n; ++i) dm += A.diag[i];
   dm /= (double)n;
-  const double sigma = dm / (double)n;
+  // a graph Laplacian with zero row sums is singular on the constants: the
+  // shift sigma 1 1^T makes it definite; with eliminated Dirichlet nodes it
+  // is definite already
+  const double sigma = singular ? dm / (double)n : 0.0;
   for (int64_t i = 0; i < n; ++i) {
     for (int64_t j = 0; j < n; ++j) B[i * n + j] = sigma;
     B[i * n + i] += A.diag[i] * (1.0 + 1e-10);
@@ -361,8 +378,10 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
     return set_error(ctx, RBFFD_ERR_INVALID_ARG,
                      "pressure graph does not coarsen below %lld nodes (disconnected?)",
                      (long long)L.back().n);
+  bool pdir = false;
+  for (int64_t i = 0; i < M; ++i) pdir = pdir || bc[i] == RBFFD_PBC_DIRICHLET;
   std::vector<double> Xd;
-  if (!coarse_inverse(L.back(), &Xd))
+  if (!coarse_inverse(L.back(), &Xd, !pdir))
     return set_error(ctx, RBFFD_ERR_INVALID_ARG, "coarsest pressure graph matrix is not positive");
 
   // Nested ordering, coarsest to finest: the coarsest level keeps its order,
@@ -465,10 +484,16 @@ int amg_build(rbffd_ctx* ctx, const rbffd_flow& f, const double* diag_a, const d
     ces += (diag_a[i] != 0.0 ? L[0].diag[p] / diag_a[i] : L[0].diag[p]) * es[i];
   }
   if ((rc = upload(ctx, a, oldi[0], &a->perm0, st))) return fail(rc);
-  if (!(ces != 0.0) || !std::isfinite(ces)) return fail(set_error(ctx, RBFFD_ERR_INVALID_ARG,
-                                                                  "pressure rank-one column is zero"));
-  a->inv_ces = 1.0 / ces;
-  a->inv_R = 1.0 / (double)M;
+  if (pdir) {
+    // nonsingular system: no rank-one completion (mu = 0, kap = 0)
+    a->inv_ces = 0.0;
+    a->inv_R = 0.0;
+  } else {
+    if (!(ces != 0.0) || !std::isfinite(ces))
+      return fail(set_error(ctx, RBFFD_ERR_INVALID_ARG, "pressure rank-one column is zero"));
+    a->inv_ces = 1.0 / ces;
+    a->inv_R = 1.0 / (double)M;
+  }
   if ((rc = upload(ctx, a, hc, &a->c, st)) || (rc = upload(ctx, a, hcn, &a->cnode, st)) ||
       (rc = upload(ctx, a, hce, &a->ce, st)) ||
       (rc = aalloc(ctx, a, &a->zp, M)) || (rc = aalloc(ctx, a, &a->zs, M)) ||

@@ -120,7 +120,76 @@ __global__ void __launch_bounds__(kAThreads)
   grid_reduce<1>(part, gr, sh, [&](double* t) { *mean = t[0] / (double)n; });
 }
 
+// Force of the fluid on a circular body (Section 5.2): the traction
+// (-p I + (grad U + grad U^T) / Re) n at each of the n_c surface P-nodes
+// (rows, in increasing angle; n from the centre through the node, i.e. from
+// the body into the fluid), the velocity gradient from the D^(P,V) rows,
+// integrated in angle by composite Simpson's rule (weights 2, 4, 2, 4, ... of
+// h/3 on the periodic grid) times the radius.  One block; the sums run in a
+// fixed order.  out[0], out[1]: C_D, C_L = F / (1/2 D) (rho = U = 1).
+constexpr int kFThreads = 256;
+__global__ void __launch_bounds__(kFThreads)
+    k_cylinder_forces(int n_c, const int32_t* __restrict__ rows, int64_t ld, int k,
+                      const int32_t* __restrict__ idx, const double* __restrict__ wdx,
+                      const double* __restrict__ wdy, const double* __restrict__ u,
+                      const double* __restrict__ v, const double* __restrict__ p,
+                      const double* __restrict__ px, const double* __restrict__ py, double cx,
+                      double cy, double radius, double inv_re, double* __restrict__ out) {
+  __shared__ double sx[kFThreads], sy[kFThreads];
+  double fx = 0.0, fy = 0.0;
+  for (int q = threadIdx.x; q < n_c; q += kFThreads) {
+    const int64_t i = rows[q];
+    double ux = 0.0, uy = 0.0, vx = 0.0, vy = 0.0;
+    for (int s = 0; s < k; ++s) {
+      const int32_t j = idx[s * ld + i];
+      const double ax = wdx[s * ld + i], ay = wdy[s * ld + i];
+      ux += ax * u[j];
+      uy += ay * u[j];
+      vx += ax * v[j];
+      vy += ay * v[j];
+    }
+    const double ex = px[i] - cx, ey = py[i] - cy, r = sqrt(ex * ex + ey * ey);
+    const double nx = ex / r, ny = ey / r;
+    const double tx = -p[i] * nx + (2.0 * ux * nx + (uy + vx) * ny) * inv_re;
+    const double ty = -p[i] * ny + ((uy + vx) * nx + 2.0 * vy * ny) * inv_re;
+    const double w = (q % 2) ? 4.0 : 2.0;
+    fx += w * tx;
+    fy += w * ty;
+  }
+  sx[threadIdx.x] = fx;
+  sy[threadIdx.x] = fy;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ax = 0.0, ay = 0.0;
+    for (int t = 0; t < kFThreads; ++t) {
+      ax += sx[t];
+      ay += sy[t];
+    }
+    const double h = 2.0 * 3.14159265358979323846 / (double)n_c;
+    const double scale = h / 3.0 * radius * 2.0 / (2.0 * radius);  // Simpson, ds, 1/(D/2)
+    out[0] = ax * scale;
+    out[1] = ay * scale;
+  }
+}
+
 }  // namespace
+
+int analysis_forces(rbffd_ctx* ctx, const rbffd_flow& f, const double* u, const double* v,
+                    const double* p, const int32_t* rows, int32_t n_c, double cx, double cy,
+                    double radius, double Re, double* out_host, cudaStream_t st) {
+  void* base = nullptr;
+  int rc = ctx_scratch(ctx, 2 * sizeof(double), &base);
+  if (rc) return rc;
+  k_cylinder_forces<<<1, kFThreads, 0, st>>>(n_c, rows, f.ld_p, ctx->prm.n, f.pv_idx, f.pv_dx,
+                                             f.pv_dy, u, v, p, f.p_x, f.p_y, cx, cy, radius,
+                                             1.0 / Re, (double*)base);
+  rc = check_cuda(ctx, cudaGetLastError(), "forces kernel");
+  if (rc) return rc;
+  rc = check_cuda(ctx, cudaMemcpyAsync(out_host, base, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                       st), "forces copy");
+  if (rc) return rc;
+  return check_cuda(ctx, cudaStreamSynchronize(st), "forces sync");
+}
 
 int analysis_mw(rbffd_ctx* ctx, const rbffd_ell* Dx, const rbffd_ell* Dy, const rbffd_ell* Dl,
                 const double* ax, const double* ay, const double* bx, const double* by,

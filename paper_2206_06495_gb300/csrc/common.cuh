@@ -146,6 +146,9 @@ int cond_build(rbffd_ctx* ctx, const double* ax, const double* ay, int64_t na, c
 int analysis_mw(rbffd_ctx* ctx, const rbffd_ell* Dx, const rbffd_ell* Dy, const rbffd_ell* Dl,
                 const double* ax, const double* ay, const double* bx, const double* by,
                 double kx, double ky, double* k1, double* k2, cudaStream_t st);
+int analysis_forces(rbffd_ctx* ctx, const rbffd_flow& f, const double* u, const double* v,
+                    const double* p, const int32_t* rows, int32_t n_c, double cx, double cy,
+                    double radius, double Re, double* out_host, cudaStream_t st);
 int analysis_error(rbffd_ctx* ctx, const rbffd_ell* D, int op, const double* ax,
                    const double* ay, const double* bx, const double* by, const double* dr,
                    double* err, double* mean, cudaStream_t st);

@@ -1320,6 +1320,7 @@ struct HelmRhsArgs {
   const float2 *u2, *v2;
   int cn;    // RBFFD_CN_*
   int proj;  // RBFFD_PROJ_*
+  const uint8_t *bcu, *bcv;  // open flows: per-component conditions (null: v_bc for both)
 };
 
 // Stage 2 right side: u* + a D_Lap (u* or u_j) inside, minus dt G0 p~_j for
@@ -1346,6 +1347,12 @@ __global__ void __launch_bounds__(kThreads) k_helm_rhs(HelmRhsArgs a) {
         bu -= a.dt * g[0];
         bv -= a.dt * g[1];
       }
+    } else if (a.bcu) {  // open flow: Dirichlet rows take the data, Neumann rows 0
+      const bool du = a.bcu[i] == RBFFD_BC_DIRICHLET, dv = a.bcv[i] == RBFFD_BC_DIRICHLET;
+      double g[2] = {0.0, 0.0};
+      if (a.km && (du || dv)) Gather<K, MIX, 2>::run(a.vp_idx, wg, a.ld_v, a.k, i, a.pt, a.pt2, g);
+      bu = du ? a.gu[i] + a.dt * g[0] : 0.0;
+      bv = dv ? a.gv[i] + a.dt * g[1] : 0.0;
     } else {
       bu = a.gu[i];
       bv = a.gv[i];
@@ -1411,6 +1418,7 @@ struct PresArgs {
   double *pt, *p;
   float2* pt2;
   int proj;
+  int nomean;  // Dirichlet pressure rows: p~ = x, no shift to mean zero
 };
 
 // Stage 3c: p~ = x - mean(x); p = p~ - a D^(P,P)_Lap p~.  Exact projection:
@@ -1419,7 +1427,7 @@ struct PresArgs {
 template <int K, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_pressure(PresArgs a) {
   const void* wl[1] = {a.lap};
-  const double mean = *a.sum / (double)a.n;
+  const double mean = a.nomean ? 0.0 : *a.sum / (double)a.n;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * kThreads) {
     double l;
@@ -1449,6 +1457,7 @@ struct CorrArgs {
   // c = -dt (sum x) / esn (the multiplier of the wall-flux column)
   int proj;
   const double *sum, *esn, *v_nx, *v_ny;
+  const uint8_t *bcu, *bcv;  // open flows: only Dirichlet components are overwritten
 };
 
 // Stage 3d: u_{j+1} = u** - dt D^(V,P)_x p~ (Eq. velocity_next_timestep).
@@ -1470,8 +1479,8 @@ __global__ void __launch_bounds__(kThreads) k_correct(CorrArgs a) {
       vn = a.vss[i] - a.dt * g[1];
     }
     if (a.overwrite && !a.proj && a.v_bc[i]) {
-      un = a.gu[i];
-      vn = a.gv[i];
+      if (!a.bcu || a.bcu[i] == RBFFD_BC_DIRICHLET) un = a.gu[i];
+      if (!a.bcv || a.bcv[i] == RBFFD_BC_DIRICHLET) vn = a.gv[i];
     }
     a.u[i] = un;
     a.v[i] = vn;
@@ -1509,9 +1518,18 @@ __global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __r
                                 const double* __restrict__ nx, const double* __restrict__ ny,
                                 int32_t* __restrict__ Lidx, double* __restrict__ Lw,
                                 double* __restrict__ es, double* __restrict__ scale,
-                                int* __restrict__ err) {
+                                int* __restrict__ err, int pdir) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (p_bc[i] == RBFFD_PBC_DIRICHLET) {  // p~ = 0: identity row, no rank-one entry
+      for (int s = 0; s < k; ++s) {
+        Lidx[s * ld + i] = (int32_t)i;
+        Lw[s * ld + i] = s == 0 ? 1.0 : 0.0;
+      }
+      es[i] = 0.0;
+      scale[i] = 1.0;
+      continue;
+    }
     const bool bnd = p_bc[i] != 0;
     const int32_t b = bnd ? bmap[i] : -1;
     if (bnd && b < 0) {  // a boundary node without a Neumann row
@@ -1542,7 +1560,7 @@ __global__ void k_build_poisson(int64_t M, int64_t ld, int k, const int32_t* __r
     }
     const double sc = diag != 0.0 ? 1.0 / diag : (sabs > 0.0 ? 1.0 / sabs : 1.0);
     for (int s = 0; s < k; ++s) Lw[s * ld + i] *= sc;
-    es[i] = bnd ? -sc : 0.0;
+    es[i] = (bnd && !pdir) ? -sc : 0.0;  // with Dirichlet rows the system is nonsingular
     scale[i] = sc;
   }
 }
@@ -1636,6 +1654,59 @@ __global__ void k_build_helm(int64_t N, int64_t ld, int k, const double* __restr
   }
 }
 
+// Open flows (per-component conditions): the shared index array of the two
+// viscous operators (the one-sided stencil of a Neumann V-row, the V->V
+// stencil elsewhere) and, per component, Hw with x + Hw x = row i of H:
+// interior -a D_Lap; Dirichlet 0 (identity row); Neumann N_i / N_ii - e_i,
+// with N = v_nx D_x + v_ny D_y (the normalised Neumann row: its diagonal is
+// the stencil's first slot, the node itself).
+__global__ void k_build_hidx(int64_t N, int64_t ld, int k, const int32_t* __restrict__ vv_idx,
+                             const int32_t* __restrict__ vmap, int64_t ld_b,
+                             const int32_t* __restrict__ vn_idx, int32_t* __restrict__ Hidx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = vmap[i];
+    for (int s = 0; s < k; ++s) Hidx[s * ld + i] = b >= 0 ? vn_idx[s * ld_b + b] : vv_idx[s * ld + i];
+  }
+}
+
+__global__ void k_build_helm_open(int64_t N, int64_t ld, int k, const double* __restrict__ lap,
+                                  const uint8_t* __restrict__ bc, const int32_t* __restrict__ vmap,
+                                  int64_t ld_b, const double* __restrict__ vn_dx,
+                                  const double* __restrict__ vn_dy, const double* __restrict__ nx,
+                                  const double* __restrict__ ny, double a,
+                                  double* __restrict__ Hw, int* __restrict__ err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (bc[i] == RBFFD_BC_NEUMANN) {
+      const int32_t b = vmap[i];
+      if (b < 0) {  // a Neumann node without a Neumann row
+        atomicOr(err, 16);
+        for (int s = 0; s < k; ++s) Hw[s * ld + i] = 0.0;
+        continue;
+      }
+      const double d = nx[i] * vn_dx[b] + ny[i] * vn_dy[b];  // slot 0: the node itself
+      const double inv = d != 0.0 ? 1.0 / d : 0.0;
+      if (!(d != 0.0)) atomicOr(err, 32);
+      for (int s = 0; s < k; ++s) {
+        const double w = nx[i] * vn_dx[s * ld_b + b] + ny[i] * vn_dy[s * ld_b + b];
+        Hw[s * ld + i] = w * inv - (s == 0 ? 1.0 : 0.0);
+      }
+    } else {
+      const double ai = bc[i] == RBFFD_BC_DIRICHLET ? 0.0 : a;
+      for (int s = 0; s < k; ++s) Hw[s * ld + i] = -ai * lap[s * ld + i];
+    }
+  }
+}
+
+__global__ void k_count_eq(int64_t n, const uint8_t* __restrict__ x, uint8_t v, int* __restrict__ cnt) {
+  int c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += x[i] == v;
+  if (c) atomicAdd(cnt, c);
+}
+
 __global__ void k_scale_by_inv_abs(int64_t n, double* __restrict__ x, const double* sum) {
   const double s = *sum != 0.0 ? 1.0 / fabs(*sum) : 1.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1726,6 +1797,15 @@ struct StepPlan {
   // apply (FP32 weights in MIXED precision, FP64 otherwise)
   unsigned char* Lt = nullptr;
   unsigned char* Ht = nullptr;
+  // open flows (per-component velocity conditions): the viscous operators'
+  // shared index array and v's own operator (Hw, Hw32, Ht serve u); pdir:
+  // the pressure system has Dirichlet rows (nonsingular, no mean removal)
+  bool open = false;
+  int pdir = 0;
+  int32_t* Hidx = nullptr;
+  double* Hw_v = nullptr;
+  float* Hw32_v = nullptr;
+  unsigned char* Ht_v = nullptr;
   // CUDA graphs of Krylov iteration chunks: one per solve (its operator,
   // vectors and preconditioner) and chunk length, captured on first use on a
   // private stream and replayed on the caller's stream
@@ -1802,6 +1882,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   p->mix = f.precision == RBFFD_PREC_MIXED;
   p->grid = sm_count() * 8;  // 8 blocks of 256 per SM: full occupancy at 32 registers
   p->proj = f.projection;
+  p->open = f.v_bcu != nullptr;
   p->kL = p->k;
   const int64_t nv = f.ld_v * p->k;
   const int64_t nmax = f.N > f.M ? f.N : f.M;
@@ -1868,17 +1949,43 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
                                         f.vp_idx, f.vp_dx, f.vp_dy, f.v_bc, f.v_nx, f.v_ny,
                                         p->kL, nullptr, p->Lidx, p->Lw, p->es, p->scale, p->err);
   } else {
+    // Dirichlet pressure rows (open flows): counted first, since any one of
+    // them removes the rank-one column from every row
+    int* dcnt = nullptr;
+    TRY(palloc(ctx, p, &dcnt, 1));
+    TRY(check_cuda(ctx, cudaMemsetAsync(dcnt, 0, sizeof(int), st), "memset"));
+    k_count_eq<<<p->grid, kThreads, 0, st>>>(f.M, f.p_bc, (uint8_t)RBFFD_PBC_DIRICHLET, dcnt);
+    TRY(check_cuda(ctx, cudaMemcpyAsync(&p->pdir, dcnt, sizeof(int), cudaMemcpyDeviceToHost, st),
+                   "Dirichlet rows"));
+    TRY(check_cuda(ctx, cudaStreamSynchronize(st), "Dirichlet rows"));
     k_scatter_rows<<<p->grid, kThreads, 0, st>>>(f.nb_p, f.M, f.pn_rows, p->bmap, p->err);
     k_build_poisson<<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->k, f.pp_idx, f.pp_lap, f.p_bc,
                                                    p->bmap, f.ld_b, f.pn_idx, f.pn_dx, f.pn_dy,
                                                    f.p_nx, f.p_ny, p->Lidx, p->Lw, p->es,
-                                                   p->scale, p->err);
+                                                   p->scale, p->err, p->pdir > 0 ? 1 : 0);
   }
   // normalise the rank-one column so that the constant mode has eigenvalue 1
   k_sum<double><<<p->grid, kThreads, 0, st>>>(p->es, f.M, p->gr, p->dscal);
   k_store_abs<<<1, 1, 0, st>>>(p->dscal, p->esn);
   k_scale_by_inv_abs<<<p->grid, kThreads, 0, st>>>(f.M, p->es, p->dscal);
-  k_build_helm<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bc, a, p->Hw);
+  if (p->open) {
+    int32_t* vmap = nullptr;
+    TRY(palloc(ctx, p, &vmap, f.N));
+    TRY(palloc(ctx, p, &p->Hidx, nv));
+    TRY(palloc(ctx, p, &p->Hw_v, nv));
+    TRY(check_cuda(ctx, cudaMemsetAsync(vmap, 0xff, sizeof(int32_t) * f.N, st), "memset"));
+    k_scatter_rows<<<p->grid, kThreads, 0, st>>>(f.nb_v, f.N, f.vn_rows, vmap, p->err);
+    k_build_hidx<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_idx, vmap, f.ld_vb,
+                                               f.vn_idx, p->Hidx);
+    k_build_helm_open<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bcu, vmap,
+                                                    f.ld_vb, f.vn_dx, f.vn_dy, f.v_nx, f.v_ny, a,
+                                                    p->Hw, p->err);
+    k_build_helm_open<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bcv, vmap,
+                                                    f.ld_vb, f.vn_dx, f.vn_dy, f.v_nx, f.v_ny, a,
+                                                    p->Hw_v, p->err);
+  } else {
+    k_build_helm<<<p->grid, kThreads, 0, st>>>(f.N, f.ld_v, p->k, f.vv_lap, f.v_bc, a, p->Hw);
+  }
   TRY(check_cuda(ctx, cudaGetLastError(), "plan kernels"));
   {
     int herr = 0;
@@ -1891,6 +1998,10 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
       step_plan_free(p);
       if (herr & 8)
         return set_error(ctx, RBFFD_ERR_INVALID_ARG, "composed pressure operator overflow");
+      if (herr & 48)
+        return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                         "Neumann V-rows (vn_rows) must list every Neumann V-node once, each with "
+                         "a nonzero normal derivative weight on the node itself (code %d)", herr);
       return set_error(ctx, RBFFD_ERR_INVALID_ARG,
                        "Neumann rows (pn_rows) must list every boundary P-node once (code %d)",
                        herr);
@@ -1926,6 +2037,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
     }
     TRY(to32(ctx, p, p->es, f.M, &p->es32, st));
     TRY(to32(ctx, p, p->Hw, nv, &p->Hw32, st));
+    if (p->open) TRY(to32(ctx, p, p->Hw_v, nv, &p->Hw32_v, st));
     TRY(to32(ctx, p, f.vv_dx, nv, &p->vv_dx32, st));
     TRY(to32(ctx, p, f.vv_dy, nv, &p->vv_dy32, st));
     TRY(to32(ctx, p, f.vv_lap, nv, &p->vv_lap32, st));
@@ -1962,7 +2074,12 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
         k_tile_records<double><<<p->grid, kThreads, 0, st>>>(ld, p->k, ntiles, idx, w64, *out);
       return check_cuda(ctx, cudaGetLastError(), "tile records");
     };
-    TRY(records(f.N, f.ld_v, f.vv_idx, p->Hw, p->Hw32, &p->Ht));
+    if (p->open) {
+      TRY(records(f.N, f.ld_v, p->Hidx, p->Hw, p->Hw32, &p->Ht));
+      TRY(records(f.N, f.ld_v, p->Hidx, p->Hw_v, p->Hw32_v, &p->Ht_v));
+    } else {
+      TRY(records(f.N, f.ld_v, f.vv_idx, p->Hw, p->Hw32, &p->Ht));
+    }
     // the composed operator's width is not the staged tiles' k: its SpMVs
     // read rows directly
     if (f.precond && !p->proj) TRY(records(f.M, f.ld_p, p->Lidx, p->Lw, p->Lw32, &p->Lt));
@@ -2559,6 +2676,13 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   const bool proj = P->proj != 0;
   if (f.precond && !proj) (MIX ? L32.tiles : L64.tiles) = P->Lt;
   (MIX ? H32.tiles : H64.tiles) = P->Ht;
+  // open flows: one viscous operator per component on the shared index array
+  KOp<double, double> Hu64{P->Hidx, P->Hw, f.ld_v, f.N, k, 1, nullptr};
+  KOp<double, double> Hv64{P->Hidx, P->Hw_v, f.ld_v, f.N, k, 1, nullptr};
+  KOp<float, float> Hu32{P->Hidx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
+  KOp<float, float> Hv32{P->Hidx, P->Hw32_v, f.ld_v, f.N, k, 1, nullptr, nullptr};
+  (MIX ? Hu32.tiles : Hu64.tiles) = P->Ht;
+  (MIX ? Hv32.tiles : Hv64.tiles) = P->Ht_v;
   for (int32_t step = 0; step < n_steps; ++step) {
     ConvArgs ca{f.N,  f.ld_v,       k,  f.vv_idx, vdx, vdy,   s->u,  s->v,  P->u2,
                 P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2, P->vs2, f.dt,
@@ -2567,7 +2691,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     HelmRhsArgs ha{f.N,    f.ld_v, k,      f.vv_idx, vlap,   P->us,  P->vs,  P->us2,
                    P->vs2, f.vp_idx, gdx,  gdy,      s->pt,  P->pt2, f.v_bc, f.v_nx,
                    f.v_ny, gu,     gv,     a,        f.dt,   f.km_mode, P->ru, P->rv,
-                   P->uss, P->vss, s->u,   s->v,     P->u2,  P->v2, f.cn_form, P->proj};
+                   P->uss, P->vss, s->u,   s->v,     P->u2,  P->v2, f.cn_form, P->proj,
+                   f.v_bcu, f.v_bcv};
     k_helm_rhs<K, MIX><<<G, kThreads, 0, st>>>(ha);
     P->launches += 2 + (MIX ? 2 : 0) + 4 + (MIX ? 1 : 0);  // stage kernels of this step
     int rc = check_cuda(ctx, cudaGetLastError(), "stage 1-2 kernels");
@@ -2579,12 +2704,33 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     // The viscous operator is well conditioned: its FP32 inner solves go to the
     // square of the inner tolerance (each FP64 residual of the 3M-row, two-sided
     // solve costs more than a few extra FP32 iterations).
-    if (MIX)
+    if (P->open) {
+      // per-component operators: one solve each
+      SolveResult h2[2];
+      int sw[2] = {0, 0};
+      for (int c = 0; c < 2 && !rc; ++c) {
+        const KOp<double, double>& o64 = c ? Hv64 : Hu64;
+        const KOp<float, float>& o32 = c ? Hv32 : Hu32;
+        if (MIX)
+          rc = refine<K, 1, false>(ctx, P, o64, o32, &hx[c], &hb[c], f.tol,
+                                   f.inner_tol * f.inner_tol, f.max_iter, &h2[c], &sw[c], st);
+        else
+          rc = bicgstab<K, 1, false, double, double>(ctx, P, o64, &hx[c], &hb[c], P->kw64, f.tol,
+                                                     f.max_iter, &h2[c], st);
+      }
+      hr = h2[0];
+      hr.iters = h2[0].iters + h2[1].iters;
+      hr.relres = std::max(h2[0].relres, h2[1].relres);
+      hr.converged = h2[0].converged && h2[1].converged;
+      if (!h2[1].converged || h2[1].status == 2) hr.status = h2[1].status;
+      sweeps = sw[0] + sw[1];
+    } else if (MIX) {
       rc = refine<K, 2, false>(ctx, P, H64, H32, hx, hb, f.tol, f.inner_tol * f.inner_tol,
                                f.max_iter, &hr, &sweeps, st);
-    else
+    } else {
       rc = bicgstab<K, 2, false, double, double>(ctx, P, H64, hx, hb, P->kw64, f.tol, f.max_iter,
                                                  &hr, st);
+    }
     if (rc) return rc;
     if (stats) {
       stats->helm_iters += hr.iters;
@@ -2662,7 +2808,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     k_sum<double><<<G, kThreads, 0, st>>>(P->px, f.M, P->gr, P->dscal);
     if (MIX) k_split<<<G, kThreads, 0, st>>>(f.M, P->px, P->px2);
     PresArgs pa{f.M,   f.ld_p, k,    f.pp_idx, plap,   P->px,  P->px2,
-                P->dscal, a,   s->pt, s->p, P->pt2,   P->proj};
+                P->dscal, a,   s->pt, s->p, P->pt2,   P->proj, P->pdir > 0 ? 1 : 0};
     k_pressure<K, MIX><<<G, kThreads, 0, st>>>(pa);
     // The exact projection corrects with G0 x (x = phi + const) and the wall
     // flux, with FP64 weights in both precisions (like the divergence), so
@@ -2671,7 +2817,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                 proj ? f.vp_dy : gdy,       proj ? P->px : s->pt,   proj ? P->px2 : P->pt2,
                 P->uss,   P->vss, f.v_bc,   gu,             gv,   f.dt,
                 f.overwrite_bc,   s->u,     s->v,           P->u2, P->v2,
-                P->proj,  P->dscal, P->esn, f.v_nx,         f.v_ny};
+                P->proj,  P->dscal, P->esn, f.v_nx,         f.v_ny,
+                f.v_bcu,  f.v_bcv};
     if (proj && MIX) {
       k_correct<K, false><<<G, kThreads, 0, st>>>(ka);
       k_split<<<G, kThreads, 0, st>>>(f.N, s->u, P->u2);
@@ -3155,6 +3302,9 @@ int adjoint_run(rbffd_ctx* ctx, const rbffd_flow* fp, const rbffd_state* s, rbff
     if (rc) return rc;
   }
   StepPlan* P = ctx->plan;
+  if (P->pdir)
+    return set_error(ctx, RBFFD_ERR_INVALID_ARG,
+                     "the adjoint exists for the bordered pressure system only (no Dirichlet rows)");
   if (!P->adj) {
     int rc = build_adjoint_plan(ctx, P, f, st);
     if (rc) return rc;

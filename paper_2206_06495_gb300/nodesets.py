@@ -252,18 +252,21 @@ def _edge_nodes(a, b, hfun):
 def cylinder_wake(h_wall: float = 0.03, h_wake: float = 0.04, h_far: float = 0.5,
                   x0: float = -8.0, x1: float = 24.0, y0: float = -8.0, y1: float = 8.0,
                   radius: float = 0.5, growth: float = 0.12, seed: int = 3,
-                  jitter: float = 0.25) -> StaggeredNodes:
+                  jitter: float = 0.25, rings: int = 6) -> StaggeredNodes:
     """Staggered nodes for flow past a cylinder (Section 5.2): the rectangle
     [x0, x1] x [y0, y1] outside the circle of `radius` about the origin
     (radius 0: no cylinder, a plain channel), graded by wake_spacing.
 
     P-nodes: boundary nodes on the circle (an even count, uniform in angle,
     the first at angle 0) and on the four sides (spaced by the local target
-    spacing, corners included once); interior nodes one per leaf of a
-    quadtree refined until each leaf is no larger than the target spacing at
-    its centre, placed at the leaf centre jittered by U(+-jitter * leaf
-    side), and dropped where they come closer than 0.6 of the local spacing
-    to a boundary.  The P-nodes are triangulated (Delaunay, with a ring of
+    spacing, corners included once); `rings` layers of nodes on circles
+    about the cylinder, each sqrt(3)/2 of the local spacing further out,
+    uniform in angle at the local spacing and turned by half a spacing from
+    the layer below (near-equilateral triangles along the curved wall);
+    outside them, one node per leaf of a quadtree refined until each leaf is
+    no larger than the target spacing at its centre, placed at the leaf
+    centre jittered by U(+-jitter * leaf side), and dropped where it comes
+    closer than 0.6 of the local spacing to a boundary or to the last ring.  The P-nodes are triangulated (Delaunay, with a ring of
     ghost points outside the rectangle so that the sides stay straight;
     triangles inside the cylinder, touching a ghost, or joining two
     non-adjacent circle nodes are dropped).  V-nodes: the midpoints of the
@@ -330,6 +333,23 @@ def cylinder_wake(h_wall: float = 0.03, h_wake: float = 0.04, h_far: float = 0.5
     lsy = np.concatenate(leaves_sy)
     ix = lx + rng.uniform(-jitter, jitter, lx.size) * lsx
     iy = ly + rng.uniform(-jitter, jitter, ly.size) * lsy
+    # ring layers about the cylinder
+    rx, ry = [], []
+    r_last = radius
+    if radius > 0.0:
+        n_prev = nc
+        for layer in range(1, rings + 1):
+            h_r = float(hfun(np.array([r_last]), np.array([0.0]))[0])
+            r_k = r_last + 0.5 * np.sqrt(3.0) * h_r
+            n_k = max(n_prev, 2 * int(round(np.pi * r_k / h_r)))
+            th = 2.0 * np.pi * (np.arange(n_k) + 0.5 * (layer % 2)) / n_k
+            px_k, py_k = r_k * np.cos(th), r_k * np.sin(th)
+            ok = (px_k > x0) & (px_k < x1) & (py_k > y0) & (py_k < y1)
+            rx.append(px_k[ok])
+            ry.append(py_k[ok])
+            r_last, n_prev = r_k, n_k
+    rx = np.concatenate(rx) if rx else np.zeros(0)
+    ry = np.concatenate(ry) if ry else np.zeros(0)
     hloc = hfun(ix, iy)
     # the margin takes the larger of the node's own spacing and the boundary
     # spacing at its projection, so no node enters the diametral circle of a
@@ -340,9 +360,9 @@ def cylinder_wake(h_wall: float = 0.03, h_wake: float = 0.04, h_far: float = 0.5
         (y1 - iy > 0.6 * np.maximum(hloc, hfun(ix, np.full_like(ix, y1))))
     if radius > 0.0:
         r_i = np.maximum(np.hypot(ix, iy), 1e-300)
-        h_proj = hfun(radius * ix / r_i, radius * iy / r_i)
-        keep &= r_i - radius > 0.6 * np.maximum(hloc, h_proj)
-    ix, iy = ix[keep], iy[keep]
+        h_proj = hfun(r_last * ix / r_i, r_last * iy / r_i)
+        keep &= r_i - r_last > 0.6 * np.maximum(hloc, h_proj)
+    ix, iy = np.concatenate([rx, ix[keep]]), np.concatenate([ry, iy[keep]])
 
     x = np.concatenate([bx, ix])
     y = np.concatenate([by, iy])

@@ -28,6 +28,8 @@ OP_INTERP, OP_DX, OP_DY, OP_LAP = 1, 2, 4, 8
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 PROJ_PAPER, PROJ_EXACT = 0, 1
+BC_DIRICHLET, BC_NEUMANN = 1, 2  # rbffd_flow.v_bcu / v_bcv
+PBC_DIRICHLET = 2                # rbffd_flow.p_bc: p~ = 0 row
 CN_PRINTED, CN_KIM_MOIN = 0, 1
 
 _ERRNAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_SINGULAR_STENCIL: "SINGULAR_STENCIL",
@@ -68,7 +70,10 @@ class FlowC(C.Structure):
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("max_iter", C.c_int32),
                 ("km_mode", C.c_int32), ("overwrite_bc", C.c_int32), ("profile", C.c_int32),
                 ("p_edges", C.c_void_p), ("n_edges", C.c_int64), ("p_x", C.c_void_p),
-                ("p_y", C.c_void_p), ("projection", C.c_int32), ("cn_form", C.c_int32)]
+                ("p_y", C.c_void_p), ("projection", C.c_int32), ("cn_form", C.c_int32),
+                ("v_bcu", C.c_void_p), ("v_bcv", C.c_void_p), ("nb_v", C.c_int64),
+                ("ld_vb", C.c_int64), ("vn_rows", C.c_void_p), ("vn_idx", C.c_void_p),
+                ("vn_dx", C.c_void_p), ("vn_dy", C.c_void_p)]
 
 
 class StateC(C.Structure):
@@ -139,6 +144,10 @@ PROTOTYPES = {
     "rbffd_adjoint_step": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.POINTER(StateC),
                                      C.POINTER(AdjointC), C.c_void_p, C.c_void_p,
                                      C.POINTER(Stats), C.c_void_p]),
+    "rbffd_cylinder_forces": (C.c_int, [C.c_void_p, C.POINTER(FlowC), C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                        C.c_double, C.c_double, C.c_double,
+                                        C.POINTER(C.c_double), C.c_void_p]),
 }
 
 
@@ -320,7 +329,15 @@ class Flow:
                      p_edges=p("p_edges") if "p_edges" in t else None,
                      n_edges=t["p_edges"].shape[0] if "p_edges" in t else 0,
                      p_x=p("px") if "px" in t else None, p_y=p("py") if "py" in t else None,
-                     projection=self.projection, cn_form=self.cn_form)
+                     projection=self.projection, cn_form=self.cn_form,
+                     v_bcu=p("v_bcu") if "v_bcu" in t else None,
+                     v_bcv=p("v_bcv") if "v_bcv" in t else None,
+                     nb_v=t["vn_rows"].numel() if "vn_rows" in t else 0,
+                     ld_vb=t["vn_idx"].shape[1] if "vn_idx" in t else 0,
+                     vn_rows=p("vn_rows") if "vn_rows" in t else None,
+                     vn_idx=p("vn_idx") if "vn_idx" in t else None,
+                     vn_dx=p("vn_dx") if "vn_dx" in t else None,
+                     vn_dy=p("vn_dy") if "vn_dy" in t else None)
 
 
 def flow_from_nodes(ctx: Context, nodes, Re: float, dt: float, device="cuda", **kw) -> Flow:
@@ -526,3 +543,15 @@ def probe_fma(ctx: Context, dtype: int = F64, iters: int = 4096) -> float:
 
 def version() -> int:
     return lib().rbffd_version()
+
+
+def cylinder_forces(ctx: Context, flow: Flow, state: State, rows, radius: float, Re: float,
+                    cx: float = 0.0, cy: float = 0.0):
+    """rbffd_cylinder_forces: (C_D, C_L) of the circular body whose surface
+    P-nodes are `rows` (int32 device tensor, increasing angle, even count)."""
+    out = (C.c_double * 2)()
+    fc = flow.cstruct()
+    ctx.check(lib().rbffd_cylinder_forces(ctx.handle, C.byref(fc), _ptr(state.u), _ptr(state.v),
+                                          _ptr(state.p), _ptr(rows), rows.numel(), cx, cy,
+                                          radius, Re, out, _stream()))
+    return float(out[0]), float(out[1])

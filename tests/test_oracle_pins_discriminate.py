@@ -126,3 +126,39 @@ def test_wrong_sign_of_pressure_increment_is_caught(monkeypatch):
     monkeypatch.setattr(O.FractionalStep, "__init__", init)
     with np.errstate(all="ignore"):
         assert _fails(pins.test_exact_projection_taylor_green_space_and_time)
+
+
+def _planted(monkeypatch, fn_name, old, new):
+    """Replace `old` by `new` in the source of oracle function `fn_name` and
+    install the result in the oracle module (one planted mistake)."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(O, fn_name)))
+    assert src.count(old) == 1, (fn_name, old)
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), f"<planted {fn_name}>", "exec"), ns)
+    monkeypatch.setattr(O, fn_name, ns[fn_name])
+
+
+@pytest.mark.parametrize("old,new,field", [
+    ("(uy + vx) * nx", "uy * nx", "v=x^2"),        # grad U^T dropped from the stress
+    ("-pc * nx", "pc * nx", "p=x"),                 # pressure traction with the wrong sign
+    ("return 2.0 * fx / d, 2.0 * fy / d", "return fx / d, fy / d", "u=y^2"),  # C = F / D
+])
+def test_force_mistakes_are_caught(monkeypatch, old, new, field):
+    from paper_2206_06495_gb300 import nodesets as ns
+    from tests import test_oracle_pins_wake as wp
+    nd = ns.cylinder_wake(**wp.SMALL)
+    wake = (nd, O.build_operators(nd))
+    _planted(monkeypatch, "cylinder_forces", old, new)
+    assert _fails(wp.test_forces_of_polynomial_fields, wake, field)
+
+
+def test_tangential_derivative_in_neumann_rows_is_caught(monkeypatch):
+    """Neumann V-rows built from D_x alone instead of n_x D_x + n_y D_y."""
+    from paper_2206_06495_gb300 import nodesets as ns
+    from tests import test_oracle_pins_wake as wp
+    nd = ns.cylinder_wake(**wp.SMALL)
+    _planted(monkeypatch, "neumann_rows", "nodes.v_nx[rows, None] * w[OP_DX] + "
+             "nodes.v_ny[rows, None] * w[OP_DY]", "w[OP_DX]")
+    assert _fails(wp.test_neumann_velocity_rows_reproduce_cubics, (nd, None))
