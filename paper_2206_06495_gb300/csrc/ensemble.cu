@@ -121,6 +121,22 @@ __device__ __forceinline__ void col_reduce(double (&v)[NV], int C, EReduce rd, F
                f = I * (C) + ef_c;                                                       \
        I < ef_r1; I += ef_step, f += kT)
 
+// The same items for the gathering kernels, in another row order: row group
+// g = t / C of the kT / C groups walks its own contiguous part of the block's
+// rows one after the other, so a warp's consecutive rows are neighbours in
+// the (Morton) node order and find most of their stencil's operand lines
+// still in L1 from the row before.  The column is t mod C, as in EFOR.
+#define EFOR_SEQ(n, C, I)                                                                 \
+  const int64_t es_share = ((int64_t)(n) + gridDim.x - 1) / gridDim.x;                   \
+  const int64_t es_r0 = min((int64_t)(n), es_share * blockIdx.x);                        \
+  const int64_t es_r1 = min((int64_t)(n), es_share * (blockIdx.x + 1));                  \
+  const int es_groups = kT / (C);                                                        \
+  const int64_t es_sub = (es_share + es_groups - 1) / es_groups;                         \
+  const int ef_c = (int)threadIdx.x % (C);                                               \
+  const int64_t es_a = min(es_r1, es_r0 + es_sub * ((int)threadIdx.x / (C)));             \
+  const int64_t es_b = min(es_r1, es_a + es_sub);                                        \
+  for (int64_t I = es_a, f = es_a * (C) + ef_c; I < es_b; ++I, f += (C))
+
 // ------------------------------------------------------------ explicit stages
 // sum_s w[s][i] (x2[j][c] - x2[ref][c]) over split FP32 copies
 // (K > 0: the stencil size at compile time, every gather issued at once)
@@ -360,7 +376,7 @@ __global__ void __launch_bounds__(kT)
   const float sig = op.visc ? 0.f : (float)sc->sum_p[c0];
   double acc[1] = {0.0};
   if (act) {
-    EFOR(op.n, C, i) {
+    EFOR_SEQ(op.n, C, i) {
       float y = erow32<K>(op, w, i, zp, C, ef_c);
       if (op.visc)
         y = zp[f] - ac * y;
@@ -415,7 +431,7 @@ __global__ void __launch_bounds__(kT)
   const float sig = op.visc ? 0.f : (float)sc->sum_s[c0];
   double acc[2] = {0.0, 0.0};
   if (act) {
-    EFOR(op.n, C, i) {
+    EFOR_SEQ(op.n, C, i) {
       float y = erow32<K>(op, w, i, zs, C, ef_c);
       if (op.visc)
         y = zs[f] - ac * y;
@@ -527,7 +543,7 @@ __global__ void __launch_bounds__(kT)
     e_pc_restrict(AmgLevel F, int64_t nagg, int C, const float* __restrict__ r,
                   float* __restrict__ x, float* __restrict__ rc, const EScal* sc) {
   if (sc->done) return;
-  EFOR(nagg, C, I) {
+  EFOR_SEQ(nagg, C, I) {
     const int c = ef_c;
     float acc = 0.f;
     for (int32_t i = F.cptr[I]; i < F.cptr[I + 1]; ++i) {
@@ -644,7 +660,7 @@ __global__ void __launch_bounds__(kT)
             double inv_ces, double inv_R, EScal* sc, EReduce rd) {
   if (sc->done) return;
   double acc[1] = {0.0};
-  EFOR(F.n, C, i) {
+  EFOR_SEQ(F.n, C, i) {
     const int c = ef_c;
     const float xi = x[f];
     float ax = F.diag[i] * xi;
@@ -714,7 +730,7 @@ __global__ void __launch_bounds__(kT)
                  const double* __restrict__ b, double* __restrict__ r,
                  const double* __restrict__ xsum, int C, EReduce rd, double* out) {
   double acc[2] = {0.0, 0.0};
-  EFOR(op.n, C, i) {
+  EFOR_SEQ(op.n, C, i) {
     const int c = ef_c;
     double y = 0.0;
     const int kk = K > 0 ? K : op.k;

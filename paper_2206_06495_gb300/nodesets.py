@@ -249,9 +249,9 @@ def _edge_nodes(a, b, hfun):
     return a[0] + (b[0] - a[0]) * t, a[1] + (b[1] - a[1]) * t
 
 
-def cylinder_wake(h_wall: float = 0.03, h_wake: float = 0.04, h_far: float = 0.5,
+def cylinder_wake(h_wall: float = 0.03, h_wake: float = 0.04, h_far: float = 0.3,
                   x0: float = -8.0, x1: float = 24.0, y0: float = -8.0, y1: float = 8.0,
-                  radius: float = 0.5, growth: float = 0.12, seed: int = 3,
+                  radius: float = 0.5, growth: float = 0.14, seed: int = 3,
                   jitter: float = 0.25, rings: int = 6) -> StaggeredNodes:
     """Staggered nodes for flow past a cylinder (Section 5.2): the rectangle
     [x0, x1] x [y0, y1] outside the circle of `radius` about the origin

@@ -129,8 +129,8 @@ def test_open_flows_refuse_what_they_do_not_support(R):
 
 
 def test_cylinder_wake_matches_the_papers_coefficients(R):
-    """Section 5.2's Re = 100 case on the paper-sized layout (M = 17,847,
-    N = 53,226; Delta r 0.03 at the wall, 0.04 on the wake centreline),
+    """Section 5.2's Re = 100 case on the paper-sized layout (M = 18,348,
+    N = 54,610; Delta r 0.03 at the wall, 0.04 on the wake centreline),
     dt = 0.005 from the impulsive start, MIXED precision: after the vortex
     street has formed (t = 150), the mean drag, the lift amplitude and the
     Strouhal number over the last 40 time units lie within the spread of the
