@@ -70,6 +70,13 @@ def parse():
                     help="profiler capture: the batched ensemble (--ensemble members on an "
                          "--ens-n cavity) after --warmup steps, then one ensemble step between "
                          "cudaProfilerStart/Stop; prints its statistics")
+    ap.add_argument("--wake", type=int, default=0,
+                    help="the cylinder wake of Section 5.2 instead of the benchmark: this many "
+                         "steps (dt 0.005, Re --wake-re) from the impulsive start on the "
+                         "paper-sized layout, drag and lift every 10 steps; prints a summary "
+                         "(and writes the history to --wake-out)")
+    ap.add_argument("--wake-re", type=float, default=100.0)
+    ap.add_argument("--wake-out", default="")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiler capture: set up, take --warmup steps, then one step between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off); prints its "
@@ -896,6 +903,57 @@ def profile_ensemble(args):
     return {"profile_ensemble": E, "M": nd.M, "N": nd.N, "dt": args.ens_dt, "stats": s}
 
 
+def wake_run(args):
+    """The cylinder wake (Section 5.2) on the paper-sized layout: --wake steps
+    of dt 0.005 from the impulsive start (u = 1 off the cylinder), MIXED
+    precision, solves to 1e-10; C_D and C_L every 10 steps.  The summary gives
+    the cost per step and, over the last quarter of the run, the mean drag,
+    the lift amplitude and the Strouhal number of the lift."""
+    import numpy as np
+    import torch
+
+    from paper_2206_06495_gb300 import build
+    from paper_2206_06495_gb300 import nodesets as ns
+    build.build()
+    from paper_2206_06495_gb300 import rbffd as R
+    from paper_2206_06495_gb300 import wake
+
+    nd = ns.cylinder_wake()
+    ctx = R.Context(28, 7, 3)
+    flow = wake.wake_flow(ctx, nd, Re=args.wake_re, dt=0.005, precision=R.PREC_MIXED,
+                          tol=1e-10, inner_tol=1e-2)
+    gu, gv = wake.wake_data(nd)
+    st = R.State.zeros(flow)
+    cyl = torch.as_tensor(nd.v_wall == ns.WALL_CYLINDER, device="cuda")
+    st.u.copy_(torch.where(cyl, torch.zeros_like(gu), torch.ones_like(gu)))
+    rows, _ = wake.surface_rows(nd)
+    hist, iters = [], 0
+    t0 = time.time()
+    for j in range(0, args.wake, 10):
+        s = R.step(ctx, flow, st, gu, gv, min(10, args.wake - j))
+        iters += s["poisson_iters"]
+        cd, cl = wake.forces(ctx, flow, st, nd, rows)
+        hist.append((min(j + 10, args.wake) * 0.005, cd, cl))
+    wall = time.time() - t0
+    h = np.array(hist)
+    if args.wake_out:
+        np.savetxt(args.wake_out, h, header="t C_D C_L")
+    tail = h[h[:, 0] >= 0.75 * h[-1, 0]]
+    try:
+        st_num = wake.strouhal(tail[:, 0], tail[:, 2])
+    except ValueError:
+        st_num = None
+    return {"wake": {"Re": args.wake_re, "M": nd.M, "N": nd.N, "steps": args.wake,
+                     "t_end": float(h[-1, 0]), "ms_per_step": 1e3 * wall / args.wake,
+                     "poisson_iters_per_step": iters / args.wake,
+                     "window": [float(tail[0, 0]), float(tail[-1, 0])],
+                     "C_D_mean": float(tail[:, 1].mean()),
+                     "C_L_amplitude": float(0.5 * (tail[:, 2].max() - tail[:, 2].min())),
+                     "St": st_num,
+                     "C_D_at": {f"{t:g}": float(h[np.argmin(np.abs(h[:, 0] - t)), 1])
+                                for t in (5, 10, 20, 40, 60, 80, 100) if t <= h[-1, 0]}}}
+
+
 def profile_ops(args):
     """Operator kernels of the benchmark's node family between
     cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
@@ -946,6 +1004,9 @@ def main():
         return
     if args.profile_ensemble:
         print(json.dumps(profile_ensemble(args)))
+        return
+    if args.wake:
+        print(json.dumps(wake_run(args)))
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
