@@ -1209,6 +1209,31 @@ __global__ void k_extrapolate(int64_t n, double* __restrict__ x, double* __restr
   }
 }
 
+// x <- 3 x - 3 x_prev2 + x_prev3 (quadratic extrapolation of the last three
+// solutions), and the history moves by one step
+__global__ void k_extrapolate3(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2,
+                               double* __restrict__ x_prev3) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = x[i], t2 = x_prev2[i];
+    x[i] = 3.0 * (t - t2) + x_prev3[i];
+    x_prev3[i] = t2;
+    x_prev2[i] = t;
+  }
+}
+
+// x <- 2 x - x_prev2, keeping x_prev2 as x_prev3 for the next step
+__global__ void k_extrapolate2(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2,
+                               double* __restrict__ x_prev3) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = x[i], t2 = x_prev2[i];
+    x[i] = 2.0 * t - t2;
+    x_prev3[i] = t2;
+    x_prev2[i] = t;
+  }
+}
+
 __global__ void k_split(int64_t n, const double* __restrict__ x, float2* __restrict__ x2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -1780,6 +1805,8 @@ struct StepPlan {
   int64_t px_step = -1;  // step index whose pressure solve left its solution in px
   double* pxp = nullptr;   // the pressure solution of the step before px's
   int64_t pxp_step = -1;   // px_step of pxp's solution when it was current
+  double* pxpp = nullptr;  // the one before that
+  int64_t pxpp_step = -1;
   float2 *u2 = nullptr, *v2 = nullptr, *us2 = nullptr, *vs2 = nullptr, *uss2 = nullptr,
          *vss2 = nullptr, *pt2 = nullptr, *px2 = nullptr;
   // Krylov work (6 vectors x 2 right sides) in FP64 and FP32
@@ -1934,6 +1961,7 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   TRY(palloc(ctx, p, &p->pb, f.M));
   TRY(palloc(ctx, p, &p->px, f.M));
   TRY(palloc(ctx, p, &p->pxp, f.M));
+  TRY(palloc(ctx, p, &p->pxpp, f.M));
   for (int a = 0; a < 7; ++a)
     for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw64[a][b], nmax));
   TRY(palloc(ctx, p, &p->sc, 1));
@@ -2764,8 +2792,18 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                              "warm start");
       if (rc) return rc;
       P->pxp_step = -1;
+      P->pxpp_step = -1;
     } else {
-      if (P->pxp_step == s->j - 1) {
+      static const bool quad = getenv("RBFFD_QUAD") != nullptr;  // TEMPORARY A/B switch
+      if (quad && P->pxp_step == s->j - 1 && P->pxpp_step == s->j - 2) {
+        k_extrapolate3<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp, P->pxpp);
+        rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
+        P->pxpp_step = s->j - 1;
+      } else if (quad && P->pxp_step == s->j - 1) {
+        k_extrapolate2<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp, P->pxpp);
+        rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
+        P->pxpp_step = s->j - 1;
+      } else if (P->pxp_step == s->j - 1) {
         k_extrapolate<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp);
         rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
       } else {
