@@ -18,7 +18,6 @@
 // preconditioned by a batched V-cycle on the multigrid hierarchy of step.cu
 // (amg.cuh), with the same rank-one completion of the constant mode per
 // column.  Per-column reductions are summed in a fixed order.
-#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -315,20 +314,7 @@ struct EOp {
   const float* a;       // viscous: a per column
   const float* es;      // pressure: rank-one column
   const float* a1;      // pressure: row sums
-  // staged operand (null: gathers from global memory): the rows of tile t
-  // (kTileRowsE consecutive rows) reference the operand rows
-  // ulist[uoff[t] .. uoff[t+1]), and slot s of row i the entry lidx[s][i]
-  // of that list
-  const int32_t* uoff = nullptr;
-  const int32_t* ulist = nullptr;
-  const uint16_t* lidx = nullptr;
-  int64_t ntile = 0;
 };
-
-// Rows per tile of the staged batched SpMV, and its shared-memory budget in
-// floats (48 KB: the operand rows of a tile, all columns).
-constexpr int kTileRowsE = 32;
-constexpr int kStageFloats = 12288;
 
 template <int K>
 __device__ __forceinline__ float erow32(const EOp& op, const float* w, int64_t i, const float* x,
@@ -375,43 +361,6 @@ __global__ void __launch_bounds__(kT)
   });
 }
 
-// Staged rows of a batched SpMV (op.ulist set).  The block walks the tiles
-// blockIdx.x, + gridDim.x, ...; it copies the operand rows a tile references
-// (all C columns of each, coalesced) into shared memory, then row group
-// g = t / C takes the tile's rows g, g + kT / C, ... and sums each row from
-// shared memory in slot order (the order of erow32).  A tile that references
-// more operand rows than the budget holds gathers from global memory
-// instead.  row(i, f, sum) finishes row i (item f = i C + c0).
-template <int K, typename Row>
-__device__ __forceinline__ void staged_rows(const EOp& op, const float* __restrict__ w,
-                                            const float* __restrict__ x, int C, int c0, bool act,
-                                            float* xs, Row row) {
-  const int umax = kStageFloats / C;
-  const int kk = K > 0 ? K : op.k;
-  for (int64_t tile = blockIdx.x; tile < op.ntile; tile += gridDim.x) {
-    const int32_t u0 = op.uoff[tile], nu = op.uoff[tile + 1] - u0;
-    const bool staged = nu <= umax;
-    __syncthreads();  // the block is done with the previous tile's rows
-    if (staged)
-      for (int e = threadIdx.x; e < nu * C; e += kT)
-        xs[e] = x[(int64_t)op.ulist[u0 + e / C] * C + e % C];
-    __syncthreads();
-    if (!act) continue;
-    for (int r = (int)threadIdx.x / C; r < kTileRowsE; r += kT / C) {
-      const int64_t i = tile * kTileRowsE + r;
-      if (i >= op.n) break;
-      float acc = 0.f;
-#pragma unroll(K > 0 ? K : 1)
-      for (int s = 0; s < kk; ++s) {
-        const float xv = staged ? xs[(int)op.lidx[s * op.ld + i] * C + c0]
-                                : x[(int64_t)op.idx[s * op.ld + i] * C + c0];
-        acc += w[s * op.ld + i] * xv;
-      }
-      row(i, i * C + c0, acc);
-    }
-  }
-}
-
 // v = A zp (+ rank-one terms); reduce (rh, v) -> alpha
 template <int K>
 __global__ void __launch_bounds__(kT)
@@ -426,17 +375,7 @@ __global__ void __launch_bounds__(kT)
   const float kap = op.visc ? 0.f : (float)sc->kap[0][c0];
   const float sig = op.visc ? 0.f : (float)sc->sum_p[c0];
   double acc[1] = {0.0};
-  if (op.ulist) {
-    extern __shared__ float xs_v[];
-    staged_rows<K>(op, w, zp, C, c0, act, xs_v, [&](int64_t i, int64_t f, float y) {
-      if (op.visc)
-        y = zp[f] - ac * y;
-      else
-        y += kap * op.a1[i] + op.es[i] * sig;
-      v[f] = y;
-      acc[0] += (double)rh[f] * y;
-    });
-  } else if (act) {
+  if (act) {
     EFOR_SEQ(op.n, C, i) {
       float y = erow32<K>(op, w, i, zp, C, ef_c);
       if (op.visc)
@@ -491,18 +430,7 @@ __global__ void __launch_bounds__(kT)
   const float kap = op.visc ? 0.f : (float)sc->kap[1][c0];
   const float sig = op.visc ? 0.f : (float)sc->sum_s[c0];
   double acc[2] = {0.0, 0.0};
-  if (op.ulist) {
-    extern __shared__ float xs_t[];
-    staged_rows<K>(op, w, zs, C, c0, act, xs_t, [&](int64_t i, int64_t f, float y) {
-      if (op.visc)
-        y = zs[f] - ac * y;
-      else
-        y += kap * op.a1[i] + op.es[i] * sig;
-      tv[f] = y;
-      acc[0] += (double)y * s[f];
-      acc[1] += (double)y * y;
-    });
-  } else if (act) {
+  if (act) {
     EFOR_SEQ(op.n, C, i) {
       float y = erow32<K>(op, w, i, zs, C, ef_c);
       if (op.visc)
@@ -884,10 +812,6 @@ struct EnsPlan {
   // batched V-cycle work per level (r, x) and the coarse r, z
   float* lr[kAmgMaxLevels + 1] = {};
   float* lx[kAmgMaxLevels + 1] = {};
-  // staged-operand tables of the pressure operator (see EOp)
-  int32_t *t_uoff = nullptr, *t_ulist = nullptr;
-  uint16_t* t_lidx = nullptr;
-  int64_t t_ntile = 0;
   EScal* sc = nullptr;
   EScal* sc_t = nullptr;  // scalars of the timed SpMV launches (profile)
   EReduce rd{};
@@ -912,15 +836,6 @@ int ealloc(rbffd_ctx* ctx, EnsPlan* p, T** out, size_t count) {
   *out = (T*)ptr;
   return RBFFD_OK;
 }
-
-// kern<28> / kern<0> as EK, with `smem` bytes of dynamic shared memory
-#define EKS(kern, grid, smem, ...)                               \
-  do {                                                           \
-    if (k == 28)                                                 \
-      kern<28><<<grid, kT, smem, st>>>(__VA_ARGS__);             \
-    else                                                         \
-      kern<0><<<grid, kT, smem, st>>>(__VA_ARGS__);              \
-  } while (0)
 
 // kern<28> when the stencil size k is 28 (every gather of a row unrolled and
 // issued at once), kern<0> (runtime size) otherwise
@@ -1112,48 +1027,6 @@ int ens_build(rbffd_ctx* ctx, const rbffd_flow& f, int E, EnsPlan** out, cudaStr
     TRY(amg_build(ctx, f, hd.data(), hes.data(), &p->amg, st));
   }
   TRY(ens_to32(ctx, p, p->Lw, np, &p->Lw32, st));
-  {
-    // staged-operand tables of the pressure operator: for each tile of
-    // kTileRowsE rows the sorted distinct operand rows it references, and
-    // each slot's position in that list (at most kTileRowsE k < 65536)
-    std::vector<int32_t> hidx((size_t)np);
-    TRY(check_cuda(ctx, cudaMemcpyAsync(hidx.data(), p->Lidx, sizeof(int32_t) * np,
-                                        cudaMemcpyDeviceToHost, st), "index copy"));
-    TRY(check_cuda(ctx, cudaStreamSynchronize(st), "index copy"));
-    const int64_t nt = (f.M + kTileRowsE - 1) / kTileRowsE;
-    std::vector<int32_t> uoff(nt + 1, 0), ulist, buf;
-    std::vector<uint16_t> lidx((size_t)np, 0);
-    for (int64_t t = 0; t < nt; ++t) {
-      const int64_t r0 = t * kTileRowsE, r1 = std::min<int64_t>(f.M, r0 + kTileRowsE);
-      buf.clear();
-      for (int q = 0; q < k; ++q)
-        for (int64_t i = r0; i < r1; ++i) buf.push_back(hidx[q * f.ld_p + i]);
-      std::sort(buf.begin(), buf.end());
-      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-      for (int q = 0; q < k; ++q)
-        for (int64_t i = r0; i < r1; ++i)
-          lidx[q * f.ld_p + i] = (uint16_t)(std::lower_bound(buf.begin(), buf.end(),
-                                                             hidx[q * f.ld_p + i]) - buf.begin());
-      ulist.insert(ulist.end(), buf.begin(), buf.end());
-      uoff[t + 1] = (int32_t)ulist.size();
-    }
-    TRY(ealloc(ctx, p, &p->t_uoff, uoff.size()));
-    TRY(ealloc(ctx, p, &p->t_ulist, ulist.size()));
-    TRY(ealloc(ctx, p, &p->t_lidx, lidx.size()));
-    TRY(check_cuda(ctx, cudaMemcpyAsync(p->t_uoff, uoff.data(), sizeof(int32_t) * uoff.size(),
-                                        cudaMemcpyHostToDevice, st), "tile tables"));
-    TRY(check_cuda(ctx, cudaMemcpyAsync(p->t_ulist, ulist.data(), sizeof(int32_t) * ulist.size(),
-                                        cudaMemcpyHostToDevice, st), "tile tables"));
-    TRY(check_cuda(ctx, cudaMemcpyAsync(p->t_lidx, lidx.data(), sizeof(uint16_t) * lidx.size(),
-                                        cudaMemcpyHostToDevice, st), "tile tables"));
-    TRY(check_cuda(ctx, cudaStreamSynchronize(st), "tile tables"));
-    p->t_ntile = nt;
-    const int smem = kStageFloats * (int)sizeof(float);
-    TRY(check_cuda(ctx, cudaFuncSetAttribute(e_spmv_v<28>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "smem"));
-    TRY(check_cuda(ctx, cudaFuncSetAttribute(e_spmv_v<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "smem"));
-    TRY(check_cuda(ctx, cudaFuncSetAttribute(e_spmv_t<28>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "smem"));
-    TRY(check_cuda(ctx, cudaFuncSetAttribute(e_spmv_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "smem"));
-  }
   TRY(ens_to32(ctx, p, p->es, f.M, &p->es32, st));
   TRY(ealloc(ctx, p, &p->a1_32, f.M));
   e_rowsum<<<p->grid, kT, 0, st>>>(f.M, f.ld_p, k, p->Lw, p->a1_32);
@@ -1246,7 +1119,6 @@ struct ESolve {
 int ens_bicgstab(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const float* w32, int C, bool pc,
                  double inner_tol, int maxit, ESolve* res, cudaStream_t st) {
   const int G = P->grid, k = op.k;
-  const int smem = op.ulist ? kStageFloats * (int)sizeof(float) : 0;
   float *x = P->kw[0], *r = P->kw[1], *rh = P->kw[2], *pp = P->kw[3], *v = P->kw[4],
         *s = P->kw[5], *t = P->kw[6], *zp = P->kw[7], *zs = P->kw[8];
   const float* cnode = pc ? P->amg->cnode : nullptr;
@@ -1264,13 +1136,13 @@ int ens_bicgstab(rbffd_ctx* ctx, EnsPlan* P, const EOp& op, const float* w32, in
         ens_vcycle(P, pp, 0, zp, st);
         zpp = zp;
       }
-      EKS(e_spmv_v, G, smem, op, w32, zpp, v, rh, P->sc, P->rd);
+      EK(e_spmv_v, G, op, w32, zpp, v, rh, P->sc, P->rd);
       e_update_s<<<G, kT, 0, st>>>(n, r, v, s, cnode, P->sc, P->rd);
       if (pc) {
         ens_vcycle(P, s, 1, zs, st);
         zss = zs;
       }
-      EKS(e_spmv_t, G, smem, op, w32, zss, t, s, P->sc, P->rd);
+      EK(e_spmv_t, G, op, w32, zss, t, s, P->sc, P->rd);
       e_update_xr<<<G, kT, 0, st>>>(n, x, r, rh, zpp, zss, s, t, pc ? 1 : 0, P->sc, P->rd);
       e_update_p<<<G, kT, 0, st>>>(n, pp, r, v, cnode, P->sc, P->rd);
       P->launches += 5;
@@ -1393,10 +1265,6 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
   const int64_t l0 = P->launches;
   EOp H{f.vv_idx, f.ld_v, f.N, k, 1, P->aV32, nullptr, nullptr};
   EOp L{P->Lidx, f.ld_p, f.M, k, 0, nullptr, P->es32, P->a1_32};
-  L.uoff = P->t_uoff;
-  L.ulist = P->t_ulist;
-  L.lidx = P->t_lidx;
-  L.ntile = P->t_ntile;
   for (int32_t step = 0; step < n_steps; ++step) {
     EK(e_convect, G, f.N, f.ld_v, k, E, f.vv_idx, P->vv_dx32, P->vv_dy32, s->u, s->v,
                                 P->u2, P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2,
@@ -1469,8 +1337,7 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
       constexpr int kReps = 20;
       cudaEventRecord(e0, st);
       for (int r = 0; r < kReps; ++r)
-        EKS(e_spmv_v, G, kStageFloats * (int)sizeof(float), L, P->Lw32, P->kw[7], P->kw[4],
-            P->kw[2], P->sc_t, P->rd);
+        EK(e_spmv_v, G, L, P->Lw32, P->kw[7], P->kw[4], P->kw[2], P->sc_t, P->rd);
       cudaEventRecord(e1, st);
       float ms = 0.f;
       rc = check_cuda(ctx, cudaEventSynchronize(e1), "timing sync");

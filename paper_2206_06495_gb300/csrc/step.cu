@@ -1198,19 +1198,9 @@ __global__ void k_addcorr(int64_t n, Vecs<double, NRHS> x, Vecs<float, NRHS> e32
   }
 }
 
-// Initial guess of a pressure solve from the two previous solutions (linear
-// extrapolation in time): x = 2 x_prev - x_prev2, and x_prev2 takes x_prev.
-__global__ void k_extrapolate(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double t = x[i];
-    x[i] = 2.0 * t - x_prev2[i];
-    x_prev2[i] = t;
-  }
-}
-
-// x <- 3 x - 3 x_prev2 + x_prev3 (quadratic extrapolation of the last three
-// solutions), and the history moves by one step
+// Initial guess of a pressure solve from the three previous solutions
+// (quadratic extrapolation in time): x <- 3 x - 3 x_prev2 + x_prev3, and the
+// history moves by one step.
 __global__ void k_extrapolate3(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2,
                                double* __restrict__ x_prev3) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1222,7 +1212,8 @@ __global__ void k_extrapolate3(int64_t n, double* __restrict__ x, double* __rest
   }
 }
 
-// x <- 2 x - x_prev2, keeping x_prev2 as x_prev3 for the next step
+// The same from two solutions (linear extrapolation): x <- 2 x - x_prev2,
+// keeping x_prev2 as x_prev3 for the next step.
 __global__ void k_extrapolate2(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2,
                                double* __restrict__ x_prev3) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -2780,10 +2771,11 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, f.pv_dx,  f.pv_dy,      P->uss,
                P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb, P->proj};
     k_divergence<K, false><<<G, kThreads, 0, st>>>(da);
-    // Initial guess: the linear extrapolation of the two previous steps'
-    // solutions when both are at hand, else the previous solution, else the
-    // state's p~.  Any guess leaves the converged solution the same; a better
-    // one saves iterations (p~ changes smoothly from step to step).
+    // Initial guess: the quadratic extrapolation of the three previous steps'
+    // solutions when all are at hand, the linear one of two, else the previous
+    // solution, else the state's p~.  Any guess leaves the converged solution
+    // the same; a better one saves iterations (p~ changes smoothly from step
+    // to step, and the quadratic guess is off by O(dt^3)).
     if (P->px_step != s->j) {
       // the exact projection solves for the increment of p~: start from zero
       rc = proj ? check_cuda(ctx, cudaMemsetAsync(P->px, 0, sizeof(double) * f.M, st), "zero start")
@@ -2794,22 +2786,19 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
       P->pxp_step = -1;
       P->pxpp_step = -1;
     } else {
-      static const bool quad = getenv("RBFFD_QUAD") != nullptr;  // TEMPORARY A/B switch
-      if (quad && P->pxp_step == s->j - 1 && P->pxpp_step == s->j - 2) {
+      if (P->pxp_step == s->j - 1 && P->pxpp_step == s->j - 2) {
         k_extrapolate3<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp, P->pxpp);
         rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
         P->pxpp_step = s->j - 1;
-      } else if (quad && P->pxp_step == s->j - 1) {
+      } else if (P->pxp_step == s->j - 1) {
         k_extrapolate2<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp, P->pxpp);
         rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
         P->pxpp_step = s->j - 1;
-      } else if (P->pxp_step == s->j - 1) {
-        k_extrapolate<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp);
-        rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
       } else {
         rc = check_cuda(ctx, cudaMemcpyAsync(P->pxp, P->px, sizeof(double) * f.M,
                                              cudaMemcpyDeviceToDevice, st),
                         "previous solution");
+        P->pxpp_step = -1;
       }
       if (rc) return rc;
       P->pxp_step = s->j;
