@@ -5,9 +5,10 @@ Workload: lid-driven cavity at Re = 10^4 on a jittered 1000 x 1000 P-lattice
 (1,000,000 pressure nodes, ~3,000,000 velocity nodes), (n, m, q) = (28, 7, 3),
 dt = 2e-4, from rest.  A step is one full fractional step (convection,
 Crank-Nicolson viscous solves, divergence, pressure Poisson solve, pressure,
-correction) through rbffd_step.  The headline is the MIXED path (FP32 SpMVs and
-inner Krylov iterations, FP64 refinement to 1e-10 relative residual); the FP64
-path is timed beside it on the same box.
+correction) through rbffd_step.  The headline is the FP64 path (FP64 weights,
+vectors and Krylov recurrences, FP32 multigrid preconditioner, solves to 1e-10
+relative residual); the MIXED path (FP32 SpMVs and inner Krylov iterations,
+FP64 refinement to the same residual) is timed beside it on the same box.
 
 The timed steps follow --spinup steps from rest (a developed start) and
 --warmup steps.  Prints one JSON line.  `--impl reference` times the CPU
@@ -605,7 +606,9 @@ def run_ours(args):
         return None
     if not res:
         return {"metric": METRIC, "value": None, "unit": UNIT, "error": failed}
-    head = "mixed" if "mixed" in res else "fp64"
+    # the headline is the FP64 path (the faster one since the pressure and
+    # viscous solves start from extrapolated guesses); MIXED is timed beside it
+    head = "fp64" if "fp64" in res else "mixed"
     r = res[head]
     value = whole_job_rate(args.steps, world, r["ms"])
     e2e = whole_job_rate(args.steps, world, r["e2e_ms"])

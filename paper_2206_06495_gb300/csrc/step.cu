@@ -91,6 +91,8 @@ struct KOp {
   // tile records of (idx, w) in the layout of one EllStage each (null: none):
   // a staged SpMV then moves a whole tile with one bulk copy
   const unsigned char* tiles = nullptr;
+  // rows in difference form (needs a1): (A x)_i = sum_s w_s (x_j - x_i) + a1_i x_i
+  int diff = 0;
 };
 
 template <typename T>
@@ -122,7 +124,8 @@ __device__ __forceinline__ bool index_ok(long long j, long long n, int site, lon
 #endif
 
 // sum_s w[s][i] * x[idx[s][i]] for one or two vectors sharing the stencil,
-// accumulated in the precision of the vectors
+// accumulated in the precision of the vectors (in difference form when
+// op.diff is set, as k_spmv_pc applies those rows)
 template <int K, int NRHS, typename TW, typename TV>
 __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, const TV* const* x,
                                             typename Acc<TV>::t* acc) {
@@ -130,6 +133,22 @@ __device__ __forceinline__ void gather_rows(const KOp<TW, TV>& op, int64_t i, co
 #pragma unroll
   for (int r = 0; r < NRHS; ++r) acc[r] = 0;
   const int k = K > 0 ? K : op.k;
+  if (op.diff) {
+    A xi[NRHS];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) xi[r] = (A)x[r][i];
+#pragma unroll(K > 0 ? K : 1)
+    for (int s = 0; s < k; ++s) {
+      const int j = op.idx[s * op.ld + i];
+      if (K == 0) RBFFD_CHECK(j, op.n, 1, i);
+      const A w = (A)op.w[s * op.ld + i];
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) acc[r] += w * ((A)x[r][j] - xi[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) acc[r] += (A)op.a1[i] * xi[r];
+    return;
+  }
 #pragma unroll(K > 0 ? K : 1)
   for (int s = 0; s < k; ++s) {
     const int j = op.idx[s * op.ld + i];
@@ -984,6 +1003,14 @@ struct ZAcc<float, float> {  // FP32 inner solves: plain FP32 sums
 //   y = A z + kap (A 1) + es mu,   mu = rank-one sum of B v (sc->sum_p / sum_s)
 // WHICH = 0: v = A p^, reduce (rh, v) -> alpha;  WHICH = 1: t = A s^, reduce
 // (t, s), (t, t) -> omega.
+// op.diff (the FP32 rows of the MIXED inner solves): A z = sum_s w_s (z_j - z_i)
+// + a1_i z_i with a1 the FP64 row sums.  Summed directly, FP32 rows of a
+// Laplacian lose the smooth modes: the row sum of the rounded weights is off
+// by about eps32 times the largest weight, against an eigenvalue of order h^2
+// times it (a relative error near 6 % at 1M nodes), which capped every
+// refinement sweep near a 1e-2 reduction.  In difference form a constant
+// operand gives exactly a1_i z_i, and the rounding of each term scales with
+// the differences, smaller by a factor h.
 template <int K, typename TW, typename TV, int WHICH, int DIRECT = 0>
 __global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
     k_spmv_pc(KOp<TW, TV> op, const TV* __restrict__ z, TV* __restrict__ y,
@@ -996,8 +1023,11 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
   const TV kap = (TV)sc->kap[WHICH];
   const TV sig = (TV)(WHICH ? sc->sum_s : sc->sum_p);
   TV d0 = 0, d1 = 0;
-  auto finish_row = [&](int64_t i, TV acc) {
-    const TV yi = acc + kap * op.a1[i] + op.es[i] * sig;
+  // FP32 rows are always in difference form here (the plan sets op.diff
+  // with a1 for every preconditioned FP32 operator); FP64 rows never are
+  constexpr bool dif = std::is_same<TW, float>::value;
+  auto finish_row = [&](int64_t i, TV acc, TV zi) {
+    const TV yi = acc + (dif ? zi + kap : kap) * op.a1[i] + op.es[i] * sig;
     y[i] = yi;
     const TV di = dotv[i];  // rh for WHICH 0, s for WHICH 1
     d0 += di * yi;
@@ -1019,10 +1049,12 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
       const int64_t i = row0 + threadIdx.x;
       if (i < op.n) {
         ZAcc<TW, TV> acc;
+        const TV zi = dif ? z[i] : (TV)0;
 #pragma unroll
         for (int q = 0; q < K; ++q)
-          acc.add(tile->w[q * kTileRows + threadIdx.x], z[tile->idx[q * kTileRows + threadIdx.x]]);
-        finish_row(i, (TV)acc.get());
+          acc.add(tile->w[q * kTileRows + threadIdx.x],
+                  z[tile->idx[q * kTileRows + threadIdx.x]] - zi);
+        finish_row(i, (TV)acc.get(), zi);
       }
     }
   } else {
@@ -1030,12 +1062,13 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
          i += (int64_t)gridDim.x * kThreads) {
       ZAcc<TW, TV> acc;
       const int kk = K > 0 ? K : op.k;
+      const TV zi = dif ? z[i] : (TV)0;
 #pragma unroll(K > 0 ? K : 1)
       for (int q = 0; q < kk; ++q) {
         RBFFD_CHECK(op.idx[q * op.ld + i], op.n, 2, i);
-        acc.add(op.w[q * op.ld + i], z[op.idx[q * op.ld + i]]);
+        acc.add(op.w[q * op.ld + i], z[op.idx[q * op.ld + i]] - zi);
       }
-      finish_row(i, (TV)acc.get());
+      finish_row(i, (TV)acc.get(), zi);
     }
   }
   double vv[NU_] = {(double)d0, (double)d1};
@@ -1124,6 +1157,52 @@ __global__ void __launch_bounds__(kThreads)
   });
 }
 
+// Resumes a preconditioned solve whose right side was replaced between
+// refinement sweeps, keeping its Krylov directions: r = b (the new normalised
+// FP64 residual), x = 0, and beta from (rh, r) and the previous iteration's
+// rho, alpha, omega.  s = (old residual norm) / (new residual norm) carries
+// the old scale to the new one: p and v scale by s, so beta is stored times s
+// and k_update_p forms p = r + beta s (p - omega v) unchanged.  A zero (rh, r)
+// ends the call as a breakdown (status 4), which restarts the method.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_resume(int64_t n, const TV* __restrict__ b, TV* __restrict__ r, TV* __restrict__ x,
+             const TV* __restrict__ rh, KScal* sc, GridReduce gr, double s, double tol2,
+             int maxit) {
+  constexpr int NU_ = 2;
+  __shared__ double sh[NU_ * kThreads];
+  TV prh = 0, prr = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const TV bi = b[i];
+    r[i] = bi;
+    x[i] = 0;
+    prh += rh[i] * bi;
+    prr += bi * bi;
+  }
+  double vv[NU_] = {(double)prh, (double)prr};
+  grid_reduce<NU_>(vv, gr, sh, [&](double* t) {
+    const double rho_new = t[0], rr = t[1], rho_old = sc->rho[0] * s;
+    sc->tol2 = tol2;
+    sc->maxit = maxit;
+    sc->iters = 0;
+    sc->status = 0;
+    sc->stage_err = 0;
+    sc->rr[0] = rr;
+    sc->bb[0] = rr;
+    sc->half[0] = 0;
+    sc->active[1] = 0;
+    const bool ok = isfinite(rr) && rho_new != 0.0 && rho_old != 0.0 && sc->omega[0] != 0.0;
+    if (!ok) sc->status = isfinite(rr) ? 4 : 2;
+    sc->active[0] = (ok && rr > 0.0) ? 1 : 0;
+    if (ok) {
+      sc->beta[0] = (rho_new / rho_old) * (sc->alpha[0] / sc->omega[0]) * s;
+      sc->rho[0] = rho_new;
+    }
+    sc->done = (sc->active[0] && maxit > 0) ? 0 : 1;
+  });
+}
+
 // row sums of an ELL operator in FP64 (A 1)
 template <typename TW>
 __global__ void k_rowsum(int64_t n, int64_t ld, int k, const TW* __restrict__ w,
@@ -1198,30 +1277,31 @@ __global__ void k_addcorr(int64_t n, Vecs<double, NRHS> x, Vecs<float, NRHS> e32
   }
 }
 
-// Initial guess of a pressure solve from the three previous solutions
-// (quadratic extrapolation in time): x <- 3 x - 3 x_prev2 + x_prev3, and the
-// history moves by one step.
-__global__ void k_extrapolate3(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2,
-                               double* __restrict__ x_prev3) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double t = x[i], t2 = x_prev2[i];
-    x[i] = 3.0 * (t - t2) + x_prev3[i];
-    x_prev3[i] = t2;
-    x_prev2[i] = t;
+// Initial guess of a pressure solve by polynomial extrapolation in time
+// through the last ord + 1 solutions: x holds the newest, h[0..] the older
+// ones (newest first), and x <- sum_k (-1)^k C(ord + 1, k + 1) x_{j-k}
+// (ord 1: 2 x - h0; ord 2: 3 x - 3 h0 + h1; ord 3: 4 x - 6 h0 + 4 h1 - h2;
+// error O(dt^(ord+1)) for a smooth solution).  The old x goes to the oldest
+// slot h[kMaxHist - 1], which the caller then takes as the newest.
+constexpr int kMaxHist = 3;  // cubic: measured best on the 1M cavity (8.9 iterations per
+                             // FP64 solve against 14.6 quadratic, 9.3 quartic, 10.2 quintic)
+struct History {
+  double* h[kMaxHist];
+};
+__global__ void k_extrapolate(int64_t n, int ord, double* __restrict__ x, History H) {
+  double c[kMaxHist + 1];
+  double b = ord + 1.0;  // C(ord + 1, k + 1) with alternating signs
+  for (int k = 0; k <= ord; ++k) {
+    c[k] = (k & 1) ? -b : b;
+    b = b * (ord - k) / (k + 2.0);
   }
-}
-
-// The same from two solutions (linear extrapolation): x <- 2 x - x_prev2,
-// keeping x_prev2 as x_prev3 for the next step.
-__global__ void k_extrapolate2(int64_t n, double* __restrict__ x, double* __restrict__ x_prev2,
-                               double* __restrict__ x_prev3) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double t = x[i], t2 = x_prev2[i];
-    x[i] = 2.0 * t - t2;
-    x_prev3[i] = t2;
-    x_prev2[i] = t;
+    const double t0 = x[i];
+    double y = c[0] * t0;
+    for (int k = 1; k <= ord; ++k) y += c[k] * H.h[k - 1][i];
+    x[i] = y;
+    H.h[kMaxHist - 1][i] = t0;
   }
 }
 
@@ -1337,6 +1417,15 @@ struct HelmRhsArgs {
   int cn;    // RBFFD_CN_*
   int proj;  // RBFFD_PROJ_*
   const uint8_t *bcu, *bcv;  // open flows: per-component conditions (null: v_bc for both)
+  // Initial guess of the viscous solves: vord < 0: the right side; else the
+  // extrapolation of order vord through the previous solution (in xu, xv)
+  // and the older ones in hu, hv (newest first), coefficients vc; the
+  // previous solution then goes to the oldest slot.  Rows with a Dirichlet
+  // condition start from their data.
+  int vord = -1;
+  double vc[kMaxHist + 1] = {};
+  double* hu[kMaxHist] = {};
+  double* hv[kMaxHist] = {};
 };
 
 // Stage 2 right side: u* + a D_Lap (u* or u_j) inside, minus dt G0 p~_j for
@@ -1388,8 +1477,24 @@ __global__ void __launch_bounds__(kThreads) k_helm_rhs(HelmRhsArgs a) {
     }
     a.ru[i] = bu;
     a.rv[i] = bv;
-    a.xu[i] = bu;
-    a.xv[i] = bv;
+    double xu = bu, xv = bv;
+    if (a.vord >= 0) {
+      const double pu = a.xu[i], pv = a.xv[i];
+      const bool fu = a.bcu ? a.bcu[i] != RBFFD_BC_DIRICHLET : !a.v_bc[i];
+      const bool fv = a.bcu ? a.bcv[i] != RBFFD_BC_DIRICHLET : !a.v_bc[i];
+      if (fu) {
+        xu = a.vc[0] * pu;
+        for (int q = 1; q <= a.vord; ++q) xu += a.vc[q] * a.hu[q - 1][i];
+      }
+      if (fv) {
+        xv = a.vc[0] * pv;
+        for (int q = 1; q <= a.vord; ++q) xv += a.vc[q] * a.hv[q - 1][i];
+      }
+      a.hu[kMaxHist - 1][i] = pu;
+      a.hv[kMaxHist - 1][i] = pv;
+    }
+    a.xu[i] = xu;
+    a.xv[i] = xv;
   }
 }
 
@@ -1794,10 +1899,15 @@ struct StepPlan {
   double *us = nullptr, *vs = nullptr, *ru = nullptr, *rv = nullptr, *uss = nullptr,
          *vss = nullptr, *pb = nullptr, *px = nullptr;
   int64_t px_step = -1;  // step index whose pressure solve left its solution in px
-  double* pxp = nullptr;   // the pressure solution of the step before px's
-  int64_t pxp_step = -1;   // px_step of pxp's solution when it was current
-  double* pxpp = nullptr;  // the one before that
-  int64_t pxpp_step = -1;
+  // the pressure solutions of the steps before px's, newest first; the first
+  // nhist of them are those of consecutive steps
+  double* pxh[kMaxHist] = {};
+  int nhist = 0;
+  // the viscous solutions (u**, v**) of the steps before, as a ring like pxh
+  double* vhu[kMaxHist] = {};
+  double* vhv[kMaxHist] = {};
+  int vhist = 0, vhead = 0;
+  int hhead = 0;  // pxh[hhead] is the newest, then pxh[hhead + 1], ... (mod kMaxHist)
   float2 *u2 = nullptr, *v2 = nullptr, *us2 = nullptr, *vs2 = nullptr, *uss2 = nullptr,
          *vss2 = nullptr, *pt2 = nullptr, *px2 = nullptr;
   // Krylov work (6 vectors x 2 right sides) in FP64 and FP32
@@ -1810,7 +1920,7 @@ struct StepPlan {
   struct AdjointPlan* adj = nullptr;  // transposed operators, built on first use
   Amg* amg = nullptr;                 // pressure preconditioner (precond = 1)
   double* a1 = nullptr;    // row sums of the FP64 pressure operator
-  float* a1_32 = nullptr;  // row sums of its FP32 copy
+  float* a1_32 = nullptr;  // the same in FP32 (complement of the difference-form FP32 rows)
   // tile records of the pressure and viscous operators the Krylov solves
   // apply (FP32 weights in MIXED precision, FP64 otherwise)
   unsigned char* Lt = nullptr;
@@ -1951,8 +2061,11 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   TRY(palloc(ctx, p, &p->vss, f.N));
   TRY(palloc(ctx, p, &p->pb, f.M));
   TRY(palloc(ctx, p, &p->px, f.M));
-  TRY(palloc(ctx, p, &p->pxp, f.M));
-  TRY(palloc(ctx, p, &p->pxpp, f.M));
+  for (int q = 0; q < kMaxHist; ++q) {
+    TRY(palloc(ctx, p, &p->pxh[q], f.M));
+    TRY(palloc(ctx, p, &p->vhu[q], f.N));
+    TRY(palloc(ctx, p, &p->vhv[q], f.N));
+  }
   for (int a = 0; a < 7; ++a)
     for (int b = 0; b < 2; ++b) TRY(palloc(ctx, p, &p->kw64[a][b], nmax));
   TRY(palloc(ctx, p, &p->sc, 1));
@@ -2049,11 +2162,9 @@ int build_plan(rbffd_ctx* ctx, const rbffd_flow& f, StepPlan** out, cudaStream_t
   }
   if (p->mix) {
     TRY(to32(ctx, p, p->Lw, np, &p->Lw32, st));
-    if (f.precond) {
-      k_rowsum<float><<<p->grid, kThreads, 0, st>>>(f.M, f.ld_p, p->kL, p->Lw32, p->kw64[0][0]);
-      TRY(check_cuda(ctx, cudaGetLastError(), "row sums"));
-      TRY(to32(ctx, p, p->kw64[0][0], f.M, &p->a1_32, st));
-    }
+    // the FP32 pressure rows are applied in difference form with the FP64
+    // row sums (near zero) as their diagonal complement (see k_spmv_pc)
+    if (f.precond) TRY(to32(ctx, p, p->a1, f.M, &p->a1_32, st));
     TRY(to32(ctx, p, p->es, f.M, &p->es32, st));
     TRY(to32(ctx, p, p->Hw, nv, &p->Hw32, st));
     if (p->open) TRY(to32(ctx, p, p->Hw_v, nv, &p->Hw32_v, st));
@@ -2114,6 +2225,9 @@ struct SolveResult {
   double relres = 0.0;
   int status = 0;  // as KScal::status
   bool converged = false;
+  // a preconditioned solve that converged without breakdown on a full
+  // iteration: k_resume can carry its directions to a new right side
+  bool resumable = false;
 };
 
 // Add up the durations of the recorded SpMV launches (the stream is idle here).
@@ -2279,7 +2393,7 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
              cudaStream_t st, bool prof = false, uint32_t seed_base = 0,
-             const Amg* pc = nullptr, bool x_zero = false) {
+             const Amg* pc = nullptr, bool x_zero = false, double resume = 0.0) {
   Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
@@ -2363,14 +2477,28 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   for (int restart = 0;; ++restart) {
     // the caller's x0 = 0 holds only until the first restart
     const bool xz = x_zero && restart == 0;
-    if (RANK1 && !xz) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx, op.rdot);
-    k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
-                                                    tol * tol, maxit - total,
-                                                    (restart || seed_base)
-                                                        ? 0x51ED27u + 977u * seed_base + restart
-                                                        : 0u,
-                                                    pcc, xz ? 1 : 0);
-    P->launches += (RANK1 && !xz ? 2 : 1) + (pc ? vc_launches : 0);
+    bool resumed = false;
+    if constexpr (NRHS == 1 && RANK1) {
+      // resume > 0: the previous call's directions carry over (k_resume)
+      if (pc && restart == 0 && resume > 0.0) {
+        k_resume<TV><<<G, kThreads, 0, st>>>(op.n, B.v[0], R.v[0], X.v[0], RH.v[0], P->sc, P->gr,
+                                             resume, tol * tol, maxit - total);
+        k_update_p<NRHS, RANK1><<<G, kThreads, 0, st>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
+                                                       pcc);
+        P->launches += 2 + vc_launches;
+        resumed = true;
+      }
+    }
+    if (!resumed) {
+      if (RANK1 && !xz) k_sum<TV><<<G, kThreads, 0, st>>>(x[0], op.n, P->gr, sigx, op.rdot);
+      k_init<K, NRHS, RANK1><<<G, kThreads, 0, st>>>(op, X, B, R, RH, PP, sigx, P->sc, P->gr,
+                                                      tol * tol, maxit - total,
+                                                      (restart || seed_base)
+                                                          ? 0x51ED27u + 977u * seed_base + restart
+                                                          : 0u,
+                                                      pcc, xz ? 1 : 0);
+      P->launches += (RANK1 && !xz ? 2 : 1) + (pc ? vc_launches : 0);
+    }
     if (pc) vcycle<TV>(P, pc, PP.v[0], 0, zbuf<TV>(pc, 0), st);
     int rc = check_cuda(ctx, cudaGetLastError(), "bicgstab init");
     if (rc) return rc;
@@ -2388,6 +2516,9 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
       rc = check_cuda(ctx, cudaStreamSynchronize(st), "bicgstab sync");
       if (rc) return rc;
       if (prof) collect_events(P);
+      if (trace_on())
+        fprintf(stderr, "[rbffd]   %s iters=%d rr/bb=%.3e\n", sizeof(TV) == 8 ? "fp64" : "fp32",
+                h->iters, h->bb[0] > 0 ? h->rr[0] / h->bb[0] : h->rr[0]);
       if (h->done || issued >= budget) break;
       // Next chunk: the iterations that the residual's rate over the last
       // chunk predicts are still needed, plus one (doubling while it has no rate).
@@ -2504,6 +2635,7 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     res->status = h->status;
     res->relres = worst;
     res->converged = conv;
+    res->resumable = pc != nullptr && conv && h->status == 0 && !h->half[0];
     if (trace_on())
       fprintf(stderr, "[rbffd] bicgstab %s nrhs=%d restart=%d iters=%d relres=%.3e status=%d\n",
               sizeof(TV) == 8 ? "fp64" : "fp32", NRHS, restart, h->iters, worst, h->status);
@@ -2583,6 +2715,7 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
   const int G = P->grid;
   int used = 0, failures = 0, retries = 0;
   double prev_rel = INFINITY, last_nrm[2] = {0, 0};
+  bool resumable = false;  // the last inner solve's directions can carry over
   res->iters = 0;
   res->status = 0;
   *sweeps = 0;
@@ -2618,6 +2751,7 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
       rc = check_cuda(ctx, cudaGetLastError(), "undo correction");
       if (rc) return rc;
       ++retries;
+      resumable = false;
       if (++failures > 6 || used >= maxit) {
         res->relres = prev_rel;
         res->converged = false;
@@ -2639,11 +2773,17 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     const double i1 = NRHS > 1 && nrm[NRHS - 1] > 0 ? 1.0 / nrm[NRHS - 1] : 0.0;
     k_to32<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, R32, E32, i0, i1);
     P->launches += 2;  // with the correction below
+    // A preconditioned inner solve resumes the previous sweep's Krylov
+    // directions on the new residual (k_resume) instead of starting afresh:
+    // the sweeps then converge at nearly the rate of one unbroken solve.
+    const double resume =
+        resumable && nrm[0] > 0.0 && last_nrm[0] > 0.0 ? last_nrm[0] / nrm[0] : 0.0;
     SolveResult inner;
     rc = bicgstab<K, NRHS, RANK1, float, float>(ctx, P, op32, E32.v, R32.v, P->kw32, inner_tol,
                                                 maxit - used, &inner, st, prof, retries,
-                                                RANK1 ? P->amg : nullptr, true);
+                                                RANK1 ? P->amg : nullptr, true, resume);
     if (rc) return rc;
+    resumable = inner.resumable;
     used += inner.iters > 0 ? inner.iters : 1;
     res->iters += inner.iters;
     last_nrm[0] = nrm[0];
@@ -2692,6 +2832,7 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   KOp<double, double> L64{P->Lidx, P->Lw, f.ld_p, f.M, P->kL, 0, P->es, nullptr, P->a1};
   KOp<float, float> H32{f.vv_idx, P->Hw32, f.ld_v, f.N, k, 1, nullptr, nullptr};
   KOp<float, float> L32{P->Lidx, P->Lw32, f.ld_p, f.M, P->kL, 0, P->es32, nullptr, P->a1_32};
+  L32.diff = P->a1_32 ? 1 : 0;
   const bool proj = P->proj != 0;
   if (f.precond && !proj) (MIX ? L32.tiles : L64.tiles) = P->Lt;
   (MIX ? H32.tiles : H64.tiles) = P->Ht;
@@ -2712,6 +2853,25 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                    f.v_ny, gu,     gv,     a,        f.dt,   f.km_mode, P->ru, P->rv,
                    P->uss, P->vss, s->u,   s->v,     P->u2,  P->v2, f.cn_form, P->proj,
                    f.v_bcu, f.v_bcv};
+    // the viscous solves start from the extrapolation of the previous steps'
+    // solutions when this plan made them (P->px_step == s->j), as the
+    // pressure solve does
+    if (P->px_step == s->j) {
+      ha.vord = std::min(P->vhist, kMaxHist);
+      double b = ha.vord + 1.0;  // C(vord + 1, q + 1) with alternating signs
+      for (int q = 0; q <= ha.vord; ++q) {
+        ha.vc[q] = (q & 1) ? -b : b;
+        b = b * (ha.vord - q) / (q + 2.0);
+      }
+      for (int q = 0; q < kMaxHist; ++q) {
+        ha.hu[q] = P->vhu[(P->vhead + q) % kMaxHist];
+        ha.hv[q] = P->vhv[(P->vhead + q) % kMaxHist];
+      }
+      P->vhead = (P->vhead + kMaxHist - 1) % kMaxHist;
+      P->vhist = std::min(P->vhist + 1, kMaxHist);
+    } else {
+      P->vhist = 0;
+    }
     k_helm_rhs<K, MIX><<<G, kThreads, 0, st>>>(ha);
     P->launches += 2 + (MIX ? 2 : 0) + 4 + (MIX ? 1 : 0);  // stage kernels of this step
     int rc = check_cuda(ctx, cudaGetLastError(), "stage 1-2 kernels");
@@ -2723,6 +2883,15 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     // The viscous operator is well conditioned: its FP32 inner solves go to the
     // square of the inner tolerance (each FP64 residual of the 3M-row, two-sided
     // solve costs more than a few extra FP32 iterations).
+    // In the FP64 path of a closed flow the viscous solves go 1000 times below
+    // the tolerance (not below 1e-13; tolerances under 1e-13 are kept): the
+    // error of u** enters the pressure right side through the divergence, and
+    // what the extrapolated pressure guess cannot predict costs pressure
+    // iterations (on the 1M cavity 25.5 per step at the tolerance, 9.0 at 1e-4
+    // of it, each viscous solve 2 iterations from its extrapolated guess).  In
+    // MIXED precision the FP32 explicit stages leave more than that in the
+    // right side, so the tolerance stays.
+    const double vtol = (MIX || P->open || f.tol < 1e-13) ? f.tol : std::max(f.tol * 1e-3, 1e-13);
     if (P->open) {
       // per-component operators: one solve each
       SolveResult h2[2];
@@ -2744,10 +2913,10 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
       if (!h2[1].converged || h2[1].status == 2) hr.status = h2[1].status;
       sweeps = sw[0] + sw[1];
     } else if (MIX) {
-      rc = refine<K, 2, false>(ctx, P, H64, H32, hx, hb, f.tol, f.inner_tol * f.inner_tol,
+      rc = refine<K, 2, false>(ctx, P, H64, H32, hx, hb, vtol, f.inner_tol * f.inner_tol,
                                f.max_iter, &hr, &sweeps, st);
     } else {
-      rc = bicgstab<K, 2, false, double, double>(ctx, P, H64, hx, hb, P->kw64, f.tol, f.max_iter,
+      rc = bicgstab<K, 2, false, double, double>(ctx, P, H64, hx, hb, P->kw64, vtol, f.max_iter,
                                                  &hr, st);
     }
     if (rc) return rc;
@@ -2757,7 +2926,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
       stats->refinements += sweeps;
     }
     if (hr.status == 2) return set_error(ctx, RBFFD_ERR_NONFINITE, "non-finite viscous solve");
-    if (!hr.converged)
+    // a solve short of the tighter target but within the tolerance is accepted
+    if (!hr.converged && !(hr.relres <= f.tol))
       return set_error(ctx, RBFFD_ERR_NOT_CONVERGED,
                        "viscous solve: relative residual %.3e after %d iterations (status %d)",
                        hr.relres, hr.iters, hr.status);
@@ -2771,11 +2941,10 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     DivArgs da{f.M,    f.ld_p,  k,      f.pv_idx, f.pv_dx,  f.pv_dy,      P->uss,
                P->vss, P->uss2, P->vss2, f.p_bc,  P->scale, 1.0 / f.dt, P->pb, P->proj};
     k_divergence<K, false><<<G, kThreads, 0, st>>>(da);
-    // Initial guess: the quadratic extrapolation of the three previous steps'
-    // solutions when all are at hand, the linear one of two, else the previous
-    // solution, else the state's p~.  Any guess leaves the converged solution
-    // the same; a better one saves iterations (p~ changes smoothly from step
-    // to step, and the quadratic guess is off by O(dt^3)).
+    // Initial guess: the extrapolation in time through the previous steps'
+    // solutions (up to cubic), else the state's p~.  Any guess
+    // leaves the converged solution the same; a better one saves iterations
+    // (p~ changes smoothly from step to step).
     if (P->px_step != s->j) {
       // the exact projection solves for the increment of p~: start from zero
       rc = proj ? check_cuda(ctx, cudaMemsetAsync(P->px, 0, sizeof(double) * f.M, st), "zero start")
@@ -2783,25 +2952,16 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                                                   cudaMemcpyDeviceToDevice, st),
                              "warm start");
       if (rc) return rc;
-      P->pxp_step = -1;
-      P->pxpp_step = -1;
+      P->nhist = 0;
     } else {
-      if (P->pxp_step == s->j - 1 && P->pxpp_step == s->j - 2) {
-        k_extrapolate3<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp, P->pxpp);
-        rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
-        P->pxpp_step = s->j - 1;
-      } else if (P->pxp_step == s->j - 1) {
-        k_extrapolate2<<<G, kThreads, 0, st>>>(f.M, P->px, P->pxp, P->pxpp);
-        rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
-        P->pxpp_step = s->j - 1;
-      } else {
-        rc = check_cuda(ctx, cudaMemcpyAsync(P->pxp, P->px, sizeof(double) * f.M,
-                                             cudaMemcpyDeviceToDevice, st),
-                        "previous solution");
-        P->pxpp_step = -1;
-      }
+      const int ord = std::min(P->nhist, kMaxHist);
+      History H;
+      for (int q = 0; q < kMaxHist; ++q) H.h[q] = P->pxh[(P->hhead + q) % kMaxHist];
+      k_extrapolate<<<G, kThreads, 0, st>>>(f.M, ord, P->px, H);
+      rc = check_cuda(ctx, cudaGetLastError(), "extrapolation");
       if (rc) return rc;
-      P->pxp_step = s->j;
+      P->hhead = (P->hhead + kMaxHist - 1) % kMaxHist;  // the recycled slot is the newest
+      P->nhist = std::min(P->nhist + 1, kMaxHist);
     }
     double* px[1] = {P->px};
     const double* pbv[1] = {P->pb};
