@@ -36,7 +36,7 @@ UNIT = "steps/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1000, help="P-lattice side (n x n P-nodes)")
@@ -760,27 +760,33 @@ def ensemble_record(R, args, hbm, peak_kind):
         k = 28
         bytes_launch = nd.M * (k * 4 + k * 4) + nd.M * E * (4 + 4)
         achieved = bytes_launch / (per_ms * 1e-3) / 1e9 if per_ms > 0 else None
-        # the same members one at a time
-        seq_ms, seq_iters, nm = 0.0, 0, min(4, E)
+        # the same members one at a time, in the ensemble's precision (MIXED)
+        # and in FP64 (the faster single-flow path)
+        nm = min(4, E)
         g1 = torch.zeros(nd.N, dtype=torch.float64, device="cuda")
         topd = torch.as_tensor(top, device="cuda")
-        for e in range(nm):
-            fl1 = R.Flow(N=flow.N, M=flow.M, tensors=flow.tensors, Re=Re[e], dt=dt,
-                         precision=R.PREC_MIXED, tol=args.tol, inner_tol=args.inner_tol,
-                         max_iter=args.max_iter)
-            s1 = R.State.zeros(fl1)
-            g1.zero_()
-            g1[topd] = float(lid[e])
-            g2 = torch.zeros_like(g1)
-            R.step(ctx, fl1, s1, g1, g2, max(args.warmup, 3))
-            torch.cuda.synchronize()
-            e0.record(stream)
-            r1 = R.step(ctx, fl1, s1, g1, g2, steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            seq_ms += e0.elapsed_time(e1)
-            seq_iters += r1["poisson_iters"]
-        seq_rate = nm * steps / (seq_ms * 1e-3)
+        seq = {}
+        for pname, prec in (("mixed", R.PREC_MIXED), ("fp64", R.PREC_FP64)):
+            seq_ms, seq_iters = 0.0, 0
+            for e in range(nm):
+                fl1 = R.Flow(N=flow.N, M=flow.M, tensors=flow.tensors, Re=Re[e], dt=dt,
+                             precision=prec, tol=args.tol, inner_tol=args.inner_tol,
+                             max_iter=args.max_iter)
+                s1 = R.State.zeros(fl1)
+                g1.zero_()
+                g1[topd] = float(lid[e])
+                g2 = torch.zeros_like(g1)
+                R.step(ctx, fl1, s1, g1, g2, max(args.warmup, 3))
+                torch.cuda.synchronize()
+                e0.record(stream)
+                r1 = R.step(ctx, fl1, s1, g1, g2, steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                seq_ms += e0.elapsed_time(e1)
+                seq_iters += r1["poisson_iters"]
+            seq[pname] = (nm * steps / (seq_ms * 1e-3), seq_iters / (nm * steps))
+        seq_rate = seq["mixed"][0]
+        seq_iters_step = seq["mixed"][1]
         rate = E * steps / (ms * 1e-3)
         return {"members": E, "M": nd.M, "N": nd.N, "dt": dt, "steps": steps,
                 "re_range": [min(Re), max(Re)],
@@ -790,8 +796,11 @@ def ensemble_record(R, args, hbm, peak_kind):
                 "helm_iters_per_step": s["helm_iters"] / steps,
                 "launches_per_step": s["launches"] / steps,
                 "sequential_steps_per_s": seq_rate,
-                "sequential_poisson_iters_per_step": seq_iters / (nm * steps),
+                "sequential_poisson_iters_per_step": seq_iters_step,
                 "speedup_vs_sequential": rate / seq_rate,
+                "sequential_fp64_steps_per_s": seq["fp64"][0],
+                "sequential_fp64_poisson_iters_per_step": seq["fp64"][1],
+                "speedup_vs_best_sequential": rate / max(seq_rate, seq["fp64"][0]),
                 "spmm_roofline": {"kernel": "e_spmv_v (batched pressure SpMV)", "bound": "hbm",
                                   "bytes_per_member_row": (k * 8) / E + 8,
                                   "us_per_launch": per_ms * 1e3, "achieved": achieved,
@@ -799,7 +808,8 @@ def ensemble_record(R, args, hbm, peak_kind):
                                   "frac": achieved / hbm if achieved else None},
                 "how": "CUDA events around the timed steps after warm-up; the same flows one "
                        "at a time through rbffd_step (first four members, each with its own "
-                       "step plan) give the sequential rate; MIXED precision, solves to "
+                       "step plan) give the sequential rates, in MIXED (the ensemble's "
+                       "precision) and in FP64; MIXED precision, solves to "
                        f"{args.tol:g}; the SpMV timed alone in 20 back-to-back launches"}
     except R.RbffdError as e:
         return {"members": E, "error": str(e)[:300]}

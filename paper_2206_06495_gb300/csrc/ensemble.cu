@@ -290,6 +290,32 @@ __global__ void __launch_bounds__(kT)
   }
 }
 
+// Initial guess of a solve by extrapolation in time from a ring of earlier
+// solutions h[0] (the previous step's), h[1], ... (newest first):
+// x = sum_k (-1)^k C(ord + 1, k + 1) h[k], the polynomial of degree ord through
+// the last ord + 1 solutions at the next step.  Rows with skip[i / per] set
+// (Dirichlet rows) keep the value the caller wrote (their data).
+constexpr int kEHist = 4;  // the previous solution and three older ones: cubic
+struct EHist {
+  const double* h[kEHist];
+};
+__global__ void e_extrapolate(int64_t n, int ord, EHist H, const uint8_t* __restrict__ skip,
+                              int per, double* __restrict__ x) {
+  double c[kEHist];
+  double b = ord + 1.0;  // C(ord + 1, k + 1) with alternating signs
+  for (int k = 0; k <= ord; ++k) {
+    c[k] = (k & 1) ? -b : b;
+    b = b * (ord - k) / (k + 2.0);
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (skip && skip[i / per]) continue;
+    double y = 0.0;
+    for (int k = 0; k <= ord; ++k) y += c[k] * H.h[k][i];
+    x[i] = y;
+  }
+}
+
 __global__ void e_split(int64_t n, const double* __restrict__ x, float2* __restrict__ x2) {
   for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
     x2[i] = split2e(x[i]);
@@ -812,6 +838,13 @@ struct EnsPlan {
   // batched V-cycle work per level (r, x) and the coarse r, z
   float* lr[kAmgMaxLevels + 1] = {};
   float* lx[kAmgMaxLevels + 1] = {};
+  // rings of earlier solutions for the initial guesses (newest at index
+  // head): viscous (C columns) and pressure (E columns); n*: how many hold
+  // solutions of consecutive steps ending at the state's previous step
+  double* vh[kEHist] = {};
+  double* ph[kEHist] = {};
+  int nvh = 0, nph = 0, hv = 0, hp = 0;
+  int64_t last_j = -1;  // the state's step index after this plan's last step
   EScal* sc = nullptr;
   EScal* sc_t = nullptr;  // scalars of the timed SpMV launches (profile)
   EReduce rd{};
@@ -1044,6 +1077,10 @@ int ens_build(rbffd_ctx* ctx, const rbffd_flow& f, int E, EnsPlan** out, cudaStr
   TRY(ealloc(ctx, p, &p->xv, nW));
   TRY(ealloc(ctx, p, &p->pb, nP));
   TRY(ealloc(ctx, p, &p->px, nP));
+  for (int q = 0; q < kEHist; ++q) {
+    TRY(ealloc(ctx, p, &p->vh[q], nW));
+    TRY(ealloc(ctx, p, &p->ph[q], nP));
+  }
   TRY(ealloc(ctx, p, &p->u2, nV));
   TRY(ealloc(ctx, p, &p->v2, nV));
   TRY(ealloc(ctx, p, &p->us2, nV));
@@ -1258,14 +1295,38 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
                                                 cudaMemcpyHostToDevice, st), "aE");
   if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(st), "a sync");
   if (rc) return rc;
-  const int64_t nV = f.N * E, nP = f.M * E;
+  const int64_t nV = f.N * E, nP = f.M * E, nW = f.N * C;
   e_split<<<G, kT, 0, st>>>(nV, s->u, P->u2);
   e_split<<<G, kT, 0, st>>>(nV, s->v, P->v2);
   e_split<<<G, kT, 0, st>>>(nP, s->pt, P->pt2);
   const int64_t l0 = P->launches;
   EOp H{f.vv_idx, f.ld_v, f.N, k, 1, P->aV32, nullptr, nullptr};
   EOp L{P->Lidx, f.ld_p, f.M, k, 0, nullptr, P->es32, P->a1_32};
+  // push x (a solve's solution of the state's previous step) into a ring of
+  // earlier solutions; returns the order of the extrapolation the ring allows
+  auto push = [&](double* const* ring, int* head, int* count, const double* x, int64_t n) {
+    const int slot = (*head + kEHist - 1) % kEHist;
+    int r = check_cuda(ctx, cudaMemcpyAsync(ring[slot], x, sizeof(double) * n,
+                                            cudaMemcpyDeviceToDevice, st),
+                       "solution history");
+    *head = slot;
+    *count = std::min(*count + 1, kEHist);
+    return r;
+  };
+  auto ring_of = [&](double* const* ring, int head) {
+    EHist H;
+    for (int q = 0; q < kEHist; ++q) H.h[q] = ring[(head + q) % kEHist];
+    return H;
+  };
   for (int32_t step = 0; step < n_steps; ++step) {
+    // the solves start from the extrapolation of their previous solutions
+    // while this plan made the state's previous steps
+    const bool hist = P->last_j == s->j;
+    if (!hist) P->nvh = P->nph = 0;
+    if (hist) {
+      rc = push(P->vh, &P->hv, &P->nvh, P->xv, nW);
+      if (rc) return rc;
+    }
     EK(e_convect, G, f.N, f.ld_v, k, E, f.vv_idx, P->vv_dx32, P->vv_dy32, s->u, s->v,
                                 P->u2, P->v2, s->cu_prev, s->cv_prev, P->us, P->vs, P->us2,
                                 P->vs2, f.dt, s->j == 0 ? 1 : 0);
@@ -1274,6 +1335,10 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
                                  f.vp_idx, P->vp_dx32, P->vp_dy32, P->pt2, f.v_bc, f.v_nx,
                                  f.v_ny, gu, gv, P->aE, f.dt, f.km_mode, P->rhs, P->xv);
     P->launches += 2;
+    if (P->nvh > 0) {
+      e_extrapolate<<<G, kT, 0, st>>>(nW, P->nvh - 1, ring_of(P->vh, P->hv), f.v_bc, C, P->xv);
+      P->launches += 1;
+    }
     rc = check_cuda(ctx, cudaGetLastError(), "ensemble stages 1-2");
     if (rc) return rc;
     ESolve hr;
@@ -1290,9 +1355,16 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
                        "ensemble viscous solve: relative residual %.3e", hr.relres);
     EK(e_divergence, G, f.M, f.ld_p, k, E, f.pv_idx, f.pv_dx, f.pv_dy, P->xv, f.p_bc,
                                    P->scale, 1.0 / f.dt, P->pb);
-    rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * nP,
-                                         cudaMemcpyDeviceToDevice, st), "warm start");
-    if (rc) return rc;
+    if (hist) {
+      rc = push(P->ph, &P->hp, &P->nph, P->px, nP);
+      if (rc) return rc;
+      e_extrapolate<<<G, kT, 0, st>>>(nP, P->nph - 1, ring_of(P->ph, P->hp), nullptr, 1, P->px);
+      P->launches += 1;
+    } else {
+      rc = check_cuda(ctx, cudaMemcpyAsync(P->px, s->pt, sizeof(double) * nP,
+                                           cudaMemcpyDeviceToDevice, st), "warm start");
+      if (rc) return rc;
+    }
     ESolve pr;
     rc = ens_refine(ctx, P, L, P->Lw, P->Lw32, E, P->amg != nullptr, P->px, P->pb, f.tol,
                     f.inner_tol, f.max_iter, &pr, st);
@@ -1316,6 +1388,7 @@ int ensemble_run(rbffd_ctx* ctx, const rbffd_flow* fp, int E, const double* Re, 
     rc = check_cuda(ctx, cudaGetLastError(), "ensemble stage 3");
     if (rc) return rc;
     s->j += 1;
+    P->last_j = s->j;
     if (stats) stats->steps += 1;
   }
   rc = check_cuda(ctx, cudaStreamSynchronize(st), "ensemble sync");
