@@ -2453,11 +2453,13 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
   }
   // Pressure SpMVs of the preconditioned solve: FP32 operators stage 256-row
   // tiles (48 us per launch at 1M rows, against 50-61 us with direct loads at
-  // 4-8 blocks per SM); FP64 operators load directly at 6 blocks per SM
-  // (91.5 against 97 us: an FP64 tile leaves room for two blocks per SM).
-  constexpr int kPcDirect = std::is_same<TW, double>::value ? 6 : 0;
+  // 4-8 blocks per SM); FP64 operators load directly at 4 blocks per SM, 64
+  // registers a thread for the gathers in flight (69.3 us at 1M rows, against
+  // 70.2, 92.4 and 72.2 at 3, 6 and 8 blocks per SM and 97 staged: an FP64 tile
+  // leaves room for two blocks per SM).
+  constexpr int kPcDirect = std::is_same<TW, double>::value ? 4 : 0;
   const int Gd = (int)std::max<int64_t>(
-      1, std::min<int64_t>((op.n + kThreads - 1) / kThreads, (int64_t)sm_count() * 6));
+      1, std::min<int64_t>((op.n + kThreads - 1) / kThreads, (int64_t)sm_count() * kPcDirect));
   auto spmv_pc = [&](auto W, cudaStream_t s, const TV* z, TV* y, const TV* dv, KScal* scp,
                      int* wf) {
     constexpr int WH = decltype(W)::value;
