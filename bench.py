@@ -180,18 +180,29 @@ def measured_peaks():
 # helpers and the kernel itself (step.cu, between these markers).  Its hash
 # keys the committed DRAM-traffic capture, so that a change to the kernel, and
 # only to the kernel, retires the counters.
-SPMV_SOURCE_MARKERS = (
-    ("// ------------------------------------------------ staged ELL tiles (bulk copies)",
-     "// ----------------------------------------------------------- Krylov kernels"),
-    ("// Preconditioned-solve SpMVs with the operand",
-     "// x += alpha (zp + kap_p) + omega (zs + kap_s)"),
-)
+SPMV_SOURCE_MARKERS = {
+    # the pressure SpMV: the tile-staging helpers and k_spmv_pc
+    "k_spmv_pc": (
+        ("// ------------------------------------------------ staged ELL tiles (bulk copies)",
+         "// ----------------------------------------------------------- Krylov kernels"),
+        ("// Preconditioned-solve SpMVs with the operand",
+         "// x += alpha (zp + kap_p) + omega (zs + kap_s)"),
+    ),
+    # the viscous SpMV (direct loads): the row gather and k_spmv_p
+    "k_spmv_p": (
+        ("// sum_s w[s][i] * x[idx[s][i]] for one or two vectors sharing the stencil,",
+         "// ------------------------------------------------ staged ELL tiles (bulk copies)"),
+        ("// v = A p ; reduce (rh, v).", "// s = r - alpha v ; reduce (s, s) and sum(s)"),
+    ),
+}
 
 
-def spmv_source_sha() -> str:
+def spmv_source_sha(kernel_key: str = "k_spmv_pc") -> str:
+    """Fingerprint of the source of the kernel a traffic record belongs to."""
+    family = "k_spmv_pc" if kernel_key.startswith("k_spmv_pc") else "k_spmv_p"
     src = open(os.path.join(ROOT, "paper_2206_06495_gb300", "csrc", "step.cu")).read()
     h = hashlib.sha256()
-    for a, b in SPMV_SOURCE_MARKERS:
+    for a, b in SPMV_SOURCE_MARKERS[family]:
         i = src.index(a)
         h.update(src[i:src.index(b, i)].encode())
     return h.hexdigest()[:16]
@@ -202,7 +213,7 @@ def profiled_traffic(kernel_key: str, rows: int):
     to `rows`, or None when the kernel's source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
-        sha = spmv_source_sha()
+        sha = spmv_source_sha(kernel_key)
         for line in open(path):
             line = line.split("#")[0].split()
             if len(line) >= 4 and line[0] == kernel_key and line[3] == sha:
@@ -439,6 +450,8 @@ def run_ours(args):
         res[name]["spmv_ms"], res[name]["spmv_launches"] = s["spmv_ms"], s["spmv_launches"]
         res[name]["spmv_batch_ms"] = s["spmv_batch_ms"]
         res[name]["spmv_batch_launches"] = s["spmv_batch_launches"]
+        res[name]["vspmv_batch_ms"] = s["vspmv_batch_ms"]
+        res[name]["vspmv_batch_launches"] = s["vspmv_batch_launches"]
         res[name]["state"] = st
         # End to end, on the same steps: a second context takes the same steps
         # from rest (the path is deterministic, so it reaches the same state
@@ -633,6 +646,45 @@ def run_ours(args):
     in_step = (nd.M * bytes_row / (in_step_ms * 1e-3) / 1e9
                if r["spmv_launches"] > 0 and in_step_ms > 0 else None)
     traffic = profiled_traffic(key, nd.M)
+    pres_roof = {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                 "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                 "traffic": traffic,
+                 "bytes_per_row": bytes_row, "fused_bytes_per_row": fused,
+                 "frac_with_fused": ((achieved * (bytes_row + fused) / bytes_row) / hbm
+                                     if achieved else None),
+                 "rows": nd.M, "peak_kind": peak_kind,
+                 "launches_timed": r["spmv_batch_launches"],
+                 "us_per_launch": per_launch_ms * 1e3,
+                 "timing": "CUDA events around 20 back-to-back launches of this kernel on "
+                           "the operator and vectors of each pressure solve of one "
+                           "profiled step right after the timed steps",
+                 "in_step": {"us_per_launch": in_step_ms * 1e3, "achieved": in_step,
+                             "frac": in_step / hbm if in_step else None,
+                             "launches_timed": r["spmv_launches"],
+                             "timing": "external event-record graph nodes around every "
+                                       "launch inside the profiled step's solves"}}
+    # the viscous SpMV (k_spmv_p, two right sides, FP64, direct loads): the
+    # largest single kernel of the FP64 step (its launch list is in
+    # profiles/step_launches_fp64_cavity1m.md); algorithmic bytes of a row: k
+    # indices and k weights once for both right sides, each operand read once
+    # and each output written (368 B), plus the fused dot-product partner of
+    # each right side
+    roofline = pres_roof
+    if head == "fp64" and r.get("vspmv_batch_launches", 0) > 0 and r["vspmv_batch_ms"] > 0:
+        vrow, vfused = 12 * k + 2 * (8 + 8), 2 * 8
+        v_ms = r["vspmv_batch_ms"] / r["vspmv_batch_launches"]
+        v_ach = nd.N * vrow / (v_ms * 1e-3) / 1e9
+        roofline = {"kernel": "k_spmv_p_fp64_2rhs", "bound": "hbm", "achieved": v_ach,
+                    "peak": hbm, "unit": "GB/s", "frac": v_ach / hbm,
+                    "traffic": profiled_traffic("k_spmv_p_fp64_2rhs", nd.N),
+                    "bytes_per_row": vrow, "fused_bytes_per_row": vfused,
+                    "frac_with_fused": v_ach * (vrow + vfused) / vrow / hbm,
+                    "rows": nd.N, "peak_kind": peak_kind,
+                    "launches_timed": r["vspmv_batch_launches"], "us_per_launch": v_ms * 1e3,
+                    "timing": "CUDA events around 20 back-to-back launches of this kernel on "
+                              "the operator and vectors of each viscous solve of one "
+                              "profiled step right after the timed steps",
+                    "pressure_spmv": pres_roof}
     iters_ok = r.get("e2e_same_steps")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -643,7 +695,8 @@ def run_ours(args):
                                f"P-lattice (M={nd.M}, N={nd.N}), (n,m,q)=(28,7,3), "
                                f"dt={args.dt:g}, timed after {args.spinup} spin-up and "
                                f"{args.warmup} warm-up steps from rest, pressure/viscous solves "
-                               f"to {args.tol:g} relative residual",
+                               f"to {args.tol:g} relative residual (the FP64 path's viscous "
+                               f"solves to 1e-3 of it, not below 1e-13)",
                    "precision": head, "parallelism": f"replicas{world}",
                    "spinup_steps": args.spinup,
                    "l2": "working set (operators ~7 GB) exceeds L2; no flush needed"},
@@ -659,23 +712,7 @@ def run_ours(args):
                        "steps again through rbffd_step with wall data copied in from pinned "
                        "host memory and u, v copied out every step; same_steps: equal "
                        "pressure iteration counts step by step"},
-        "roofline": {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-                     "traffic": traffic,
-                     "bytes_per_row": bytes_row, "fused_bytes_per_row": fused,
-                     "frac_with_fused": ((achieved * (bytes_row + fused) / bytes_row) / hbm
-                                         if achieved else None),
-                     "rows": nd.M, "peak_kind": peak_kind,
-                     "launches_timed": r["spmv_batch_launches"],
-                     "us_per_launch": per_launch_ms * 1e3,
-                     "timing": "CUDA events around 20 back-to-back launches of this kernel on "
-                               "the operator and vectors of each pressure solve of one "
-                               "profiled step right after the timed steps",
-                     "in_step": {"us_per_launch": in_step_ms * 1e3, "achieved": in_step,
-                                 "frac": in_step / hbm if in_step else None,
-                                 "launches_timed": r["spmv_launches"],
-                                 "timing": "external event-record graph nodes around every "
-                                           "launch inside the profiled step's solves"}},
+        "roofline": roofline,
         "spmv": spmv,
         "weights": weights,
         "sweep": sweep,

@@ -348,6 +348,10 @@ typedef struct rbffd_stats {
   double spmv_batch_ms;     /* profile: their summed durations, milliseconds  */
   double wall_flux;         /* RBFFD_PROJ_EXACT: wall-normal velocity mu dt of the
                                last step; 0 otherwise                          */
+  int64_t vspmv_batch_launches; /* profile, FP64 closed flows: the viscous SpMV (two
+                                   right sides) relaunched back to back after each
+                                   viscous solve (20 per solve)                 */
+  double vspmv_batch_ms;    /* profile: their summed durations, milliseconds  */
 } rbffd_stats;
 
 /*

@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(kThreads)
 
 // v = A p ; reduce (rh, v).  K > 0: rows come in staged tiles (dynamic shared
 // memory holds one EllStage); K == 0: rows are read directly.
-template <int K, int NRHS, bool RANK1, typename TW, typename TV>
-__global__ void __launch_bounds__(kThreads)
+template <int K, int NRHS, bool RANK1, typename TW, typename TV, int DIRECT = 0>
+__global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
     k_spmv_p(KOp<TW, TV> op, Vecs<TV, NRHS> p, Vecs<TV, NRHS> v, Vecs<TV, NRHS> rh, KScal* sc,
              GridReduce gr, int* worked) {
   using A = typename Acc<TV>::t;
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kThreads)
       pd[q] += (A)rh.v[q][i] * y;
     }
   };
-  if constexpr (kStage<K, TW>) {
+  if constexpr (kStage<K, TW> && DIRECT == 0) {
     extern __shared__ __align__(128) unsigned char dsm[];
     auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
     __shared__ uint64_t bar;
@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(kThreads)
 
 // t = A s^ ; reduce (t, s), (t, t)  (staged tiles when K > 0).  s^ = s, or the
 // preconditioned B s in a preconditioned solve; sres = s.
-template <int K, int NRHS, bool RANK1, typename TW, typename TV>
-__global__ void __launch_bounds__(kThreads)
+template <int K, int NRHS, bool RANK1, typename TW, typename TV, int DIRECT = 0>
+__global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
     k_spmv_s(KOp<TW, TV> op, Vecs<TV, NRHS> s, Vecs<TV, NRHS> sres, Vecs<TV, NRHS> t, KScal* sc,
              GridReduce gr, int* worked) {
   using A = typename Acc<TV>::t;
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kThreads)
       ptt[q] += y * y;
     }
   };
-  if constexpr (kStage<K, TW>) {
+  if constexpr (kStage<K, TW> && DIRECT == 0) {
     extern __shared__ __align__(128) unsigned char dsm[];
     auto* tile = reinterpret_cast<EllStage<K, TW>*>(dsm);
     __shared__ uint64_t bar;
@@ -1954,6 +1954,8 @@ struct StepPlan {
   int64_t spmv_launches = 0;
   double spmv_batch_ms = 0.0;  // back-to-back SpMV launches of profiled solves
   int64_t spmv_batch_launches = 0;
+  double vspmv_batch_ms = 0.0;  // the same for the viscous SpMV (two right sides)
+  int64_t vspmv_batch_launches = 0;
   KScal* sc_timing = nullptr;
   GridReduce gr{};
 };
@@ -2393,7 +2395,8 @@ template <int K, int NRHS, bool RANK1, typename TW, typename TV>
 int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
              const TV* const* b, TV* (*work)[2], double tol, int maxit, SolveResult* res,
              cudaStream_t st, bool prof = false, uint32_t seed_base = 0,
-             const Amg* pc = nullptr, bool x_zero = false, double resume = 0.0) {
+             const Amg* pc = nullptr, bool x_zero = false, double resume = 0.0,
+             bool time_spmv = false) {
   Vecs<TV, NRHS> X, B, R, RH, PP, V, S, T;
   for (int q = 0; q < NRHS; ++q) {
     X.v[q] = x[q];
@@ -2451,6 +2454,14 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
     }
     if (rc0) return rc0;
   }
+  // FP64 SpMVs with two right sides (the viscous solves) load directly at 3
+  // blocks per SM, 85 registers a thread for the gathers of both right sides
+  // in flight: 327 us per launch at 3M rows, against 347 at 4 blocks per SM
+  // and 370 staged (an FP64 tile leaves room for two blocks per SM)
+  constexpr int kVDirect = 3;
+  const int vdir = (std::is_same<TW, double>::value && NRHS == 2 && !pc) ? kVDirect : 0;
+  const int Gv = (int)std::max<int64_t>(
+      1, std::min<int64_t>((op.n + kThreads - 1) / kThreads, (int64_t)sm_count() * kVDirect));
   // Pressure SpMVs of the preconditioned solve: FP32 operators stage 256-row
   // tiles (48 us per launch at 1M rows, against 50-61 us with direct loads at
   // 4-8 blocks per SM); FP64 operators load directly at 4 blocks per SM, 64
@@ -2571,14 +2582,22 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
             continue;
           }
           if (prof) record_ev(s);
-          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PP, V, RH, P->sc, P->gr,
-                                                              work_flag());
+          if (vdir)
+            k_spmv_p<K, NRHS, RANK1, TW, TV, kVDirect><<<Gv, kThreads, 0, s>>>(
+                op, PP, V, RH, P->sc, P->gr, work_flag());
+          else
+            k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, PP, V, RH, P->sc, P->gr,
+                                                                work_flag());
           if (prof) record_ev(s);
           k_update_s<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, V, S, P->sc, P->gr, op.rdot,
                                                          pcc);
           if (prof) record_ev(s);
-          k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, S, S, T, P->sc, P->gr,
-                                                              work_flag());
+          if (vdir)
+            k_spmv_s<K, NRHS, RANK1, TW, TV, kVDirect><<<Gv, kThreads, 0, s>>>(
+                op, S, S, T, P->sc, P->gr, work_flag());
+          else
+            k_spmv_s<K, NRHS, RANK1><<<Gs, kThreads, smem, s>>>(op, S, S, T, P->sc, P->gr,
+                                                                work_flag());
           if (prof) record_ev(s);
           k_update_xr<NRHS><<<G, kThreads, 0, s>>>(op.n, X, R, RH, PP, S, S, T, P->sc, P->gr);
           k_update_p<NRHS, RANK1><<<G, kThreads, 0, s>>>(op.n, R, PP, V, P->sc, P->gr, op.rdot,
@@ -2685,6 +2704,44 @@ int bicgstab(rbffd_ctx* ctx, StepPlan* P, const KOp<TW, TV>& op, TV* const* x,
           cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]) == cudaSuccess) {
         P->spmv_batch_ms += ms;
         P->spmv_batch_launches += kReps;
+      }
+      P->launches += kReps;
+      rc = check_cuda(ctx, cudaGetLastError(), "SpMV timing");
+      if (rc) return rc;
+    }
+  }
+  if constexpr (NRHS == 2 && !RANK1) {
+    if (time_spmv) {
+      // The viscous SpMV (both right sides) the same way: 20 launches back to
+      // back on this solve's operator and vectors, output into a work vector
+      constexpr int kReps = 20;
+      int rc = 0;
+      if (!P->sc_timing) rc = palloc(ctx, P, &P->sc_timing, 1);
+      if (!rc)
+        rc = check_cuda(ctx, cudaMemcpyAsync(P->sc_timing, P->sc, sizeof(KScal),
+                                             cudaMemcpyDeviceToDevice, st),
+                        "timing scalars");
+      if (!rc)
+        rc = check_cuda(ctx, cudaMemsetAsync(&P->sc_timing->done, 0, sizeof(int), st), "timing");
+      if (!rc)
+        rc = check_cuda(ctx, cudaMemsetAsync(&P->sc_timing->stage_err, 0, sizeof(int), st),
+                        "timing");
+      if (rc) return rc;
+      cudaEventRecord(P->ev[0], st);
+      for (int r = 0; r < kReps; ++r) {
+        if (vdir)
+          k_spmv_p<K, NRHS, RANK1, TW, TV, kVDirect><<<Gv, kThreads, 0, st>>>(
+              op, PP, T, RH, P->sc_timing, P->gr, nullptr);
+        else
+          k_spmv_p<K, NRHS, RANK1><<<Gs, kThreads, smem, st>>>(op, PP, T, RH, P->sc_timing, P->gr,
+                                                               nullptr);
+      }
+      cudaEventRecord(P->ev[1], st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(P->ev[1]) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]) == cudaSuccess) {
+        P->vspmv_batch_ms += ms;
+        P->vspmv_batch_launches += kReps;
       }
       P->launches += kReps;
       rc = check_cuda(ctx, cudaGetLastError(), "SpMV timing");
@@ -2820,6 +2877,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
   P->spmv_launches = 0;
   P->spmv_batch_ms = 0.0;
   P->spmv_batch_launches = 0;
+  P->vspmv_batch_ms = 0.0;
+  P->vspmv_batch_launches = 0;
   if (f.profile && !P->ev[0]) {
     for (int i = 0; i < StepPlan::kEv; ++i) {
       int rc = check_cuda(ctx, cudaEventCreate(&P->ev[i]), "event create");
@@ -2919,7 +2978,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
                                f.max_iter, &hr, &sweeps, st);
     } else {
       rc = bicgstab<K, 2, false, double, double>(ctx, P, H64, hx, hb, P->kw64, vtol, f.max_iter,
-                                                 &hr, st);
+                                                 &hr, st, false, 0, nullptr, false, 0.0,
+                                                 f.profile != 0);
     }
     if (rc) return rc;
     if (stats) {
@@ -3034,6 +3094,8 @@ int run_steps(rbffd_ctx* ctx, StepPlan* P, const rbffd_flow& f, rbffd_state* s, 
     stats->spmv_ms = P->spmv_ms;
     stats->spmv_batch_launches = P->spmv_batch_launches;
     stats->spmv_batch_ms = P->spmv_batch_ms;
+    stats->vspmv_batch_launches = P->vspmv_batch_launches;
+    stats->vspmv_batch_ms = P->vspmv_batch_ms;
   }
   return rc;
 }

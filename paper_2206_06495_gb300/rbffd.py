@@ -93,7 +93,8 @@ class Stats(C.Structure):
                 ("poisson_relres", C.c_double), ("launches", C.c_int64),
                 ("spmv_launches", C.c_int64), ("spmv_ms", C.c_double),
                 ("spmv_batch_launches", C.c_int64), ("spmv_batch_ms", C.c_double),
-                ("wall_flux", C.c_double)]
+                ("wall_flux", C.c_double), ("vspmv_batch_launches", C.c_int64),
+                ("vspmv_batch_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
