@@ -29,10 +29,11 @@ def _d(a):
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
 
 
-def _setup(R, n=16, **kw):
+def _setup(R, n=16, precision=None, **kw):
     ctx = R.Context(28, 7, 3)
     nd = ns.jittered_cavity(n, 0)
-    flow = R.flow_from_nodes(ctx, nd, Re=100.0, dt=2e-3, precision=R.PREC_FP64, tol=1e-12, **kw)
+    prec = R.PREC_FP64 if precision is None else precision
+    flow = R.flow_from_nodes(ctx, nd, Re=100.0, dt=2e-3, precision=prec, tol=1e-12, **kw)
     gu, gv = O.lid_bc(nd)
     return ctx, nd, flow, _d(gu), _d(gv)
 
@@ -77,8 +78,9 @@ def test_staged_copy_wait_that_gives_up_reports_and_recovers(R):
     """With the first wait limited to zero polls every staged SpMV tile is
     given up: the step returns RBFFD_ERR_CUDA naming the bounded wait, and
     after the default limit is restored the same context steps normally and
-    matches a fresh run bit for bit."""
-    ctx, nd, flow, gu, gv = _setup(R)
+    matches a fresh run bit for bit.  MIXED precision: its FP32 Krylov SpMVs
+    stage their tiles (the FP64 ones load directly)."""
+    ctx, nd, flow, gu, gv = _setup(R, precision=R.PREC_MIXED)
     st = R.State.zeros(flow)
     R.debug_set_wait_limit(ctx, 0)
     try:
@@ -90,7 +92,7 @@ def test_staged_copy_wait_that_gives_up_reports_and_recovers(R):
     assert st.j == 0
     st = R.State.zeros(flow)
     R.step(ctx, flow, st, gu, gv, 3)
-    ctx2, _, flow2, _, _ = _setup(R)
+    ctx2, _, flow2, _, _ = _setup(R, precision=R.PREC_MIXED)
     st2 = R.State.zeros(flow2)
     R.step(ctx2, flow2, st2, gu, gv, 3)
     assert torch.equal(st.u, st2.u) and torch.equal(st.pt, st2.pt)
