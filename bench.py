@@ -691,15 +691,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": f"lid-driven cavity Re={args.re:g}, jittered {args.n}x{args.n} "
-                               f"P-lattice (M={nd.M}, N={nd.N}), (n,m,q)=(28,7,3), "
-                               f"dt={args.dt:g}, timed after {args.spinup} spin-up and "
-                               f"{args.warmup} warm-up steps from rest, pressure/viscous solves "
-                               f"to {args.tol:g} relative residual (the FP64 path's viscous "
-                               f"solves to 1e-3 of it, not below 1e-13)",
-                   "precision": head, "parallelism": f"replicas{world}",
-                   "spinup_steps": args.spinup,
-                   "l2": "working set (operators ~7 GB) exceeds L2; no flush needed"},
+        "config": workload_config(args, nd.M, nd.N, head, world),
         "gpu_launches": agg["launches"],
         "poisson_iters_per_step": agg["poisson_iters"] / args.steps,
         "helm_iters_per_step": agg["helm_iters"] / args.steps,
@@ -854,6 +846,19 @@ def ensemble_record(R, args, hbm, peak_kind):
         ctx.close()
 
 
+def workload_config(args, M, N, precision, world):
+    """The benchmark's `config`, shared by both arms."""
+    return {"workload": f"lid-driven cavity Re={args.re:g}, jittered {args.n}x{args.n} "
+                        f"P-lattice (M={M}, N={N}), (n,m,q)=(28,7,3), "
+                        f"dt={args.dt:g}, timed after {args.spinup} spin-up and "
+                        f"{args.warmup} warm-up steps from rest, pressure/viscous solves "
+                        f"to {args.tol:g} relative residual (the FP64 path's viscous "
+                        f"solves to 1e-3 of it, not below 1e-13)",
+            "precision": precision, "parallelism": f"replicas{world}",
+            "spinup_steps": args.spinup,
+            "l2": "working set (operators ~7 GB) exceeds L2; no flush needed"}
+
+
 def run_reference(args):
     """The CPU oracle as it stands, on a 150 x 150 sample of the workload, one
     thread: --warmup untimed and --steps timed fractional steps."""
@@ -863,7 +868,9 @@ def run_reference(args):
     n_sample = 150
     t0 = time.time()
     r = oracle_sample(n=n_sample, steps=args.steps, warm=args.warmup, re=args.re, dt=args.dt)
-    M_target = args.n * args.n
+    from paper_2206_06495_gb300 import nodesets as ns
+    full = ns.jittered_cavity(args.n, replica_seed(0))
+    M_target = full.M
     value = (1.0 / r["step_s"]) * (r["M"] / M_target)
     cores, model = host_cpu()
     sample = (f"CPU oracle fractional steps (sparse-LU solves) on a {n_sample}x{n_sample} "
@@ -877,9 +884,7 @@ def run_reference(args):
             "ms_per_step": r["step_s"] * 1e3,
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"lid-driven cavity Re={args.re:g}, jittered "
-                                   f"{args.n}x{args.n} P-lattice, sampled at "
-                                   f"{n_sample}x{n_sample}"},
+            "config": workload_config(args, full.M, full.N, "fp64", world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample, "host": {"nproc": cores, "cpu_model": model}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
