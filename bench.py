@@ -663,28 +663,9 @@ def run_ours(args):
                              "launches_timed": r["spmv_launches"],
                              "timing": "external event-record graph nodes around every "
                                        "launch inside the profiled step's solves"}}
-    # the viscous SpMV (k_spmv_p, two right sides, FP64, direct loads): the
-    # largest single kernel of the FP64 step (its launch list is in
-    # profiles/step_launches_fp64_cavity1m.md); algorithmic bytes of a row: k
-    # indices and k weights once for both right sides, each operand read once
-    # and each output written (368 B), plus the fused dot-product partner of
-    # each right side
     roofline = pres_roof
-    if head == "fp64" and r.get("vspmv_batch_launches", 0) > 0 and r["vspmv_batch_ms"] > 0:
-        vrow, vfused = 12 * k + 2 * (8 + 8), 2 * 8
-        v_ms = r["vspmv_batch_ms"] / r["vspmv_batch_launches"]
-        v_ach = nd.N * vrow / (v_ms * 1e-3) / 1e9
-        roofline = {"kernel": "k_spmv_p_fp64_2rhs", "bound": "hbm", "achieved": v_ach,
-                    "peak": hbm, "unit": "GB/s", "frac": v_ach / hbm,
-                    "traffic": profiled_traffic("k_spmv_p_fp64_2rhs", nd.N),
-                    "bytes_per_row": vrow, "fused_bytes_per_row": vfused,
-                    "frac_with_fused": v_ach * (vrow + vfused) / vrow / hbm,
-                    "rows": nd.N, "peak_kind": peak_kind,
-                    "launches_timed": r["vspmv_batch_launches"], "us_per_launch": v_ms * 1e3,
-                    "timing": "CUDA events around 20 back-to-back launches of this kernel on "
-                              "the operator and vectors of each viscous solve of one "
-                              "profiled step right after the timed steps",
-                    "pressure_spmv": pres_roof}
+    if head == "fp64":
+        roofline = viscous_roofline(r, nd.N, k, hbm, peak_kind, fp64_peak, pres_roof) or pres_roof
     iters_ok = r.get("e2e_same_steps")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -844,6 +825,42 @@ def ensemble_record(R, args, hbm, peak_kind):
         return {"members": E, "error": str(e)[:300]}
     finally:
         ctx.close()
+
+
+def viscous_roofline(r, rows, k, hbm, hbm_kind, fp64_peak_gflops, pressure):
+    """Roofline of the viscous SpMV (k_spmv_p: two right sides, FP64, direct
+    loads), the largest kernel of the FP64 step (its launch list is in
+    profiles/step_launches_fp64_cavity1m.md), from the profiled step's 20
+    back-to-back launches per viscous solve.  It is bound by the FP64 pipe:
+    per row k FMAs and one dot-product FMA per right side, 4 (k + 1) flops,
+    against the FP64 FMA rate rbffd_probe_fma measures in the same run.  Its
+    HBM side: k indices and k weights once for both right sides, each operand
+    read once and each output written (368 B at k = 28), plus the fused
+    dot-product partner of each right side.  None without the timing."""
+    if not r.get("vspmv_batch_launches") or not r.get("vspmv_batch_ms") or not fp64_peak_gflops:
+        return None
+    v_ms = r["vspmv_batch_ms"] / r["vspmv_batch_launches"]
+    vrow, vfused = 12 * k + 2 * (8 + 8), 2 * 8
+    gbs = rows * vrow / (v_ms * 1e-3) / 1e9
+    flops_row = 4 * (k + 1)
+    tflops = rows * flops_row / (v_ms * 1e-3) / 1e12
+    peak = fp64_peak_gflops / 1e3
+    return {"kernel": "k_spmv_p_fp64_2rhs", "bound": "alu", "achieved": tflops, "peak": peak,
+            "unit": "TFLOP/s", "frac": tflops / peak,
+            "peak_kind": "FP64 FMA throughput measured by rbffd_probe_fma in this run "
+                         "(nominal 1.25 TFLOP/s)",
+            "flops_per_row": flops_row,
+            "traffic": profiled_traffic("k_spmv_p_fp64_2rhs", rows),
+            "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "bytes_per_row": vrow, "fused_bytes_per_row": vfused,
+                    "frac_with_fused": gbs * (vrow + vfused) / vrow / hbm,
+                    "peak_kind": hbm_kind},
+            "rows": rows, "launches_timed": r["vspmv_batch_launches"],
+            "us_per_launch": v_ms * 1e3,
+            "timing": "CUDA events around 20 back-to-back launches of this kernel on the "
+                      "operator and vectors of each viscous solve of one profiled step right "
+                      "after the timed steps",
+            "pressure_spmv": pressure}
 
 
 def workload_config(args, M, N, precision, world):
