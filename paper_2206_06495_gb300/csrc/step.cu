@@ -1005,12 +1005,13 @@ struct ZAcc<float, float> {  // FP32 inner solves: plain FP32 sums
 // (t, s), (t, t) -> omega.
 // op.diff (the FP32 rows of the MIXED inner solves): A z = sum_s w_s (z_j - z_i)
 // + a1_i z_i with a1 the FP64 row sums.  Summed directly, FP32 rows of a
-// Laplacian lose the smooth modes: the row sum of the rounded weights is off
-// by about eps32 times the largest weight, against an eigenvalue of order h^2
-// times it (a relative error near 6 % at 1M nodes), which capped every
-// refinement sweep near a 1e-2 reduction.  In difference form a constant
-// operand gives exactly a1_i z_i, and the rounding of each term scales with
-// the differences, smaller by a factor h.
+// Laplacian misrepresent the smooth modes: the row sum of the rounded weights
+// is off by about eps32 times the largest weight, against an eigenvalue of
+// order h^2 times it (a relative error near 6 % at 1M nodes).  In difference
+// form a constant operand gives exactly a1_i z_i, and the rounding of each
+// term scales with the differences, smaller by a factor h.  (On the 1M cavity
+// the MIXED step measured the same either way: its refinement sweeps are set
+// by the right side's unpredictable part, not by this rounding.)
 template <int K, typename TW, typename TV, int WHICH, int DIRECT = 0>
 __global__ void __launch_bounds__(kThreads, DIRECT ? DIRECT : 1)
     k_spmv_pc(KOp<TW, TV> op, const TV* __restrict__ z, TV* __restrict__ y,
@@ -2833,8 +2834,9 @@ int refine(rbffd_ctx* ctx, StepPlan* P, const KOp<double, double>& op64,
     k_to32<NRHS><<<G, kThreads, 0, st>>>(op64.n, R, R32, E32, i0, i1);
     P->launches += 2;  // with the correction below
     // A preconditioned inner solve resumes the previous sweep's Krylov
-    // directions on the new residual (k_resume) instead of starting afresh:
-    // the sweeps then converge at nearly the rate of one unbroken solve.
+    // directions on the new residual (k_resume) instead of starting afresh.
+    // (Measured neutral on the 1M cavity, 33.3 against 31.7 iterations per
+    // step: each sweep's FP64 residual is mostly new content.)
     const double resume =
         resumable && nrm[0] > 0.0 && last_nrm[0] > 0.0 ? last_nrm[0] / nrm[0] : 0.0;
     SolveResult inner;
