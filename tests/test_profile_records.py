@@ -36,3 +36,19 @@ def test_recorded_traffic_matches_the_algorithmic_bytes():
     for key, (nbytes, rows, _) in records().items():
         per_row = nbytes / rows
         assert abs(per_row - EXPECTED[key]) < 0.1 * EXPECTED[key], (key, per_row)
+
+
+def test_viscous_roofline_arithmetic():
+    """bench.py's roofline of the viscous SpMV: 4 (k + 1) flops per row against
+    the measured FP64 FMA rate, 12 k + 32 algorithmic bytes per row against
+    HBM; absent without the profiled timing."""
+    r = {"vspmv_batch_launches": 20, "vspmv_batch_ms": 20 * 0.25}
+    v = bench.viscous_roofline(r, 1_000_000, 28, 5000.0, "measured", 1000.0, {"p": 1})
+    assert v["bound"] == "alu" and v["unit"] == "TFLOP/s"
+    assert abs(v["achieved"] - 1e6 * 116 / 0.25e-3 / 1e12) < 1e-12
+    assert abs(v["frac"] - v["achieved"] / 1.0) < 1e-12
+    assert v["hbm"]["bytes_per_row"] == 368
+    assert abs(v["hbm"]["achieved"] - 1e6 * 368 / 0.25e-3 / 1e9) < 1e-9
+    assert v["pressure_spmv"] == {"p": 1}
+    assert bench.viscous_roofline({}, 1, 28, 1.0, "m", 1.0, None) is None
+    assert bench.viscous_roofline(r, 1, 28, 1.0, "m", 0.0, None) is None
